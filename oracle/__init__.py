@@ -1,0 +1,208 @@
+"""Plain serial CPU oracle for the flow-shop branch-and-bound bounding path.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library (``paper_1206_4973_gb300``)
+and never imports it; the two meet only through the seeded inputs of
+``paper_1206_4973_gb300.inputs``, which hold none of the method's arithmetic.
+
+The arithmetic lives in ``fsp_oracle.c`` (plain C, int32, serial), compiled
+with gcc into ``oracle/_build/libfsp_oracle.so`` by :func:`build`.  Each
+function below cites the part of the paper it follows; the bound itself is
+the two-machine Johnson bound with time lags whose O(m^2 n log n) cost
+Sec. V-D states (the paper prints no formula), together with the one-machine
+bounds.  Pins: see the header of ``fsp_oracle.c``.  Parity unpinned: the exact
+node interleaving of a pool > 1 search after the incumbent improves.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fsp_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libfsp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, INCOMPLETE, ERR_ARG, ERR_OOM = 0, 1, -1, -3
+INF = 2**31 - 1
+STATS = ("bounded", "branched", "pruned", "leaves", "iterations", "incumbent_updates")
+
+
+def build(force: bool = False) -> str:
+    """Compile fsp_oracle.c with gcc (portable flags: same results on x86 and Arm)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-fno-strict-aliasing",
+                        _SRC, "-o", tmp], check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            c_int, c_i32, c_i64 = ctypes.c_int, ctypes.c_int32, ctypes.c_int64
+            sig = {
+                "orc_num_pairs": (c_int, [c_int]),
+                "orc_release_times": (None, [c_int, c_int, i32p, u8p, c_int, i32p]),
+                "orc_makespan": (c_i32, [c_int, c_int, i32p, u8p, c_int]),
+                "orc_check_node": (c_int, [c_int, u8p, c_int]),
+                "orc_bound_pool": (c_int, [c_int, c_int, i32p, u8p, c_i64, c_int, i32p]),
+                "orc_lb_parts": (c_int, [c_int, c_int, i32p, u8p, c_int, i32p, i32p, i32p]),
+                "orc_tables_dump": (c_int, [c_int, c_int, i32p, i32p, i32p, u8p]),
+                "orc_bruteforce": (c_i32, [c_int, c_int, i32p, u8p]),
+                "orc_neh": (c_i32, [c_int, c_int, i32p, u8p]),
+                "orc_solve": (c_int, [c_int, c_int, i32p, c_i32, c_i64, c_i64, i64p, c_i64,
+                                      i32p, u8p, i64p, i64p, c_i64]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _p(arr, ctype):
+    return arr.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _inst(p):
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    if p.ndim != 2:
+        raise ValueError("p must be n x m (job-major)")
+    return p, p.shape[0], p.shape[1]
+
+
+def num_pairs(m: int) -> int:
+    return m * (m - 1) // 2
+
+
+def pairs(m: int):
+    """Machine pairs (k, l), k < l, in the oracle's numbering (k-major)."""
+    return [(k, l) for k in range(m) for l in range(k + 1, m)]
+
+
+def release_times(p, perm, d: int) -> np.ndarray:
+    """Sec. II-B: machine release times after scheduling perm[0..d)."""
+    p, n, m = _inst(p)
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    out = np.zeros(m, dtype=np.int32)
+    _load().orc_release_times(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8), int(d),
+                              _p(out, ctypes.c_int32))
+    return out
+
+
+def makespan(p, perm) -> int:
+    """Sec. II-B: completion time of the last job on the last machine."""
+    p, n, m = _inst(p)
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    return int(_load().orc_makespan(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8), len(perm)))
+
+
+def tables(p):
+    """Tails q[n,m], lags lag[P,n] and Johnson orders order[P,n] (pairs k-major)."""
+    p, n, m = _inst(p)
+    P = num_pairs(m)
+    q = np.zeros((n, m), np.int32)
+    lag = np.zeros((P, n), np.int32)
+    order = np.zeros((P, n), np.uint8)
+    rc = _load().orc_tables_dump(n, m, _p(p, ctypes.c_int32), _p(q, ctypes.c_int32),
+                                 _p(lag, ctypes.c_int32), _p(order, ctypes.c_uint8))
+    if rc != OK:
+        raise ValueError("invalid instance")
+    return q, lag, order
+
+
+def lb_parts(p, perm, d: int):
+    """The node bound and its parts: (LB, LB1, [LB_kl per pair])."""
+    p, n, m = _inst(p)
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    lb = ctypes.c_int32(0)
+    lb1 = ctypes.c_int32(0)
+    pv = np.zeros(max(num_pairs(m), 1), np.int32)
+    rc = _load().orc_lb_parts(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8), int(d),
+                              ctypes.byref(lb), ctypes.byref(lb1), _p(pv, ctypes.c_int32))
+    if rc != OK:
+        raise ValueError("invalid node")
+    return int(lb.value), int(lb1.value), pv[: num_pairs(m)].copy()
+
+
+def lb(p, perm, d: int) -> int:
+    return lb_parts(p, perm, d)[0]
+
+
+def bound_pool(p, nodes) -> np.ndarray:
+    """Bound every record of nodes (uint8 [count, stride]: perm[n], depth at byte n)."""
+    p, n, m = _inst(p)
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+    count, stride = nodes.shape
+    out = np.zeros(count, np.int32)
+    rc = _load().orc_bound_pool(n, m, _p(p, ctypes.c_int32), _p(nodes, ctypes.c_uint8), count,
+                                stride, _p(out, ctypes.c_int32))
+    if rc != OK:
+        raise ValueError(f"orc_bound_pool failed ({rc})")
+    return out
+
+
+def bruteforce(p):
+    """Optimum over all n! permutations and the lexicographically first optimal one."""
+    p, n, m = _inst(p)
+    perm = np.zeros(n, np.uint8)
+    c = _load().orc_bruteforce(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8))
+    return int(c), perm
+
+
+def neh(p):
+    """NEH insertion heuristic: (makespan, permutation)."""
+    p, n, m = _inst(p)
+    perm = np.zeros(n, np.uint8)
+    c = _load().orc_neh(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8))
+    return int(c), perm
+
+
+def solve(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, schedule=None,
+          trace_cap: int = 0, ub0_perm=None):
+    """Serial pool-synchronous depth-first B&B (Sec. II-A operators, Sec. III pool).
+
+    Returns a dict with status, cmax, perm (None if no schedule beat ub0 and no
+    ub0_perm was given), the counters of STATS and, if trace_cap > 0, the
+    per-iteration trace rows (parents, children, survivors, UB after).
+    """
+    p, n, m = _inst(p)
+    perm = np.zeros(n, np.uint8)
+    stats = np.zeros(len(STATS), np.int64)
+    cmax = ctypes.c_int32(0)
+    sched = None if schedule is None else np.ascontiguousarray(schedule, dtype=np.int64)
+    trace = np.zeros((max(trace_cap, 1), 4), np.int64)
+    rc = _load().orc_solve(n, m, _p(p, ctypes.c_int32), int(ub0), int(pool), int(node_budget),
+                           None if sched is None else _p(sched, ctypes.c_int64),
+                           0 if sched is None else len(sched), ctypes.byref(cmax),
+                           _p(perm, ctypes.c_uint8), _p(stats, ctypes.c_int64),
+                           _p(trace, ctypes.c_int64) if trace_cap > 0 else None, int(trace_cap))
+    if rc < 0:
+        raise RuntimeError(f"orc_solve failed ({rc})")
+    res = {k: int(v) for k, v in zip(STATS, stats)}
+    res["status"] = int(rc)
+    res["cmax"] = int(cmax.value)
+    if res["incumbent_updates"] > 0:
+        res["perm"] = perm
+    else:
+        res["perm"] = None if ub0_perm is None else np.asarray(ub0_perm, np.uint8)
+    if trace_cap > 0:
+        res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
+    return res

@@ -1,0 +1,328 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each check uses a different computation from the oracle's: the longest-path
+characterisation of the makespan, brute force over orders or completions,
+Johnson's theorem at m = 2, a recursive DFS, and the order-free set of nodes a
+search with a fixed incumbent must bound.  A dropped term, a wrong sign or
+index, or a swapped operand in the oracle fails at least one of them.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_4973_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers --
+def longest_path_makespan(p, perm):
+    """Makespan as the heaviest monotone lattice path through the grid of
+    (position, machine) operation times (permutation flow shop, Sec. II-B)."""
+    n_, m = len(perm), p.shape[1]
+    best = 0
+    # a path is fixed by the positions at which it steps to the next machine
+    for cuts in itertools.combinations_with_replacement(range(n_), m - 1):
+        s, pos = 0, 0
+        bounds = list(cuts) + [n_ - 1]
+        for k in range(m):
+            end = bounds[k]
+            for i in range(pos, end + 1):
+                s += int(p[perm[i], k])
+            pos = end
+        best = max(best, s)
+    return best
+
+
+def release_time_brute(p, prefix, k):
+    """Completion time on machine k of the prefix = longest path on machines 0..k."""
+    if len(prefix) == 0:
+        return 0
+    return longest_path_makespan(p[:, : k + 1], list(prefix))
+
+
+def two_machine_value(a, b, lag, order, ck, cl):
+    """Schedule the jobs in `order` on machines k then l (k from ck, l from cl,
+    job j may start on l only lag_j after it ends on k); return the end on l."""
+    tk, tl = ck, cl
+    for j in order:
+        start_k = tk
+        tk = start_k + a[j]
+        start_l = max(tl, tk + lag[j])
+        tl = start_l + b[j]
+    return tl
+
+
+def rand_nodes(n, count, seed):
+    rng = inputs.SplitMix64(seed)
+    out = []
+    for _ in range(count):
+        perm = inputs.permutation(n, rng)
+        d = int(rng.take_hi(1)[0] % np.uint64(n + 1))
+        out.append((perm, d))
+    return out
+
+
+# ------------------------------------------------------------- makespan ---
+def test_makespan_hand_worked():
+    # two jobs, two machines: job0 = (3, 2), job1 = (1, 4)
+    # order (0, 1): M1 busy [0,3) then [3,4); M2 [3,5) then [5,9)  -> 9
+    # order (1, 0): M1 [0,1) then [1,4);  M2 [1,5) then [5,7)      -> 7
+    p = np.array([[3, 2], [1, 4]], np.int32)
+    assert oracle.makespan(p, [0, 1]) == 9
+    assert oracle.makespan(p, [1, 0]) == 7
+    # one job: the sum of its times
+    assert oracle.makespan(np.array([[5, 6, 7]], np.int32), [0]) == 18
+
+
+@pytest.mark.parametrize("n,m,seed", [(3, 3, 11), (4, 5, 12), (6, 3, 13), (5, 4, 14)])
+def test_makespan_equals_longest_path(n, m, seed):
+    p = inputs.instance(n, m, seed)
+    rng = inputs.SplitMix64(seed + 1000)
+    for _ in range(6):
+        perm = inputs.permutation(n, rng)
+        assert oracle.makespan(p, perm) == longest_path_makespan(p, list(perm))
+
+
+def test_release_times_match_truncated_longest_path():
+    p = inputs.instance(6, 5, 21)
+    for perm, d in rand_nodes(6, 8, 22):
+        C = oracle.release_times(p, perm, d)
+        for k in range(5):
+            assert C[k] == release_time_brute(p, perm[:d], k)
+
+
+# ------------------------------------------------ two-machine sub-bounds ---
+@pytest.mark.parametrize("n,m,seed", [(7, 4, 31), (6, 5, 32), (7, 3, 33)])
+def test_pair_bound_is_optimal_two_machine_value(n, m, seed):
+    """LB_kl = min over every order of the remaining jobs of the lagged
+    two-machine schedule on (k, l), plus the smallest tail after l."""
+    p = inputs.instance(n, m, seed)
+    for perm, d in rand_nodes(n, 10, seed + 1):
+        prefix, U = list(perm[:d]), list(perm[d:])
+        _, _, pv = oracle.lb_parts(p, perm, d)
+        C = [release_time_brute(p, prefix, k) for k in range(m)]
+        for idx, (k, l) in enumerate(oracle.pairs(m)):
+            a, b = p[:, k], p[:, l]
+            lag = p[:, k + 1:l].sum(axis=1)
+            qmin_l = min((int(p[j, l + 1:].sum()) for j in U), default=0)
+            best = min(two_machine_value(a, b, lag, o, C[k], C[l])
+                       for o in itertools.permutations(U)) if U else C[l]
+            assert pv[idx] == best + qmin_l, (perm, d, k, l)
+
+
+@pytest.mark.parametrize("crafted", [False, True])
+def test_one_machine_bound_definition(crafted):
+    """LB1 = max_k release + remaining work + smallest tail, written from the
+    definition with brute-force release times.  The crafted instance makes
+    machine 0 the bottleneck, so the tail term decides LB1."""
+    n, m = 6, 4
+    p = inputs.instance(n, m, 41)
+    if crafted:
+        p = p % 5 + 1
+        p[:, 0] += 90
+    for perm, d in rand_nodes(n, 10, 42):
+        U = list(perm[d:])
+        lb, lb1, pv = oracle.lb_parts(p, perm, d)
+        want = 0
+        for k in range(m):
+            ck = release_time_brute(p, list(perm[:d]), k)
+            sk = sum(int(p[j, k]) for j in U)
+            qk = min((int(p[j, k + 1:].sum()) for j in U), default=0)
+            want = max(want, ck + sk + qk)
+        assert lb1 == want
+        assert lb == max(lb1, int(pv.max()))
+
+
+def test_johnson_orders_are_permutations_with_rule():
+    p = inputs.instance(9, 6, 43)
+    q, lag, order = oracle.tables(p)
+    for idx, (k, l) in enumerate(oracle.pairs(6)):
+        o = list(order[idx])
+        assert sorted(o) == list(range(9))
+        a, b = p[:, k], p[:, l]
+        first = [j for j in o if a[j] <= b[j]]
+        # set A precedes set B
+        assert o[: len(first)] == first
+
+
+# ------------------------------------------------------------ the bound ---
+@pytest.mark.parametrize("n,m,seed", [(6, 3, 51), (7, 4, 52), (5, 6, 53), (7, 5, 54)])
+def test_bound_is_valid_and_exact_at_the_leaves(n, m, seed):
+    p = inputs.instance(n, m, seed)
+    for perm, d in rand_nodes(n, 14, seed + 7):
+        lb = oracle.lb(p, perm, d)
+        best = min(oracle.makespan(p, list(perm[:d]) + list(o))
+                   for o in itertools.permutations(perm[d:]))
+        assert lb <= best
+        if d >= n - 1:
+            assert lb == best == longest_path_makespan(p, list(perm))
+
+
+@pytest.mark.parametrize("seed", [61, 62, 63, 64])
+def test_bound_exact_at_m2(seed):
+    """With two machines the pair relaxation is the problem itself (Johnson's
+    theorem): every node's bound equals its best completion."""
+    n = 7
+    p = inputs.instance(n, 2, seed)
+    opt, _ = oracle.bruteforce(p)
+    assert oracle.lb(p, np.arange(n), 0) == opt
+    for perm, d in rand_nodes(n, 12, seed + 3):
+        best = min(oracle.makespan(p, list(perm[:d]) + list(o))
+                   for o in itertools.permutations(perm[d:]))
+        assert oracle.lb(p, perm, d) == best
+
+
+def test_bound_pool_matches_single_node_and_rejects_bad_records():
+    n, m = 8, 5
+    p, _, nodes = inputs.pool_workload(n, m, 71, 64)
+    lbs = oracle.bound_pool(p, nodes)
+    for t in range(64):
+        assert lbs[t] == oracle.lb(p, nodes[t, :n], nodes[t, n])
+    bad = nodes.copy()
+    bad[3, 0] = bad[3, 1]  # repeated job
+    with pytest.raises(ValueError):
+        oracle.bound_pool(p, bad)
+    bad = nodes.copy()
+    bad[5, n] = n + 1  # depth > n
+    with pytest.raises(ValueError):
+        oracle.bound_pool(p, bad)
+
+
+# ----------------------------------------------------------- the search ---
+@pytest.mark.parametrize("n,m,seed", [(2, 3, 80), (5, 2, 81), (6, 3, 82), (7, 5, 83), (8, 4, 84),
+                                      (8, 2, 85), (9, 3, 86)])
+@pytest.mark.parametrize("pool", [1, 3, 7, 1024])
+def test_solver_reaches_brute_force_optimum(n, m, seed, pool):
+    p = inputs.instance(n, m, seed)
+    opt, _ = oracle.bruteforce(p)
+    res = oracle.solve(p, pool=pool, trace_cap=100000)
+    assert res["status"] == oracle.OK
+    assert res["cmax"] == opt
+    assert sorted(res["perm"]) == list(range(n))
+    assert oracle.makespan(p, res["perm"]) == opt
+    tr = res["trace"]
+    # a pool never holds more children than its size unless one parent alone overflows it
+    assert np.all((tr[:, 1] <= pool) | (tr[:, 0] == 1))
+    assert tr[:, 1].sum() == res["bounded"] and tr[:, 0].sum() == res["branched"]
+    assert res["bounded"] == res["leaves"] + res["pruned"] + tr[:, 2].sum()
+
+
+def textbook_dfs(p, n, ub0):
+    """Recursive depth-first B&B: branch a node, bound all its children, let
+    complete children improve the incumbent in order, drop children with
+    bound >= incumbent, recurse into the rest in order."""
+    st = {"ub": ub0, "bounded": 0, "branched": 0, "perm": None}
+
+    def visit(prefix, rem):
+        st["branched"] += 1
+        kids = []
+        for j in sorted(rem):
+            child = prefix + [j]
+            rest = sorted(set(rem) - {j})
+            kids.append((child, rest, oracle.lb(p, child + rest, len(child))))
+        st["bounded"] += len(kids)
+        for child, rest, v in kids:
+            if len(rest) == 1 and v < st["ub"]:
+                st["ub"], st["perm"] = v, child + rest
+        keep = [(c, r, v) for c, r, v in kids if len(r) > 1 and v < st["ub"]]
+        for c, r, _ in keep:
+            visit(c, r)
+
+    visit([], list(range(n)))
+    return st
+
+
+@pytest.mark.parametrize("n,m,seed", [(6, 3, 91), (7, 4, 92), (8, 3, 93)])
+def test_pool_one_equals_recursive_dfs(n, m, seed):
+    p = inputs.instance(n, m, seed)
+    ref = textbook_dfs(p, n, oracle.INF)
+    res = oracle.solve(p, pool=1)
+    assert (res["bounded"], res["branched"], res["cmax"]) == (ref["bounded"], ref["branched"], ref["ub"])
+    assert list(res["perm"]) == ref["perm"]
+
+
+@pytest.mark.parametrize("n,m,seed", [(7, 4, 101), (8, 3, 102), (8, 5, 103)])
+def test_fixed_incumbent_explores_order_free_set(n, m, seed):
+    """With ub0 = optimum the incumbent never changes, so the nodes bounded are
+    exactly the children of every node whose ancestors all bound below it,
+    whatever the pool size."""
+    p = inputs.instance(n, m, seed)
+    opt, _ = oracle.bruteforce(p)
+    bounded = branched = 0
+    frontier = [([], list(range(n)))]
+    while frontier:
+        prefix, rem = frontier.pop()
+        branched += 1
+        for j in rem:
+            child, rest = prefix + [j], [x for x in rem if x != j]
+            bounded += 1
+            if len(rest) > 1 and oracle.lb(p, child + rest, len(child)) < opt:
+                frontier.append((child, rest))
+    for pool in (1, 2, 5, 16, 4096):
+        res = oracle.solve(p, ub0=opt, pool=pool)
+        assert (res["bounded"], res["branched"]) == (bounded, branched)
+        assert res["cmax"] == opt and res["incumbent_updates"] == 0 and res["perm"] is None
+
+
+def test_solver_edge_cases():
+    p1 = np.array([[4, 5, 6]], np.int32)
+    r = oracle.solve(p1)
+    assert r["cmax"] == 15 and list(r["perm"]) == [0] and r["iterations"] == 0
+    p = inputs.instance(6, 3, 111)
+    opt, _ = oracle.bruteforce(p)
+    r = oracle.solve(p, ub0=opt - 1)  # nothing beats a UB below the optimum
+    assert r["cmax"] == opt - 1 and r["perm"] is None
+    r = oracle.solve(p, pool=4, node_budget=10)
+    assert r["status"] == oracle.INCOMPLETE and r["bounded"] >= 10
+
+
+def test_schedule_replay_equals_fixed_pool():
+    p = inputs.instance(8, 4, 121)
+    a = oracle.solve(p, pool=9)
+    b = oracle.solve(p, pool=1, schedule=[9])
+    assert {k: a[k] for k in oracle.STATS} == {k: b[k] for k in oracle.STATS}
+
+
+# ---------------------------------------------------------------- NEH -----
+@pytest.mark.parametrize("n,m,seed", [(1, 3, 130), (2, 2, 131), (7, 4, 132), (8, 5, 133)])
+def test_neh_is_a_valid_upper_bound(n, m, seed):
+    p = inputs.instance(n, m, seed)
+    c, perm = oracle.neh(p)
+    assert sorted(perm) == list(range(n))
+    assert c == oracle.makespan(p, perm) == longest_path_makespan(p, list(perm))
+    assert c >= oracle.bruteforce(p)[0]
+
+
+def test_neh_hand_worked():
+    # totals: job0 = 5, job1 = 5, job2 = 9 -> insertion order 2, 0, 1
+    # [2] -> insert 0: [0,2] = 12, [2,0] = 11 -> [2,0]
+    # insert 1 into [2,0]: [1,2,0] = 12, [2,1,0] = 15, [2,0,1] = 15 -> [1,2,0]
+    p = np.array([[3, 2], [1, 4], [4, 5]], np.int32)
+    c, perm = oracle.neh(p)
+    assert list(perm) == [1, 2, 0] and c == 12
+
+
+# --------------------------------------------------------- golden files ---
+def test_golden_files_reproduce():
+    """tests/golden/*.json were written by tests/golden/make_golden.py from the
+    oracle alone; the oracle must still reproduce them."""
+    for name in sorted(os.listdir(GOLDEN)):
+        if not name.endswith(".json"):
+            continue
+        with open(os.path.join(GOLDEN, name)) as f:
+            g = json.load(f)
+        if g["kind"] == "solve":
+            p = inputs.instance(g["n"], g["m"], g["seed"])
+            r = oracle.solve(p, ub0=g["ub0"], pool=g["pool"])
+            for k in oracle.STATS + ("cmax",):
+                assert r[k] == g[k], (name, k)
+            assert list(r["perm"]) == g["perm"]
+        elif g["kind"] == "bound_pool":
+            p, _, nodes = inputs.pool_workload(g["n"], g["m"], g["seed"], g["count"])
+            lbs = oracle.bound_pool(p, nodes)
+            assert lbs.tolist() == g["lb"]
