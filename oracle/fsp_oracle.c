@@ -523,7 +523,9 @@ int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t
         stats[ST_BOUNDED] += nch;
         stats[ST_BRANCHED] += np;
 
-        /* complete schedules update the incumbent, in L order */
+        /* complete schedules update the incumbent, in L order; the UB
+         * changes once per iteration, so an update is counted per iteration */
+        const int32_t ub_start = UB;
         for (int64_t i = 0; i < nch; i++) {
             const uint8_t *ch = children + (size_t)i * w;
             if (ch[n] != n - 1) continue;
@@ -531,9 +533,9 @@ int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t
             if (lbs[i] < UB) {
                 UB = lbs[i];
                 memcpy(perm_out, ch, (size_t)n);
-                stats[ST_UPDATES]++;
             }
         }
+        if (UB < ub_start) stats[ST_UPDATES]++;
 
         /* elimination, then push survivors in reverse L order */
         int64_t nsurv = 0;
