@@ -1,0 +1,161 @@
+/*
+ * fsp.h -- C ABI of the GB300 (sm_103a) parallel-bounding library for the
+ * permutation flow-shop branch-and-bound (Chakroun & Melab, "An Adaptative
+ * Multi-GPU based Branch-and-Bound. A Case Study: the Flow-Shop Scheduling
+ * Problem").
+ *
+ * Problem (Sec. II-B): n jobs, m machines, every job visits machines 0..m-1
+ * in that order, every machine processes the jobs in the same order (a
+ * permutation), p[j][k] is the time of job j on machine k; minimise the
+ * makespan (completion time of the last job on the last machine).
+ *
+ * A subproblem ("node", Sec. II-B: node i is the subproblem with job J_i
+ * scheduled first) is a scheduled prefix plus the set of remaining jobs.  Its
+ * record is `fsp_node_stride(n)` bytes: bytes 0..n-1 hold a permutation of
+ * 0..n-1 whose first d entries are the prefix in order and whose last n-d
+ * entries are the remaining set in any order; byte n holds d (0 <= d <= n);
+ * the rest is zero padding.  Records are contiguous, 16-byte aligned.
+ *
+ * The lower bound (the paper states only its O(m^2 n log n) cost, Sec. V-D)
+ * is the maximum of
+ *   - the one-machine bounds  C_k + S_k + qmin_k  for every machine k, and
+ *   - the two-machine bounds with time lags for every machine pair k < l:
+ *     the remaining jobs in Johnson's order for the pair (jobs with
+ *     p_k <= p_l by increasing p_k + lag, then the others by decreasing
+ *     p_l + lag; equal keys by job index), t_k = C_k, t_l = C_l,
+ *     t_k += p_k(j), t_l = max(t_l, t_k + lag(j)) + p_l(j), plus qmin_l,
+ * where C_k is machine k's completion time after the prefix, S_k the remaining
+ * work on k, qmin_k the smallest remaining tail after k (0 if none remain),
+ * and lag(j) job j's time on the machines strictly between k and l.
+ *
+ * Conventions: all functions return an int status (FSP_OK = 0, FSP_INCOMPLETE
+ * = 1 when a node budget stopped a search, negative on error) unless stated;
+ * after an error fsp_last_error() returns a message (per thread).  Device
+ * pointers are CUDA device memory of the device current at
+ * fsp_create_instance; host pointers are ordinary host memory.  The caller
+ * owns every buffer it passes; the library never frees caller memory.  A
+ * `stream` argument is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef FSP_H
+#define FSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FSP_OK 0
+#define FSP_INCOMPLETE 1
+#define FSP_ERR_ARG (-1)
+#define FSP_ERR_CUDA (-2)
+#define FSP_ERR_OOM (-3)
+#define FSP_ERR_CAPACITY (-4)
+#define FSP_ERR_TIMEOUT (-5)
+
+#define FSP_UB_INF 2147483647 /* "no upper bound yet" */
+#define FSP_LB_INVALID (-1)   /* lb_out value of a malformed node record */
+
+#define FSP_MAX_JOBS 255
+#define FSP_MAX_MACHINES 64
+
+/* Opaque instance: processing times plus the per-instance tables (tails,
+ * lags and Johnson order of every machine pair) resident on the device. */
+typedef struct fsp_instance fsp_instance;
+
+/* Search counters (Sec. II-A operators). */
+typedef struct {
+    int64_t nodes_bounded;     /* children whose bound was computed        */
+    int64_t nodes_branched;    /* parents decomposed (the root included)   */
+    int64_t nodes_pruned;      /* non-leaf children with bound >= UB       */
+    int64_t leaves;            /* children at depth n-1 (complete schedules)*/
+    int64_t iterations;        /* pool iterations                          */
+    int64_t incumbent_updates; /* strict improvements of the UB            */
+    double time_ms;            /* wall time of the search on the stream    */
+} fsp_stats;
+
+/* Options of fsp_solve; fsp_default_options() fills the defaults. */
+typedef struct {
+    int64_t pool_size;      /* children bounded per iteration (Sec. III pool); default 1024 */
+    int64_t node_budget;    /* stop (FSP_INCOMPLETE) before an iteration once this many
+                               nodes are bounded; 0 = no limit */
+    int64_t stack_capacity; /* node records in the device stack; 0 = n * (pool + n) */
+    const int32_t *ub0_perm;/* host, n entries or NULL: a schedule whose makespan is ub0 */
+    int64_t *trace;         /* host or NULL: per iteration {parents, children, survivors,
+                               UB after}, int64 x 4 */
+    int64_t trace_cap;      /* rows available in trace */
+    const int64_t *schedule;/* host or NULL: pool size of each iteration (the last entry
+                               repeats), e.g. replaying an autotuned run */
+    int64_t schedule_len;
+    void *workspace;        /* device or NULL: caller-owned scratch of at least
+                               fsp_solve_workspace_bytes() bytes, 256-byte aligned;
+                               NULL = the library allocates and frees its own */
+    void *stream;           /* cudaStream_t; NULL = legacy default stream */
+} fsp_options;
+
+/* Fill *opt with the defaults (pool 1024, no budget, default capacity). */
+int fsp_default_options(fsp_options *opt);
+
+/* Bytes per node record for n jobs: n + 1 rounded up to 16. */
+int fsp_node_stride(int n);
+
+/* Sec. II-B instance.  p: host, n*m int32, job-major (p[j*m + k]), each in
+ * 1..32767; 1 <= n <= 255, 2 <= m <= 64.  Copies p to the current device and
+ * builds the per-instance tables there (one kernel; synchronous).  *out
+ * receives a handle to release with fsp_destroy_instance.
+ * Errors: FSP_ERR_ARG (shape or values), FSP_ERR_OOM, FSP_ERR_CUDA. */
+int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance **out);
+
+/* Release the instance and its device tables (synchronises its device). */
+void fsp_destroy_instance(fsp_instance *inst);
+
+/* Copy the device tables back for inspection (synchronous).  Any pointer may
+ * be NULL.  q: host n*m int32 (q[j*m+k] = time of job j after machine k);
+ * lag: host P*n int32; order: host P*n uint8 (Johnson order of pair kl);
+ * pairs numbered k-major: (0,1), (0,2), ..., (0,m-1), (1,2), ... */
+int fsp_instance_tables(const fsp_instance *inst, int32_t *q, int32_t *lag, uint8_t *order);
+
+/* Sec. III parallel bounding (Type 1 model): the bound of `count` node
+ * records.  nodes: device, count * fsp_node_stride(n) bytes.  lb_out: device,
+ * count int32.  Every node gets its full bound, whatever `ub` (reserved for
+ * modes that stop early once a partial bound reaches ub).  Asynchronous on
+ * `stream`.  A malformed record (depth > n, a job id >= n or repeated) gets
+ * FSP_LB_INVALID and sets the instance's error flag, which fsp_check_status
+ * reports.  Errors (immediate): FSP_ERR_ARG for count < 0 or NULL buffers,
+ * FSP_ERR_CUDA for a failed launch. */
+int fsp_bound_pool(fsp_instance *inst, const uint8_t *nodes, int64_t count, int32_t ub,
+                   int32_t *lb_out, void *stream);
+
+/* Synchronise `stream` and report (then clear) the instance's error flag:
+ * FSP_ERR_ARG if a malformed record was seen since the last check. */
+int fsp_check_status(fsp_instance *inst, void *stream);
+
+/* Device scratch bytes fsp_solve needs with these options (opt may be NULL). */
+int64_t fsp_solve_workspace_bytes(const fsp_instance *inst, const fsp_options *opt);
+
+/* Exact branch-and-bound (Sec. II-A operators, Sec. III pool of deepest
+ * nodes), entirely on the device.  The search starts from the root (nothing
+ * scheduled) with UB = ub0 (FSP_UB_INF = none) and repeats: pop parents from
+ * the top of the depth-first stack while their children fit in the pool
+ * (at least one parent); bound every child (children of a parent in
+ * increasing job index of the appended job); complete schedules (depth n-1)
+ * lower the UB, first in that order winning ties; keep the other children
+ * whose bound is below the UB; push the survivors so the first is on top.
+ * Outputs: *cmax = final UB (the optimum when the search completes); perm:
+ * host, n int32, receives the optimal permutation if the search improved on
+ * ub0 (else opt->ub0_perm if given, else left untouched); stats (may be NULL).
+ * Returns FSP_OK, FSP_INCOMPLETE (budget reached; cmax is the best so far),
+ * FSP_ERR_CAPACITY (stack full; nothing was lost), FSP_ERR_ARG, FSP_ERR_OOM
+ * or FSP_ERR_CUDA.  Synchronous. */
+int fsp_solve(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
+              const fsp_options *opt);
+
+/* Message of the last error on this thread ("" if none). */
+const char *fsp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSP_H */

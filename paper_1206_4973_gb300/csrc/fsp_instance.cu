@@ -1,0 +1,188 @@
+// fsp_instance.cu -- instance creation and the per-instance tables (K0):
+// tails, lags and the Johnson order of every machine pair, computed on the
+// device once per instance.  The O(n log n) sort per pair that Sec. V-D
+// counts inside each bound is hoisted here: a job's position in the pair's
+// order is the number of jobs that precede it under Johnson's rule.
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "fsp_common.cuh"
+
+static thread_local char g_err[512];
+
+void fsp_set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+int fsp_cuda_fail(cudaError_t e, const char *what)
+{
+    fsp_set_error("CUDA error %s (%s) in %s", cudaGetErrorName(e), cudaGetErrorString(e), what);
+    return e == cudaErrorMemoryAllocation ? FSP_ERR_OOM : FSP_ERR_CUDA;
+}
+
+extern "C" const char *fsp_last_error(void) { return g_err; }
+
+extern "C" int fsp_node_stride(int n) { return (n + 1 + 15) / 16 * 16; }
+
+extern "C" int fsp_default_options(fsp_options *opt)
+{
+    if (!opt) { fsp_set_error("fsp_default_options: opt is NULL"); return FSP_ERR_ARG; }
+    memset(opt, 0, sizeof *opt);
+    opt->pool_size = 1024;
+    return FSP_OK;
+}
+
+// Tails q[j][k] = sum over h > k of p[j][h].
+__global__ void k_tails(int n, int m, const int32_t *__restrict__ p, int32_t *__restrict__ q)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * m) return;
+    const int j = i / m, k = i - j * m;
+    int32_t s = 0;
+    for (int h = k + 1; h < m; ++h) s += p[j * m + h];
+    q[i] = s;
+}
+
+// Johnson's rule with lags: does job i (a_i, b_i, lag_i) go before job j?
+// Jobs with a <= b first, by increasing a + lag; then the others by
+// decreasing b + lag; equal keys by job index.
+__device__ __forceinline__ bool johnson_precedes(int i, int32_t ai, int32_t bi, int32_t li, int j,
+                                                 int32_t aj, int32_t bj, int32_t lj)
+{
+    const bool late_i = ai > bi, late_j = aj > bj;
+    if (late_i != late_j) return !late_i;
+    if (!late_i) {
+        const int32_t ki = ai + li, kj = aj + lj;
+        if (ki != kj) return ki < kj;
+    } else {
+        const int32_t ki = bi + li, kj = bj + lj;
+        if (ki != kj) return ki > kj;
+    }
+    return i < j;
+}
+
+// One block per machine pair, one thread per job.
+__global__ void k_pair_tables(int n, int m, const int32_t *__restrict__ p, int32_t *__restrict__ lag,
+                              uint8_t *__restrict__ order, FspEntry *__restrict__ ent)
+{
+    __shared__ int32_t a_s[FSP_MAX_JOBS + 1], b_s[FSP_MAX_JOBS + 1], l_s[FSP_MAX_JOBS + 1];
+    const int kl = blockIdx.x;
+    int k = 0, rem = kl;
+    while (rem >= m - 1 - k) { rem -= m - 1 - k; ++k; }
+    const int l = k + 1 + rem;
+    const int j = threadIdx.x;
+    if (j < n) {
+        int32_t lg = 0;
+        for (int h = k + 1; h < l; ++h) lg += p[j * m + h];
+        a_s[j] = p[j * m + k];
+        b_s[j] = p[j * m + l];
+        l_s[j] = lg;
+        lag[(size_t)kl * n + j] = lg;
+    }
+    __syncthreads();
+    if (j < n) {
+        const int32_t aj = a_s[j], bj = b_s[j], lj = l_s[j];
+        int rank = 0;
+        for (int i = 0; i < n; ++i)
+            rank += (i != j) && johnson_precedes(i, a_s[i], b_s[i], l_s[i], j, aj, bj, lj);
+        order[(size_t)kl * n + rank] = (uint8_t)j;
+        FspEntry e;
+        e.w = aj + lj;
+        e.e = aj - bj;
+        e.bit = 1u << (j & 31);
+        e.widx = j >> 5;
+        ent[(size_t)kl * n + rank] = e;
+    }
+}
+
+static void free_instance(fsp_instance *I)
+{
+    if (!I) return;
+    cudaFree(I->d_p);
+    cudaFree(I->d_q);
+    cudaFree(I->d_lag);
+    cudaFree(I->d_order);
+    cudaFree(I->d_ent);
+    cudaFree(I->d_status);
+    free(I);
+}
+
+extern "C" int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance **out)
+{
+    if (!out) { fsp_set_error("fsp_create_instance: out is NULL"); return FSP_ERR_ARG; }
+    *out = nullptr;
+    if (n < 1 || n > FSP_MAX_JOBS || m < 2 || m > FSP_MAX_MACHINES || !p) {
+        fsp_set_error("fsp_create_instance: need 1 <= n <= %d, 2 <= m <= %d and p (n=%d, m=%d)",
+                      FSP_MAX_JOBS, FSP_MAX_MACHINES, n, m);
+        return FSP_ERR_ARG;
+    }
+    for (long i = 0; i < (long)n * m; ++i)
+        if (p[i] < 1 || p[i] > 32767) {
+            fsp_set_error("fsp_create_instance: p[%ld] = %d outside 1..32767", i, p[i]);
+            return FSP_ERR_ARG;
+        }
+    fsp_instance *I = (fsp_instance *)calloc(1, sizeof(fsp_instance));
+    if (!I) { fsp_set_error("fsp_create_instance: out of host memory"); return FSP_ERR_OOM; }
+    I->n = n;
+    I->m = m;
+    I->P = m * (m - 1) / 2;
+    I->stride = fsp_node_stride(n);
+    I->mp = (m % 2 == 0) ? m + 1 : m;
+    int rc = FSP_OK;
+    cudaError_t e;
+#define TRY(call)                                              \
+    do {                                                       \
+        e = (call);                                            \
+        if (e != cudaSuccess) { rc = fsp_cuda_fail(e, #call); goto fail; } \
+    } while (0)
+    TRY(cudaGetDevice(&I->device));
+    TRY(cudaDeviceGetAttribute(&I->sm_count, cudaDevAttrMultiProcessorCount, I->device));
+    TRY(cudaDeviceGetAttribute(&I->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, I->device));
+    TRY(cudaMalloc(&I->d_p, sizeof(int32_t) * n * m));
+    TRY(cudaMalloc(&I->d_q, sizeof(int32_t) * n * m));
+    TRY(cudaMalloc(&I->d_lag, sizeof(int32_t) * (size_t)I->P * n));
+    TRY(cudaMalloc(&I->d_order, (size_t)I->P * n));
+    TRY(cudaMalloc(&I->d_ent, sizeof(FspEntry) * (size_t)I->P * n));
+    TRY(cudaMalloc(&I->d_status, sizeof(int)));
+    TRY(cudaMemcpy(I->d_p, p, sizeof(int32_t) * n * m, cudaMemcpyHostToDevice));
+    TRY(cudaMemset(I->d_status, 0, sizeof(int)));
+    k_tails<<<(n * m + 255) / 256, 256>>>(n, m, I->d_p, I->d_q);
+    TRY(cudaGetLastError());
+    k_pair_tables<<<I->P, 256>>>(n, m, I->d_p, I->d_lag, I->d_order, I->d_ent);
+    TRY(cudaGetLastError());
+    TRY(cudaDeviceSynchronize());
+#undef TRY
+    *out = I;
+    return FSP_OK;
+fail:
+    free_instance(I);
+    return rc;
+}
+
+extern "C" void fsp_destroy_instance(fsp_instance *inst)
+{
+    if (!inst) return;
+    int cur = -1;
+    const int dev = inst->device;
+    cudaGetDevice(&cur);
+    if (cur != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    free_instance(inst);
+    if (cur >= 0 && cur != dev) cudaSetDevice(cur);
+}
+
+extern "C" int fsp_instance_tables(const fsp_instance *I, int32_t *q, int32_t *lag, uint8_t *order)
+{
+    if (!I) { fsp_set_error("fsp_instance_tables: inst is NULL"); return FSP_ERR_ARG; }
+    if (q) FSP_CUDA(cudaMemcpy(q, I->d_q, sizeof(int32_t) * I->n * I->m, cudaMemcpyDeviceToHost));
+    if (lag)
+        FSP_CUDA(cudaMemcpy(lag, I->d_lag, sizeof(int32_t) * (size_t)I->P * I->n, cudaMemcpyDeviceToHost));
+    if (order) FSP_CUDA(cudaMemcpy(order, I->d_order, (size_t)I->P * I->n, cudaMemcpyDeviceToHost));
+    return FSP_OK;
+}

@@ -1,0 +1,509 @@
+// fsp_solve.cu -- the exact branch-and-bound on the device (Sec. II-A
+// operators; Sec. III selection of a pool of the deepest pending nodes).
+//
+// The paper selects, branches and eliminates on the host and off-loads only
+// the bounding (Sec. III).  Here every operator runs on the device and the
+// host only launches one iteration after another:
+//   K-select  one CTA: pops the deepest parents (top of the depth-first
+//             stack) while their children fit in the pool; writes the
+//             child -> (parent, rank) map.
+//   K2+K1     one thread per child: builds the child record (prefix + job,
+//             remaining set kept in increasing job order) and bounds it;
+//             complete schedules race for the incumbent with one 64-bit
+//             atomicMin on (bound, child index), which is the first child
+//             in pool order among the smallest bounds.
+//   K3a       per block: survivors (non-leaf, bound < new UB) and leaves.
+//   K3b       stable compaction: survivors pushed in reverse pool order so
+//             the first survivor is on top; counters, trace, incumbent.
+#include <stdlib.h>
+#include <string.h>
+
+#include "fsp_bound.cuh"
+
+#define SOLVE_B 256        // threads per block of the per-child kernels
+#define SELECT_B 1024      // threads of the selection CTA
+
+struct SolveCtl {
+    long long stack_size;   // records on the stack
+    long long s_pop;        // stack size after this iteration's pops
+    long long n_parents;
+    long long n_children;
+    unsigned long long best_key;  // (bound << 32) | child index of the best leaf
+    int ub;                 // current upper bound
+    int ub_iter;            // upper bound at the start of the iteration
+    int status;             // FSP_ERR_* raised on the device, 0 if none
+    int pad0;
+    long long cnt[6];       // bounded, branched, pruned, leaves, iterations, updates
+};
+
+struct SolveWs {
+    SolveCtl *ctl;
+    uint8_t *stack;
+    long long cap;
+    uint8_t *children;
+    int32_t *lbs;
+    int2 *cmap;
+    int *blk;
+    uint8_t *inc;
+    long long *trace;
+    long long trace_cap;
+    long long max_children;
+    int max_blocks;
+};
+
+struct SolveLayout {
+    long long pool_max, max_children, cap, trace_cap;
+    int max_blocks;
+    size_t off_ctl, off_stack, off_children, off_lbs, off_cmap, off_blk, off_inc, off_trace, bytes;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout *L)
+{
+    long long pool = o->pool_size;
+    if (pool < 1 || pool > (1LL << 26)) {
+        fsp_set_error("pool_size %lld outside 1..2^26", pool);
+        return FSP_ERR_ARG;
+    }
+    long long pmax = pool;
+    if (o->schedule && o->schedule_len > 0)
+        for (long long i = 0; i < o->schedule_len; ++i) {
+            if (o->schedule[i] < 1 || o->schedule[i] > (1LL << 26)) {
+                fsp_set_error("schedule[%lld] = %lld outside 1..2^26", i, o->schedule[i]);
+                return FSP_ERR_ARG;
+            }
+            if (o->schedule[i] > pmax) pmax = o->schedule[i];
+        }
+    L->pool_max = pmax;
+    L->max_children = pmax + I->n;
+    L->max_blocks = (int)((L->max_children + SOLVE_B - 1) / SOLVE_B);
+    L->cap = o->stack_capacity > 0 ? o->stack_capacity : (long long)I->n * (pmax + I->n);
+    L->trace_cap = (o->trace && o->trace_cap > 0) ? o->trace_cap : 0;
+    size_t off = 0;
+    L->off_ctl = off; off = align256(off + sizeof(SolveCtl));
+    L->off_stack = off; off = align256(off + (size_t)L->cap * I->stride);
+    L->off_children = off; off = align256(off + (size_t)L->max_children * I->stride);
+    L->off_lbs = off; off = align256(off + (size_t)L->max_children * 4);
+    L->off_cmap = off; off = align256(off + (size_t)L->max_children * 8);
+    L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 8);
+    L->off_inc = off; off = align256(off + 256);
+    L->off_trace = off; off = align256(off + (size_t)L->trace_cap * 32);
+    L->bytes = off;
+    return FSP_OK;
+}
+
+extern "C" int64_t fsp_solve_workspace_bytes(const fsp_instance *I, const fsp_options *opt)
+{
+    if (!I) { fsp_set_error("fsp_solve_workspace_bytes: inst is NULL"); return FSP_ERR_ARG; }
+    fsp_options d;
+    if (!opt) { fsp_default_options(&d); opt = &d; }
+    SolveLayout L;
+    int rc = solve_layout(I, opt, &L);
+    return rc == FSP_OK ? (int64_t)L.bytes : (int64_t)rc;
+}
+
+// ---------------------------------------------------------------- kernels --
+
+__global__ void k_solve_init(SolveWs ws, int n, int stride, int ub0)
+{
+    const int t = threadIdx.x;
+    for (int i = t; i < stride; i += blockDim.x) ws.stack[i] = (uint8_t)(i < n ? i : 0);
+    if (t == 0) {
+        SolveCtl c;
+        memset(&c, 0, sizeof c);
+        c.stack_size = 1;
+        c.ub = ub0;
+        c.ub_iter = ub0;
+        c.best_key = ~0ull;
+        *ws.ctl = c;
+    }
+}
+
+// n == 1: the only schedule; its makespan is the sum of the job's times.
+__global__ void k_solve_single(SolveWs ws, const int32_t *p, int m, int ub0)
+{
+    if (threadIdx.x != 0) return;
+    int32_t c = 0;
+    for (int k = 0; k < m; ++k) c += p[k];
+    SolveCtl *ctl = ws.ctl;
+    memset(ctl, 0, sizeof(SolveCtl));
+    ctl->ub = ub0;
+    if (c < ub0) {
+        ctl->ub = c;
+        ctl->cnt[5] = 1;
+        ws.inc[0] = 0;
+    }
+}
+
+// Inclusive block scan of one int per thread (blockDim.x a multiple of 32).
+__device__ __forceinline__ int block_incl_scan(int v, int *warp_tot)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_tot[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const int add = wid > 0 ? warp_tot[wid - 1] : 0;
+    __syncthreads();
+    return v + add;
+}
+
+// Selection (Sec. III): deepest pending nodes first, while their children fit.
+__global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stride, long long pool)
+{
+    __shared__ int warp_tot[32];
+    __shared__ int s_last;
+    SolveCtl *ctl = ws.ctl;
+    const long long S = ctl->stack_size;
+    long long running = 0, np = 0;
+    if (S > 0) {
+        for (long long base = 0; base < S; base += SELECT_B) {
+            const long long i = base + threadIdx.x;
+            const int r = i < S ? n - (int)ws.stack[(S - 1 - i) * stride + n] : 0;
+            const int incl = block_incl_scan(r, warp_tot);
+            const bool taken = i < S && (i == 0 || running + incl <= pool);
+            const int cnt = __syncthreads_count(taken);
+            if (taken) {
+                const long long c0 = running + (incl - r);
+                for (int ci = 0; ci < r; ++ci) ws.cmap[c0 + ci] = make_int2((int)i, ci);
+            }
+            if (cnt == 0) break;
+            if (threadIdx.x == cnt - 1) s_last = incl;
+            __syncthreads();
+            running += s_last;
+            np += cnt;
+            __syncthreads();
+            if (cnt < SELECT_B) break;
+        }
+    }
+    if (threadIdx.x == 0) {
+        ctl->best_key = ~0ull;
+        ctl->ub_iter = ctl->ub;
+        if (S - np + running > ws.cap) {  // could overflow: keep the stack intact
+            ctl->status = FSP_ERR_CAPACITY;
+            ctl->n_parents = 0;
+            ctl->n_children = 0;
+            ctl->s_pop = S;
+        } else {
+            ctl->n_parents = np;
+            ctl->n_children = running;
+            ctl->s_pop = S - np;
+        }
+    }
+}
+
+// Branching + bounding, one thread per child.
+template <int NW, int MT, bool ES>
+__global__ void __launch_bounds__(256) k_branch_bound(DevInst I, SolveWs ws, BoundSmem L)
+{
+    const SolveCtl *ctl = ws.ctl;
+    const long long nch = ctl->n_children;
+    const int B = blockDim.x, tid = threadIdx.x;
+    if ((long long)blockIdx.x * B >= nch) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    FspEntry *ent_s = ES ? reinterpret_cast<FspEntry *>(smem + L.ent_off) : nullptr;
+    int32_t *p_s = reinterpret_cast<int32_t *>(smem + L.p_off);
+    int32_t *q_s = reinterpret_cast<int32_t *>(smem + L.q_off);
+    uint32_t *rec = reinterpret_cast<uint32_t *>(smem + L.rec_off) + tid;
+    int32_t *cs = reinterpret_cast<int32_t *>(smem + L.cs_off) + tid;
+    int32_t *sq = reinterpret_cast<int32_t *>(smem + L.sq_off) + tid;
+    int32_t *ss = reinterpret_cast<int32_t *>(smem + L.ss_off) + tid;
+    fsp_stage_tables(I, ent_s, p_s, q_s);
+    const FspEntry *ent = ES ? ent_s : I.ent;
+
+    const long long c = (long long)blockIdx.x * B + tid;
+    if (c >= nch) return;
+    const int n = I.n, stride = I.stride, nvec = stride >> 4;
+    const int2 pc = ws.cmap[c];
+    const long long S = ctl->s_pop + ctl->n_parents;
+    const uint4 *src = reinterpret_cast<const uint4 *>(ws.stack + (S - 1 - pc.x) * stride);
+    for (int v = 0; v < nvec; ++v) {
+        const uint4 x = src[v];
+        rec[(4 * v + 0) * B] = x.x;
+        rec[(4 * v + 1) * B] = x.y;
+        rec[(4 * v + 2) * B] = x.z;
+        rec[(4 * v + 3) * B] = x.w;
+    }
+    // Child of rank ci: prefix, then job par[d+ci], then par[d..n) without it
+    // (the remaining set stays in increasing job order).
+    const int d = (int)fsp_rec_byte(rec, B, n);
+    const int ci = pc.y;
+    const uint32_t x = fsp_rec_byte(rec, B, d + ci);
+    uint32_t prev = 0;
+    for (int w = 0; w < (stride >> 2); ++w) {
+        const uint32_t in = rec[w * B];
+        uint32_t out = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = 4 * w + b;
+            const uint32_t cur = (in >> (8 * b)) & 0xFFu;
+            const uint32_t prv = b > 0 ? (in >> (8 * (b - 1))) & 0xFFu : (prev >> 24) & 0xFFu;
+            uint32_t v;
+            if (i < d) v = cur;
+            else if (i == d) v = x;
+            else if (i <= d + ci) v = prv;
+            else if (i < n) v = cur;
+            else if (i == n) v = (uint32_t)(d + 1);
+            else v = 0u;
+            out |= v << (8 * b);
+        }
+        rec[w * B] = out;
+        prev = in;
+    }
+    bool bad;
+    const int32_t lb = fsp_node_bound<NW, MT, ES>(I, ent, p_s, q_s, rec, cs, sq, ss, B, bad);
+    if (bad) atomicOr(I.status, 2);
+    ws.lbs[c] = lb;
+    uint4 *dst = reinterpret_cast<uint4 *>(ws.children + c * stride);
+    for (int v = 0; v < nvec; ++v)
+        dst[v] = make_uint4(rec[(4 * v) * B], rec[(4 * v + 1) * B], rec[(4 * v + 2) * B],
+                            rec[(4 * v + 3) * B]);
+    if (d + 1 == n - 1 && lb < ctl->ub_iter)
+        atomicMin(&ws.ctl->best_key, ((unsigned long long)(uint32_t)lb << 32) | (unsigned long long)c);
+}
+
+__device__ __forceinline__ int solve_ub_new(const SolveCtl *ctl)
+{
+    const unsigned long long k = ctl->best_key;
+    const int ubi = ctl->ub_iter;
+    if (k == ~0ull) return ubi;
+    const int b = (int)(k >> 32);
+    return b < ubi ? b : ubi;
+}
+
+// Elimination, step 1: survivors and leaves per block.
+__global__ void __launch_bounds__(SOLVE_B) k_count(SolveWs ws, int n, int stride)
+{
+    const SolveCtl *ctl = ws.ctl;
+    const long long nch = ctl->n_children;
+    const int ubn = solve_ub_new(ctl);
+    const long long c = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
+    bool leaf = false, surv = false;
+    if (c < nch) {
+        leaf = ws.children[c * stride + n] == (uint8_t)(n - 1);
+        surv = !leaf && ws.lbs[c] < ubn;
+    }
+    const int cs = __syncthreads_count(surv);
+    const int cl = __syncthreads_count(leaf);
+    if (threadIdx.x == 0) {
+        ws.blk[2 * blockIdx.x] = cs;
+        ws.blk[2 * blockIdx.x + 1] = cl;
+    }
+}
+
+// Elimination, step 2: stable compaction onto the stack (reverse pool order).
+__global__ void __launch_bounds__(SOLVE_B) k_push(SolveWs ws, int n, int stride)
+{
+    __shared__ long long red[3][SOLVE_B / 32];
+    __shared__ int wcnt[SOLVE_B / 32];
+    SolveCtl *ctl = ws.ctl;
+    const long long nch = ctl->n_children;
+    const int ubn = solve_ub_new(ctl);
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    long long before = 0, total = 0, leaves = 0;
+    for (int i = tid; i < (int)gridDim.x; i += SOLVE_B) {
+        const long long s = ws.blk[2 * i];
+        total += s;
+        leaves += ws.blk[2 * i + 1];
+        if (i < b) before += s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        leaves += __shfl_xor_sync(0xffffffffu, leaves, o);
+    }
+    if (lane == 0) { red[0][wid] = before; red[1][wid] = total; red[2][wid] = leaves; }
+    const long long c = (long long)b * SOLVE_B + tid;
+    bool surv = false;
+    if (c < nch) surv = ws.children[c * stride + n] != (uint8_t)(n - 1) && ws.lbs[c] < ubn;
+    const unsigned bal = __ballot_sync(0xffffffffu, surv);
+    if (lane == 0) wcnt[wid] = __popc(bal);
+    __syncthreads();
+    before = total = leaves = 0;
+    int woff = 0;
+    for (int w = 0; w < SOLVE_B / 32; ++w) {
+        before += red[0][w];
+        total += red[1][w];
+        leaves += red[2][w];
+        if (w < wid) woff += wcnt[w];
+    }
+    const long long s_pop = ctl->s_pop;
+    if (surv) {
+        const long long q = before + woff + __popc(bal & ((1u << lane) - 1u));
+        const uint4 *src = reinterpret_cast<const uint4 *>(ws.children + c * stride);
+        uint4 *dst = reinterpret_cast<uint4 *>(ws.stack + (s_pop + total - 1 - q) * stride);
+        for (int v = 0; v < (stride >> 4); ++v) dst[v] = src[v];
+    }
+    if (b == 0) {
+        const int ubi = ctl->ub_iter;
+        const bool improved = ubn < ubi;
+        if (improved) {
+            const long long idx = (long long)(ctl->best_key & 0xffffffffull);
+            for (int i = tid; i < n; i += SOLVE_B) ws.inc[i] = ws.children[idx * stride + i];
+        }
+        if (tid == 0) {
+            const long long it = ctl->cnt[4];
+            ctl->cnt[0] += nch;
+            ctl->cnt[1] += ctl->n_parents;
+            ctl->cnt[2] += nch - leaves - total;
+            ctl->cnt[3] += leaves;
+            ctl->cnt[4] = it + 1;
+            if (improved) ctl->cnt[5] += 1;
+            ctl->ub = ubn;
+            ctl->stack_size = s_pop + total;
+            if (it < ws.trace_cap) {
+                ws.trace[4 * it + 0] = ctl->n_parents;
+                ws.trace[4 * it + 1] = nch;
+                ws.trace[4 * it + 2] = total;
+                ws.trace[4 * it + 3] = ubn;
+            }
+        }
+    }
+}
+
+typedef void (*BranchBoundFn)(DevInst, SolveWs, BoundSmem);
+
+static BranchBoundFn pick_branch_bound(int nw, int mt, bool es)
+{
+#define FSP_CASE(NW_, MT_, ES_) \
+    if (nw == NW_ && mt == MT_ && es == ES_) return &k_branch_bound<NW_, MT_, ES_>;
+    FSP_SHAPES(FSP_CASE)
+#undef FSP_CASE
+    return nullptr;
+}
+
+// ------------------------------------------------------------------ host --
+
+extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
+                         const fsp_options *opt)
+{
+    if (!I || !cmax || !perm) { fsp_set_error("fsp_solve: NULL argument"); return FSP_ERR_ARG; }
+    fsp_options o;
+    if (opt) o = *opt; else fsp_default_options(&o);
+    SolveLayout L;
+    int rc = solve_layout(I, &o, &L);
+    if (rc != FSP_OK) return rc;
+    BoundShape shp;
+    if ((rc = fsp_bound_shape(I, &shp)) != FSP_OK) return rc;
+    BranchBoundFn bb = pick_branch_bound(shp.nw, shp.mt, shp.es);
+    if (!bb) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
+    FSP_CUDA(cudaFuncSetAttribute((const void *)bb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)shp.L.bytes));
+    if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
+        fsp_set_error("fsp_solve: workspace must be 256-byte aligned");
+        return FSP_ERR_ARG;
+    }
+
+    cudaStream_t st = (cudaStream_t)o.stream;
+    uint8_t *base = (uint8_t *)o.workspace;
+    bool owned = false;
+    if (!base) {
+        FSP_CUDA(cudaMalloc(&base, L.bytes));
+        owned = true;
+    }
+    SolveWs ws;
+    ws.ctl = (SolveCtl *)(base + L.off_ctl);
+    ws.stack = base + L.off_stack;
+    ws.cap = L.cap;
+    ws.children = base + L.off_children;
+    ws.lbs = (int32_t *)(base + L.off_lbs);
+    ws.cmap = (int2 *)(base + L.off_cmap);
+    ws.blk = (int *)(base + L.off_blk);
+    ws.inc = base + L.off_inc;
+    ws.trace = (long long *)(base + L.off_trace);
+    ws.trace_cap = L.trace_cap;
+    ws.max_children = L.max_children;
+    ws.max_blocks = L.max_blocks;
+    const DevInst D = dev_view(I);
+
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    SolveCtl h;
+    memset(&h, 0, sizeof h);
+    cudaError_t e = cudaSuccess;
+#define TRY(call)                                                      \
+    do {                                                               \
+        e = (call);                                                    \
+        if (e != cudaSuccess) { rc = fsp_cuda_fail(e, #call); goto out; } \
+    } while (0)
+    TRY(cudaEventCreate(&ev0));
+    TRY(cudaEventCreate(&ev1));
+    TRY(cudaEventRecord(ev0, st));
+    if (I->n == 1) {
+        k_solve_single<<<1, 32, 0, st>>>(ws, I->d_p, I->m, ub0);
+        TRY(cudaGetLastError());
+        TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+    } else {
+        k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
+        TRY(cudaGetLastError());
+        for (long long it = 0;; ++it) {
+            TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            if (h.status != 0) {
+                rc = h.status;
+                fsp_set_error(rc == FSP_ERR_CAPACITY ? "fsp_solve: stack capacity exceeded"
+                                                     : "fsp_solve: device error");
+                break;
+            }
+            if (h.stack_size == 0) break;
+            if (o.node_budget > 0 && h.cnt[0] >= o.node_budget) { rc = FSP_INCOMPLETE; break; }
+            long long pool = o.pool_size;
+            if (o.schedule && o.schedule_len > 0)
+                pool = o.schedule[it < o.schedule_len ? it : o.schedule_len - 1];
+            const int grid = (int)((pool + I->n + SOLVE_B - 1) / SOLVE_B);
+            const int grid_bb = (int)((pool + I->n + shp.B - 1) / shp.B);
+            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool);
+            bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
+            k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
+            k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
+            TRY(cudaGetLastError());
+        }
+    }
+    TRY(cudaEventRecord(ev1, st));
+    TRY(cudaEventSynchronize(ev1));
+    *cmax = h.ub;
+    if (h.cnt[5] > 0) {
+        uint8_t pb[FSP_MAX_JOBS + 1];
+        TRY(cudaMemcpy(pb, ws.inc, I->n, cudaMemcpyDeviceToHost));
+        for (int i = 0; i < I->n; ++i) perm[i] = pb[i];
+    } else if (o.ub0_perm) {
+        for (int i = 0; i < I->n; ++i) perm[i] = o.ub0_perm[i];
+    }
+    if (L.trace_cap > 0) {
+        const long long rows = h.cnt[4] < L.trace_cap ? h.cnt[4] : L.trace_cap;
+        if (rows > 0)
+            TRY(cudaMemcpy(o.trace, ws.trace, (size_t)rows * 32, cudaMemcpyDeviceToHost));
+    }
+    if (stats) {
+        stats->nodes_bounded = h.cnt[0];
+        stats->nodes_branched = h.cnt[1];
+        stats->nodes_pruned = h.cnt[2];
+        stats->leaves = h.cnt[3];
+        stats->iterations = h.cnt[4];
+        stats->incumbent_updates = h.cnt[5];
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        stats->time_ms = ms;
+    }
+#undef TRY
+out:
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (owned) cudaFree(base);
+    return rc;
+}

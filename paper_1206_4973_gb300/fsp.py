@@ -1,0 +1,242 @@
+"""Thin Python binding of the C ABI declared in ``include/fsp.h``.
+
+Argument marshalling only: every step of the bounding and the search runs in
+the CUDA kernels of ``_build/libfsp.so``.  PyTorch supplies device memory
+(tensors' ``data_ptr()``) and streams (``torch.cuda.current_stream()``).  The
+library must have been built (``paper_1206_4973_gb300.build.build()``); there
+is no fallback of any kind when it is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, INCOMPLETE = 0, 1
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_CAPACITY, ERR_TIMEOUT = -1, -2, -3, -4, -5
+UB_INF = 2**31 - 1
+LB_INVALID = -1
+_NAMES = {ERR_ARG: "FSP_ERR_ARG", ERR_CUDA: "FSP_ERR_CUDA", ERR_OOM: "FSP_ERR_OOM",
+          ERR_CAPACITY: "FSP_ERR_CAPACITY", ERR_TIMEOUT: "FSP_ERR_TIMEOUT"}
+
+# Every symbol include/fsp.h declares.
+EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp_destroy_instance",
+           "fsp_instance_tables", "fsp_bound_pool", "fsp_check_status", "fsp_solve_workspace_bytes",
+           "fsp_solve", "fsp_last_error")
+
+
+class FspError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fsp_stats(ctypes.Structure):
+    _fields_ = [("nodes_bounded", ctypes.c_int64), ("nodes_branched", ctypes.c_int64),
+                ("nodes_pruned", ctypes.c_int64), ("leaves", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64),
+                ("time_ms", ctypes.c_double)]
+
+
+class fsp_options(ctypes.Structure):
+    _fields_ = [("pool_size", ctypes.c_int64), ("node_budget", ctypes.c_int64),
+                ("stack_capacity", ctypes.c_int64), ("ub0_perm", ctypes.POINTER(ctypes.c_int32)),
+                ("trace", ctypes.POINTER(ctypes.c_int64)), ("trace_cap", ctypes.c_int64),
+                ("schedule", ctypes.POINTER(ctypes.c_int64)), ("schedule_len", ctypes.c_int64),
+                ("workspace", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libfsp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                           "paper_1206_4973_gb300.build.build() (no fallback exists)")
+    L = ctypes.CDLL(path)
+    vp, i32p, u8p, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint8), ctypes.c_int64
+    sig = {
+        "fsp_default_options": (ctypes.c_int, [ctypes.POINTER(fsp_options)]),
+        "fsp_node_stride": (ctypes.c_int, [ctypes.c_int]),
+        "fsp_create_instance": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, i32p, ctypes.POINTER(vp)]),
+        "fsp_destroy_instance": (None, [vp]),
+        "fsp_instance_tables": (ctypes.c_int, [vp, i32p, i32p, u8p]),
+        "fsp_bound_pool": (ctypes.c_int, [vp, vp, i64, ctypes.c_int32, vp, vp]),
+        "fsp_check_status": (ctypes.c_int, [vp, vp]),
+        "fsp_solve_workspace_bytes": (i64, [vp, ctypes.POINTER(fsp_options)]),
+        "fsp_solve": (ctypes.c_int, [vp, ctypes.c_int32, i32p, i32p, ctypes.POINTER(fsp_stats),
+                                     ctypes.POINTER(fsp_options)]),
+        "fsp_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise FspError(rc, load().fsp_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Instance:
+    """Handle of a device-resident instance (processing times + tables)."""
+
+    def __init__(self, handle, n: int, m: int):
+        self.handle, self.n, self.m = handle, n, m
+        self.stride = fsp_node_stride(n)
+
+    def close(self):
+        if self.handle:
+            fsp_destroy_instance(self)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fsp_node_stride(n: int) -> int:
+    return int(load().fsp_node_stride(int(n)))
+
+
+def fsp_create_instance(p) -> Instance:
+    """p: n x m int32 processing times (job-major), host array-like."""
+    p = np.ascontiguousarray(np.asarray(p), dtype=np.int32)
+    if p.ndim != 2:
+        raise ValueError("p must be n x m")
+    n, m = p.shape
+    h = ctypes.c_void_p()
+    _check(load().fsp_create_instance(n, m, p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      ctypes.byref(h)))
+    return Instance(h, n, m)
+
+
+def fsp_destroy_instance(inst: Instance) -> None:
+    if inst.handle:
+        load().fsp_destroy_instance(inst.handle)
+        inst.handle = None
+
+
+def fsp_instance_tables(inst: Instance):
+    P = inst.m * (inst.m - 1) // 2
+    q = np.zeros((inst.n, inst.m), np.int32)
+    lag = np.zeros((P, inst.n), np.int32)
+    order = np.zeros((P, inst.n), np.uint8)
+    _check(load().fsp_instance_tables(inst.handle, q.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      lag.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                      order.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return q, lag, order
+
+
+def fsp_bound_pool(inst: Instance, nodes, ub: int = UB_INF, lb_out=None, stream=None, count=None):
+    """Bound node records (CUDA uint8 tensor [count, stride]) into lb_out
+    (CUDA int32 tensor [count]; allocated when None).  Asynchronous."""
+    import torch
+    if count is None:
+        count = nodes.shape[0]
+    if lb_out is None:
+        lb_out = torch.empty(count, dtype=torch.int32, device=nodes.device)
+    if nodes.dtype != torch.uint8 or not nodes.is_cuda or not lb_out.is_cuda or lb_out.dtype != torch.int32:
+        raise ValueError("nodes must be a CUDA uint8 tensor and lb_out a CUDA int32 tensor")
+    if not nodes.is_contiguous() or not lb_out.is_contiguous():
+        raise ValueError("nodes and lb_out must be contiguous")
+    if count and (nodes.numel() < count * inst.stride or lb_out.numel() < count):
+        raise ValueError("buffers smaller than count records")
+    _check(load().fsp_bound_pool(inst.handle, nodes.data_ptr(), int(count), int(ub), lb_out.data_ptr(),
+                                 _stream(stream)))
+    return lb_out
+
+
+def fsp_check_status(inst: Instance, stream=None) -> None:
+    _check(load().fsp_check_status(inst.handle, _stream(stream)))
+
+
+def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
+             schedule=None, stream=None):
+    o = fsp_options()
+    load().fsp_default_options(ctypes.byref(o))
+    o.pool_size = int(pool_size)
+    o.node_budget = int(node_budget)
+    o.stack_capacity = int(stack_capacity)
+    keep = []
+    if ub0_perm is not None:
+        a = np.ascontiguousarray(ub0_perm, dtype=np.int32)
+        keep.append(a)
+        o.ub0_perm = a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    trace = None
+    if trace_cap > 0:
+        trace = np.zeros((trace_cap, 4), np.int64)
+        keep.append(trace)
+        o.trace = trace.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        o.trace_cap = trace_cap
+    if schedule is not None:
+        s = np.ascontiguousarray(schedule, dtype=np.int64)
+        keep.append(s)
+        o.schedule = s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        o.schedule_len = len(s)
+    o.stream = _stream(stream)
+    return o, keep, trace
+
+
+def fsp_solve_workspace_bytes(inst: Instance, **kw) -> int:
+    o, _keep, _ = _options(**kw)
+    return _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
+
+
+STATS = ("nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iterations", "incumbent_updates")
+
+
+def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,
+              stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
+              workspace=None):
+    """Exact B&B on the device.  The scratch is a torch uint8 tensor (allocated
+    here when `workspace` is None).  Returns a dict: status, cmax, perm (None
+    if the search found nothing better than ub0 and no ub0_perm was given),
+    the counters of STATS, time_ms and, if trace_cap > 0, the trace rows."""
+    import torch
+    o, keep, trace = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap, schedule, stream)
+    nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
+    if workspace is None:
+        workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    elif workspace.numel() < nbytes:
+        raise ValueError(f"workspace needs {nbytes} bytes")
+    o.workspace = workspace.data_ptr()
+    perm = np.full(inst.n, -1, np.int32)
+    cmax = ctypes.c_int32(0)
+    st = fsp_stats()
+    rc = _check(load().fsp_solve(inst.handle, int(ub0), ctypes.byref(cmax),
+                                 perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(st),
+                                 ctypes.byref(o)))
+    res = {k: int(getattr(st, k)) for k in STATS}
+    res["time_ms"] = float(st.time_ms)
+    res["status"] = rc
+    res["cmax"] = int(cmax.value)
+    res["perm"] = perm if perm[0] >= 0 else None
+    if trace is not None:
+        res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
+    del keep
+    return res

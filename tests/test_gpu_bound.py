@@ -1,0 +1,128 @@
+"""GPU parity of the instance tables (K0) and the bounding kernel (K1) with the
+CPU oracle: bit-exact int32 bounds, every kernel shape, ragged pools spanning
+several CTAs, the edge depths 0, n-1 and n, malformed records, and the
+full-size 20 x 20 bounding workload (sampled)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_4973_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+# (n, m, seed): shapes cover mask words 1/2/4/8, machine templates 5/10/20,
+# the any-m path, and Johnson entries in global memory (m = 64).
+SHAPES = [(20, 20, 1), (12, 5, 0), (15, 10, 3), (7, 3, 4), (33, 5, 5), (50, 10, 6), (50, 20, 7),
+          (100, 5, 8), (130, 5, 9), (20, 7, 10), (255, 3, 11), (2, 2, 12), (24, 64, 13), (100, 20, 14)]
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    from paper_1206_4973_gb300 import build, fsp
+    build.build()
+    fsp.load()
+    assert torch.cuda.is_available()
+    return fsp
+
+
+def edge_pool(n, count, seed):
+    rng = inputs.SplitMix64(seed)
+    rec = inputs.random_prefix_pool(n, count, rng) if n >= 2 else np.zeros((count, 16), np.uint8)
+    rec[::7, n] = 0
+    rec[3::11, n] = n
+    rec[5::13, n] = max(n - 1, 0)
+    return rec
+
+
+@pytest.mark.parametrize("n,m,seed", SHAPES)
+def test_tables_match_oracle(F, n, m, seed):
+    p = inputs.instance(n, m, seed)
+    inst = F.fsp_create_instance(p)
+    q, lag, order = F.fsp_instance_tables(inst)
+    q0, lag0, order0 = oracle.tables(p)
+    assert np.array_equal(q, q0)
+    assert np.array_equal(lag, lag0)
+    assert np.array_equal(order, order0)
+
+
+@pytest.mark.parametrize("n,m,seed", SHAPES)
+def test_bound_pool_matches_oracle(F, n, m, seed):
+    import torch
+    p = inputs.instance(n, m, seed)
+    count = 3001 if n * m <= 2000 else 777
+    rec = edge_pool(n, count, seed + 500)
+    want = oracle.bound_pool(p, rec)
+    inst = F.fsp_create_instance(p)
+    nodes = torch.from_numpy(rec).cuda()
+    got = F.fsp_bound_pool(inst, nodes).cpu().numpy()
+    F.fsp_check_status(inst)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
+
+
+def test_bound_pool_small_counts_and_offsets(F):
+    import torch
+    n, m = 20, 20
+    p, _, rec = inputs.pool_workload(n, m, 1, 300)
+    want = oracle.bound_pool(p, rec)
+    inst = F.fsp_create_instance(p)
+    nodes = torch.from_numpy(rec).cuda()
+    for count in (0, 1, 31, 255, 256, 257):
+        out = torch.full((300,), -7, dtype=torch.int32, device="cuda")
+        F.fsp_bound_pool(inst, nodes, lb_out=out, count=count)
+        got = out.cpu().numpy()
+        assert np.array_equal(got[:count], want[:count])
+        assert np.all(got[count:] == -7)  # nothing written past count
+    # a pool that starts in the middle of a buffer (16-byte aligned records)
+    sub = nodes[77:]
+    got = F.fsp_bound_pool(inst, sub).cpu().numpy()
+    assert np.array_equal(got, want[77:])
+
+
+def test_malformed_records_are_flagged(F):
+    import torch
+    n, m = 12, 5
+    p, _, rec = inputs.pool_workload(n, m, 3, 64)
+    rec = rec.copy()
+    rec[3, 0] = rec[3, 1]      # repeated job
+    rec[9, n] = n + 1          # depth > n
+    rec[20, 2] = n             # job id out of range
+    inst = F.fsp_create_instance(p)
+    got = F.fsp_bound_pool(inst, torch.from_numpy(rec).cuda()).cpu().numpy()
+    assert got[3] == F.LB_INVALID and got[9] == F.LB_INVALID and got[20] == F.LB_INVALID
+    good = np.ones(64, bool)
+    good[[3, 9, 20]] = False
+    assert np.array_equal(got[good], oracle.bound_pool(p, rec[good]))
+    with pytest.raises(F.FspError) as e:
+        F.fsp_check_status(inst)
+    assert e.value.code == F.ERR_ARG
+    F.fsp_check_status(inst)  # the flag was cleared
+
+
+def test_bound_pool_argument_errors(F):
+    import torch
+    inst = F.fsp_create_instance(inputs.instance(8, 3, 1))
+    with pytest.raises(F.FspError):  # negative count
+        F._check(F.load().fsp_bound_pool(inst.handle, None, -1, 0, None, None))
+    buf = torch.zeros((4, 16), dtype=torch.uint8, device="cuda")
+    with pytest.raises(F.FspError):  # misaligned records
+        F._check(F.load().fsp_bound_pool(inst.handle, buf.data_ptr() + 1, 2, 0,
+                                         torch.zeros(4, dtype=torch.int32, device="cuda").data_ptr(), 0))
+
+
+@pytest.mark.parametrize("count", [2**12, 2**20])
+def test_full_size_20x20_workload_sampled(F, count):
+    """The 20 x 20 bounding workload as the benchmark runs it (seed 1): the
+    whole pool bounded in one launch, a spread sample checked node by node."""
+    import torch
+    n, m = 20, 20
+    p, ub_perm, rec = inputs.pool_workload(n, m, 1, count)
+    inst = F.fsp_create_instance(p)
+    got = F.fsp_bound_pool(inst, torch.from_numpy(rec).cuda()).cpu().numpy()
+    F.fsp_check_status(inst)
+    idx = np.unique(np.concatenate([np.arange(min(count, 512)), np.arange(count - 512, count),
+                                    np.linspace(0, count - 1, 4096).astype(np.int64)]))
+    want = oracle.bound_pool(p, rec[idx])
+    assert np.array_equal(got[idx], want)
+    # properties at any size: bounds are positive and never below the prefix makespan
+    assert got.min() >= 1
