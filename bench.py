@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the flow-shop B&B hot path: subproblems bounded per second
+on the 20 jobs x 20 machines workload.
+
+Step = one branch-and-bound iteration on the device (selection of the deepest
+parents, branching, bounding, elimination against the UB and compaction onto
+the stack) whose pool holds 2^18 children, started from a frontier of 20 x 20
+nodes: the bounding workload of seed 1 (p uniform [1,99]; prefixes of random
+permutations, depth uniform [1,19]; depth-19 nodes are complete-but-one and
+never wait on a stack, so the frontier keeps depths <= 18), UB = makespan of
+a random permutation.  Every step restarts from the same frontier, so every
+step does identical work.  Extra lines of the same JSON object report the
+bounding kernel alone on the 2^12..2^20 pools, the roofline, the CPU oracle
+on a bounded sample, and the end-to-end call with host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_JOBS, N_MACH, SEED = 20, 20, 1
+POOL = 2**18
+FRONTIER = 2**18
+BOUND_POOLS = (2**12, 2**15, 2**18, 2**20)
+METRIC = "subproblems bounded/s at 20x20 (plain vs learned pair order, bit-exact); solve time"
+UNIT = "subproblems/s"
+L2_FLUSH_BYTES = 512 << 20
+SMS, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# DRAM bytes (read + write) of one branch-and-bound launch of the step, from the ncu capture in
+# profiles/k_bound_pool2_20x20_2e18_full.md; None once that kernel has changed since the capture.
+BB_TRAFFIC_BYTES = 1146624
+
+
+def work_ops(depth, n=N_JOBS, m=N_MACH):
+    """Algorithmic integer ops to bound one node of depth d (r = n - d):
+    prefix release times 2md, remaining sums/min tails 3mr, one-machine bounds
+    3m, two-machine Johnson recurrences 4Pr, max over pairs 2P."""
+    P = m * (m - 1) // 2
+    d = np.asarray(depth, np.int64)
+    r = n - d
+    return 2 * m * d + 3 * m * r + 3 * m + 4 * P * r + 2 * P
+
+
+def workload(count=FRONTIER):
+    from paper_1206_4973_gb300 import inputs
+    p, ub_perm, rec = inputs.pool_workload(N_JOBS, N_MACH, SEED, count)
+    frontier = rec[rec[:, N_JOBS] <= N_JOBS - 2]
+    return p, ub_perm, rec, frontier
+
+
+def children_depths(frontier, pool):
+    """Depths of the children one iteration bounds (the selection rule: top
+    parents while their children fit in the pool, at least one)."""
+    n = N_JOBS
+    depths, total = [], 0
+    for rec in frontier[::-1]:
+        r = n - int(rec[n])
+        if depths and total + r > pool:
+            break
+        depths.append((int(rec[n]) + 1, r))
+        total += r
+    return np.repeat([d for d, _ in depths], [r for _, r in depths]), total
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.rows, self.proc = index, [], None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({nm for r in self.rows if len(r) >= 8 for nm, v in zip(names, r[4:8])
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(self.rows[0][1]),
+                "reasons": reasons, "samples": len(sm),
+                "power_w_max": max(float(r[2]) for r in self.rows if len(r) >= 8 and r[2][:1].isdigit())}
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed as the reference arm (host cores, one thread)."""
+    if rank != 0:
+        return
+    import oracle
+    p, ub_perm, _, frontier = workload()
+    ub = oracle.makespan(p, ub_perm)
+    sample_pool = 2**15
+    for _ in range(args.warmup):
+        oracle.solve(p, ub0=ub, pool=sample_pool, init_nodes=frontier, max_iterations=1)
+    bounded, t0 = 0, time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.solve(p, ub0=ub, pool=sample_pool, init_nodes=frontier, max_iterations=1)
+        bounded += r["bounded"]
+    dt = time.perf_counter() - t0
+    value = bounded / dt
+    sample = (f"one B&B iteration with a pool of {sample_pool} children from the 20x20 seed-1 frontier, "
+              f"x{args.steps} steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "20x20 B&B iteration from the seed-1 frontier (CPU oracle sample)",
+                   "n": N_JOBS, "m": N_MACH, "seed": SEED, "pool": sample_pool},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(p, ub, frontier, budget_s=12.0):
+    import oracle
+    bounded, steps, t0 = 0, 0, time.perf_counter()
+    pool = 2**16
+    while steps < 8 and (time.perf_counter() - t0) < budget_s:
+        r = oracle.solve(p, ub0=ub, pool=pool, init_nodes=frontier, max_iterations=1)
+        bounded += r["bounded"]
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": bounded / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} B&B iterations of {pool} children from the same 20x20 frontier "
+                      f"({dt:.1f} s, serial C oracle, one host core)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one B&B step and one 2^18-node bounding launch, nothing else (for ncu)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1206_4973_gb300 import build as fsp_build
+    from paper_1206_4973_gb300 import fsp
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    fsp_build.build()
+    fsp.load()
+    dev = torch.device("cuda", local)
+
+    # Rank r runs the same workload on its own GPU (independent replicas).
+    p, ub_perm, pool_nodes, frontier = workload()
+    inst = fsp.fsp_create_instance(p)
+    st = torch.cuda.current_stream()
+    full = np.zeros((1, inst.stride), np.uint8)
+    full[0, :N_JOBS] = ub_perm
+    full[0, N_JOBS] = N_JOBS
+    ub = int(fsp.fsp_bound_pool(inst, torch.from_numpy(full).to(dev)).item())  # depth n: its makespan
+    front_dev = torch.from_numpy(frontier).to(dev)
+    front_host = torch.from_numpy(frontier).pin_memory()
+    ws = torch.empty(fsp.fsp_solve_workspace_bytes(inst, pool_size=POOL, init_nodes=front_dev),
+                     dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    depths, n_children = children_depths(frontier, POOL)
+    ops_per_step = int(work_ops(depths).sum())
+
+    def step(init):
+        return fsp.fsp_solve(inst, ub0=ub, pool_size=POOL, init_nodes=init, max_iterations=1,
+                             workspace=ws, profile=True)
+
+    if args.profile_case:
+        r = step(front_dev)
+        nodes = torch.from_numpy(pool_nodes[:POOL]).to(dev)
+        fsp.fsp_bound_pool(inst, nodes, ub)
+        fsp.fsp_check_status(inst)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": True, "bounded": r["nodes_bounded"]}))
+        return
+
+    for _ in range(args.warmup):
+        r = step(front_dev)
+    assert r["nodes_bounded"] == n_children, (r["nodes_bounded"], n_children)
+
+    # ---- timed region: K steps, L2 flushed before each, CUDA events per step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bound_ms, launches, bounded = [], 0, 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_soak = time.perf_counter()  # identical steps, so the sampler sees the load for ~2 s
+        while time.perf_counter() - t_soak < 2.0:
+            step(front_dev)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            ev[i][0].record(st)
+            r = step(front_dev)
+            ev[i][1].record(st)
+            bound_ms.append(r["bound_ms"])
+            bounded += r["nodes_bounded"]
+            launches += 1 + 4 * r["iterations"]
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = bounded * world / t_total
+
+    # ---- end to end through the C ABI with host buffers (frontier H2D inside the call)
+    e2e_ms = []
+    for i in range(max(3, args.steps // 2)):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = step(front_host)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e = {"value": r["nodes_bounded"] * len(e2e_ms) / (sum(e2e_ms) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(frontier.nbytes),
+           "d2h_bytes_per_step": int(4 + 4 * N_JOBS + fsp.ctypes.sizeof(fsp.fsp_stats))}
+
+    # ---- the bounding kernel alone on the 2^12..2^20 pools (dominant kernel)
+    peak_ops = SMS * INT_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    bp = {}
+    big = pool_nodes if len(pool_nodes) >= max(BOUND_POOLS) else workload(max(BOUND_POOLS))[2]
+    for cnt in BOUND_POOLS:
+        nodes = torch.from_numpy(big[:cnt]).to(dev)
+        out = torch.empty(cnt, dtype=torch.int32, device=dev)
+        for _ in range(3):
+            fsp.fsp_bound_pool(inst, nodes, ub, out)
+        ts = []
+        for i in range(max(5, args.steps // 2)):
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            fsp.fsp_bound_pool(inst, nodes, ub, out)
+            b.record(st)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        ms = statistics.median(ts)
+        ops = int(work_ops(big[:cnt, N_JOBS]).sum())
+        bp[str(cnt)] = {"nodes_per_s": cnt / (ms / 1e3), "ms": ms, "int_ops_per_s": ops / (ms / 1e3),
+                        "frac_of_int_peak": ops / (ms / 1e3) / peak_ops}
+        fsp.fsp_check_status(inst)
+
+    achieved = ops_per_step / (statistics.mean(bound_ms) / 1e3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                "frac": achieved / peak_ops, "traffic": BB_TRAFFIC_BYTES,
+                "kernel": "k_branch_bound (branching + bounding of the pool's children)",
+                "ops_per_launch": ops_per_step, "children_per_launch": n_children,
+                "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz (issue ceiling)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "20x20 B&B iteration, pool 2^18 children, from the seed-1 frontier",
+                       "n": N_JOBS, "m": N_MACH, "seed": SEED, "pool": POOL,
+                       "frontier_nodes": int(len(frontier)), "ub": ub, "children_per_step": n_children,
+                       "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, outside the step events)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "bound_pool": bp,
+            "phase_ms": {"select": r["select_ms"], "branch_bound": r["bound_ms"], "compact": r["compact_ms"]},
+            "wall_s": t_wall,
+        }
+        if world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(p, ub, frontier)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -73,6 +73,9 @@ typedef struct {
     int64_t iterations;        /* pool iterations                          */
     int64_t incumbent_updates; /* strict improvements of the UB            */
     double time_ms;            /* wall time of the search on the stream    */
+    double select_ms;          /* device time in selection (opt->profile)  */
+    double bound_ms;           /* device time in branching + bounding      */
+    double compact_ms;         /* device time in elimination + compaction  */
 } fsp_stats;
 
 /* Options of fsp_solve; fsp_default_options() fills the defaults. */
@@ -80,7 +83,7 @@ typedef struct {
     int64_t pool_size;      /* children bounded per iteration (Sec. III pool); default 1024 */
     int64_t node_budget;    /* stop (FSP_INCOMPLETE) before an iteration once this many
                                nodes are bounded; 0 = no limit */
-    int64_t stack_capacity; /* node records in the device stack; 0 = n * (pool + n) */
+    int64_t stack_capacity; /* node records in the device stack; 0 = init_count + n * (pool + n) */
     const int32_t *ub0_perm;/* host, n entries or NULL: a schedule whose makespan is ub0 */
     int64_t *trace;         /* host or NULL: per iteration {parents, children, survivors,
                                UB after}, int64 x 4 */
@@ -92,6 +95,17 @@ typedef struct {
                                fsp_solve_workspace_bytes() bytes, 256-byte aligned;
                                NULL = the library allocates and frees its own */
     void *stream;           /* cudaStream_t; NULL = legacy default stream */
+    const uint8_t *init_nodes; /* host or device or NULL: start from these node records
+                               (bottom of the stack first) instead of the root; each
+                               must have depth <= n-2; the remaining part of each
+                               record is re-sorted by job index on the device */
+    int64_t init_count;
+    int64_t max_iterations; /* stop (FSP_INCOMPLETE) after this many iterations; 0 = no limit */
+    uint8_t *out_nodes;     /* host or device or NULL: receives the stack left when the
+                               search stops (bottom first), if it holds <= out_cap records */
+    int64_t out_cap;
+    int64_t *out_count;     /* host or NULL: records left on the stack */
+    int profile;            /* nonzero: fill the *_ms phase times of fsp_stats */
 } fsp_options;
 
 /* Fill *opt with the defaults (pool 1024, no budget, default capacity). */
@@ -142,10 +156,14 @@ int64_t fsp_solve_workspace_bytes(const fsp_instance *inst, const fsp_options *o
  * increasing job index of the appended job); complete schedules (depth n-1)
  * lower the UB, first in that order winning ties; keep the other children
  * whose bound is below the UB; push the survivors so the first is on top.
+ * A search resumes from a checkpoint by passing the stack it left
+ * (out_nodes) as init_nodes together with its cmax as ub0 and its permutation
+ * as ub0_perm.
  * Outputs: *cmax = final UB (the optimum when the search completes); perm:
  * host, n int32, receives the optimal permutation if the search improved on
  * ub0 (else opt->ub0_perm if given, else left untouched); stats (may be NULL).
- * Returns FSP_OK, FSP_INCOMPLETE (budget reached; cmax is the best so far),
+ * Returns FSP_OK, FSP_INCOMPLETE (node or iteration budget reached; cmax is
+ * the best so far),
  * FSP_ERR_CAPACITY (stack full; nothing was lost), FSP_ERR_ARG, FSP_ERR_OOM
  * or FSP_ERR_CUDA.  Synchronous. */
 int fsp_solve(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,

@@ -67,7 +67,8 @@ def _load():
                 "orc_bruteforce": (c_i32, [c_int, c_int, i32p, u8p]),
                 "orc_neh": (c_i32, [c_int, c_int, i32p, u8p]),
                 "orc_solve": (c_int, [c_int, c_int, i32p, c_i32, c_i64, c_i64, i64p, c_i64,
-                                      i32p, u8p, i64p, i64p, c_i64]),
+                                      u8p, c_i64, c_int, c_i64,
+                                      i32p, u8p, i64p, i64p, c_i64, u8p, c_i64, i64p]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -176,12 +177,15 @@ def neh(p):
 
 
 def solve(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, schedule=None,
-          trace_cap: int = 0, ub0_perm=None):
+          trace_cap: int = 0, ub0_perm=None, init_nodes=None, max_iterations: int = 0,
+          export_stack: bool = False):
     """Serial pool-synchronous depth-first B&B (Sec. II-A operators, Sec. III pool).
 
     Returns a dict with status, cmax, perm (None if no schedule beat ub0 and no
     ub0_perm was given), the counters of STATS and, if trace_cap > 0, the
     per-iteration trace rows (parents, children, survivors, UB after).
+    init_nodes (uint8 [count, stride] records) replaces the root as the starting
+    stack; export_stack returns the stack left at the end under "stack".
     """
     p, n, m = _inst(p)
     perm = np.zeros(n, np.uint8)
@@ -189,13 +193,32 @@ def solve(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, schedule=No
     cmax = ctypes.c_int32(0)
     sched = None if schedule is None else np.ascontiguousarray(schedule, dtype=np.int64)
     trace = np.zeros((max(trace_cap, 1), 4), np.int64)
-    rc = _load().orc_solve(n, m, _p(p, ctypes.c_int32), int(ub0), int(pool), int(node_budget),
-                           None if sched is None else _p(sched, ctypes.c_int64),
-                           0 if sched is None else len(sched), ctypes.byref(cmax),
-                           _p(perm, ctypes.c_uint8), _p(stats, ctypes.c_int64),
-                           _p(trace, ctypes.c_int64) if trace_cap > 0 else None, int(trace_cap))
+    stride = (n + 1 + 15) // 16 * 16
+    init = None
+    if init_nodes is not None:
+        init = np.ascontiguousarray(init_nodes, dtype=np.uint8)
+        stride = init.shape[1]
+    out_count = ctypes.c_int64(0)
+    args = [n, m, _p(p, ctypes.c_int32), int(ub0), int(pool), int(node_budget),
+            None if sched is None else _p(sched, ctypes.c_int64), 0 if sched is None else len(sched),
+            None if init is None else _p(init, ctypes.c_uint8), 0 if init is None else len(init),
+            stride, int(max_iterations), ctypes.byref(cmax), _p(perm, ctypes.c_uint8),
+            _p(stats, ctypes.c_int64), _p(trace, ctypes.c_int64) if trace_cap > 0 else None,
+            int(trace_cap), None, 0, ctypes.byref(out_count)]
+    rc = _load().orc_solve(*args)
+    if rc == ERR_ARG:
+        raise ValueError("orc_solve: invalid arguments or init node")
     if rc < 0:
         raise RuntimeError(f"orc_solve failed ({rc})")
+    stack = None
+    if export_stack:  # second run with a buffer of the right size (the search is deterministic)
+        stack = np.zeros((int(out_count.value), stride), np.uint8)
+        stats2 = np.zeros(len(STATS), np.int64)
+        args[13] = _p(np.zeros(n, np.uint8), ctypes.c_uint8)
+        args[14] = _p(stats2, ctypes.c_int64)
+        args[15], args[16] = None, 0
+        args[17], args[18] = _p(stack, ctypes.c_uint8), len(stack)
+        _load().orc_solve(*args)
     res = {k: int(v) for k, v in zip(STATS, stats)}
     res["status"] = int(rc)
     res["cmax"] = int(cmax.value)
@@ -205,4 +228,7 @@ def solve(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, schedule=No
         res["perm"] = None if ub0_perm is None else np.asarray(ub0_perm, np.uint8)
     if trace_cap > 0:
         res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
+    res["stack_left"] = int(out_count.value)
+    if export_stack:
+        res["stack"] = stack
     return res

@@ -423,15 +423,28 @@ static int stack_push(orc_stack *s, const uint8_t *perm, int d)
  * schedule (may be NULL): pool size of each iteration (the last entry repeats),
  * to replay a tuned run.  trace (may be NULL): per iteration
  * {parents, children, survivors, UB after}, up to trace_cap iterations.
- * node_budget > 0 stops before an iteration once that many nodes are bounded
- * (returns ORC_INCOMPLETE).
+ * node_budget > 0 stops before an iteration once that many nodes are bounded,
+ * max_iterations > 0 once that many iterations ran (both return
+ * ORC_INCOMPLETE).  init (may be NULL): init_count records of rec_stride bytes
+ * (perm, depth at byte n; depth <= n-2) form the starting stack, bottom
+ * first, instead of the root.  out (may be NULL): receives the stack left at
+ * the end (bottom first, rec_stride bytes per record) if it holds at most
+ * out_cap records; *out_count (may be NULL) its size.
  */
 int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t node_budget,
               const int64_t *schedule, int64_t schedule_len,
+              const uint8_t *init, int64_t init_count, int rec_stride, int64_t max_iterations,
               int32_t *cmax, uint8_t *perm_out, int64_t *stats,
-              int64_t *trace, int64_t trace_cap)
+              int64_t *trace, int64_t trace_cap,
+              uint8_t *out, int64_t out_cap, int64_t *out_count)
 {
     if (!shape_ok(n, m, p) || pool < 1) return ORC_ERR_ARG;
+    if ((init || out) && rec_stride < n + 1) return ORC_ERR_ARG;
+    if (init)
+        for (int64_t i = 0; i < init_count; i++) {
+            const uint8_t *r = init + (size_t)i * rec_stride;
+            if (n < 2 || !orc_check_node(n, r, r[n]) || r[n] > n - 2) return ORC_ERR_ARG;
+        }
     for (int i = 0; i < ST_N; i++) stats[i] = 0;
     int32_t UB = ub0;
 
@@ -452,13 +465,21 @@ int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t
     int64_t par_cap = 0, ch_cap = 0;
     int rc = ORC_OK;
 
-    uint8_t root[ORC_MAXN];
-    for (int i = 0; i < n; i++) root[i] = (uint8_t)i;
-    if ((rc = stack_push(&st, root, 0)) != ORC_OK) goto done;
+    if (init) {
+        for (int64_t i = 0; i < init_count; i++) {
+            const uint8_t *r = init + (size_t)i * rec_stride;
+            if ((rc = stack_push(&st, r, r[n])) != ORC_OK) goto done;
+        }
+    } else {
+        uint8_t root[ORC_MAXN];
+        for (int i = 0; i < n; i++) root[i] = (uint8_t)i;
+        if ((rc = stack_push(&st, root, 0)) != ORC_OK) goto done;
+    }
 
     int64_t it = 0;
     while (st.size > 0) {
         if (node_budget > 0 && stats[ST_BOUNDED] >= node_budget) { rc = ORC_INCOMPLETE; break; }
+        if (max_iterations > 0 && it >= max_iterations) { rc = ORC_INCOMPLETE; break; }
         int64_t psz = pool;
         if (schedule && schedule_len > 0) psz = schedule[it < schedule_len ? it : schedule_len - 1];
         if (psz < 1) psz = 1;
@@ -560,6 +581,13 @@ int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t
         stats[ST_ITERATIONS] = it;
     }
     *cmax = UB;
+    if (out_count) *out_count = st.size;
+    if (out && st.size <= out_cap)
+        for (int64_t i = 0; i < st.size; i++) {
+            uint8_t *dst = out + (size_t)i * rec_stride;
+            memset(dst, 0, (size_t)rec_stride);
+            memcpy(dst, st.rec + (size_t)i * w, (size_t)w);
+        }
 
 done:
     free(st.rec);

@@ -6,6 +6,8 @@
 // and the P x n Johnson entries) into shared memory once, so every table read
 // of the pair loop is a broadcast (all lanes read the same entry).  The grid
 // is persistent (SMs x resident CTAs) and strides over the pool.
+#include <stdlib.h>
+
 #include "fsp_bound.cuh"
 
 template <int NW, int MT, bool ES>
@@ -47,6 +49,72 @@ __global__ void __launch_bounds__(256) k_bound_pool(DevInst I, const uint8_t *__
     }
 }
 
+// Fast path: NPT nodes per thread, registers, DPX add-max (fsp_bound2.cuh).
+template <int MT, int NV, int NW>
+__global__ void __launch_bounds__(FSP_B2) k_bound_pool2(DevInst I, const uint8_t *__restrict__ nodes,
+                                                        long long count, int32_t *__restrict__ lb_out,
+                                                        Bound2Smem L)
+{
+    constexpr int NPT = FSP_NPT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    FspEntry *ent_s = reinterpret_cast<FspEntry *>(smem + L.ent_off);
+    int2 *pq_s = reinterpret_cast<int2 *>(smem + L.pq_off);
+    int32_t *cs = reinterpret_cast<int32_t *>(smem + L.cs_off);
+    int32_t *sq = reinterpret_cast<int32_t *>(smem + L.sq_off);
+    fsp_stage_pq(I, ent_s, pq_s);
+    const int B = blockDim.x, tid = threadIdx.x, SB = B * NPT;
+    int slot[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) slot[j] = tid + j * B;
+    for (long long base = (long long)blockIdx.x * SB; base < count; base += (long long)gridDim.x * SB) {
+        uint32_t Um[NPT][NW];
+        int32_t lb[NPT];
+        bool bad[NPT];
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const long long node = base + slot[j];
+            FspRec<NV> r;
+            if (node < count) {
+                fsp_load_rec(r, nodes + node * I.stride);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4 * NV; ++q) r.w[q] = 0u;
+            }
+            int32_t C[MT], SQ[MT];
+            fsp_prologue<MT, NV, NW>(r, I.n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad[j]);
+#pragma unroll
+            for (int k = 0; k < MT; ++k) {
+                cs[k * SB + slot[j]] = C[k];
+                sq[k * SB + slot[j]] = SQ[k];
+            }
+        }
+        fsp_pair_scan<MT, NPT, NW>(I.n, ent_s, cs, sq, SB, slot, Um, lb);
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const long long node = base + slot[j];
+            if (node < count) {
+                int32_t v = lb[j];
+                if (bad[j]) {
+                    v = FSP_LB_INVALID;
+                    atomicOr(I.status, 1);
+                }
+                lb_out[node] = v;
+            }
+        }
+    }
+}
+
+typedef void (*BoundPool2Fn)(DevInst, const uint8_t *, long long, int32_t *, Bound2Smem);
+
+static BoundPool2Fn pick_bound_pool2(int mt, int nv, int nw)
+{
+#define FSP_CASE2(MT_, NV_, NW_) \
+    if (mt == MT_ && nv == NV_ && nw == NW_) return &k_bound_pool2<MT_, NV_, NW_>;
+    FSP_SHAPES2(FSP_CASE2)
+#undef FSP_CASE2
+    return nullptr;
+}
+
 typedef void (*BoundPoolFn)(DevInst, const uint8_t *, long long, int32_t *, BoundSmem);
 
 static BoundPoolFn pick_bound_pool(int nw, int mt, bool es)
@@ -61,6 +129,15 @@ static BoundPoolFn pick_bound_pool(int nw, int mt, bool es)
 int fsp_bound_shape(const fsp_instance *I, BoundShape *s)
 {
     int nw = fsp_nw(I->n), mt = fsp_mt(I->m);
+    s->nv = I->stride / 16;
+    if (mt != 0 && nw <= 2 && s->nv <= 4 && !getenv("FSP_BOUND_V1")) {
+        Bound2Smem L2 = bound2_smem_layout(I, FSP_B2, FSP_NPT, mt);
+        if ((int)L2.bytes <= I->smem_optin) {
+            s->ver = 2; s->nw = nw; s->mt = mt; s->es = false; s->B = FSP_B2; s->L2 = L2;
+            return FSP_OK;
+        }
+    }
+    s->ver = 1;
     if (nw == 8) mt = 0;
     const int blocks[4] = {256, 128, 64, 32};
     for (int t = 0; t < 4; ++t) {
@@ -95,6 +172,23 @@ extern "C" int fsp_bound_pool(fsp_instance *I, const uint8_t *nodes, int64_t cou
     BoundShape s;
     int rc = fsp_bound_shape(I, &s);
     if (rc != FSP_OK) return rc;
+    if (s.ver == 2) {
+        BoundPool2Fn fn2 = pick_bound_pool2(s.mt, s.nv, s.nw);
+        if (!fn2) { fsp_set_error("fsp_bound_pool: no kernel for this shape"); return FSP_ERR_ARG; }
+        FSP_CUDA(cudaFuncSetAttribute((const void *)fn2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)s.L2.bytes));
+        int per_sm = 0;
+        FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn2, s.B, s.L2.bytes));
+        if (per_sm < 1) per_sm = 1;
+        const long long per_block = (long long)s.B * FSP_NPT;
+        long long need = (count + per_block - 1) / per_block;
+        long long grid = (long long)I->sm_count * per_sm;
+        if (need < grid) grid = need;
+        fn2<<<(unsigned)grid, s.B, s.L2.bytes, (cudaStream_t)stream>>>(dev_view(I), nodes, (long long)count,
+                                                                       lb_out, s.L2);
+        FSP_CUDA(cudaGetLastError());
+        return FSP_OK;
+    }
     BoundPoolFn fn = pick_bound_pool(s.nw, s.mt, s.es);
     if (!fn) { fsp_set_error("fsp_bound_pool: no kernel for this shape"); return FSP_ERR_ARG; }
     FSP_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -2,7 +2,7 @@
 // kernels.
 #pragma once
 
-#include "fsp_common.cuh"
+#include "fsp_bound2.cuh"
 
 // Shapes compiled: mask words NW (n <= 32, 64, 128, 255) x machine template
 // MT (5, 10, 20, or 0 = any m) with the Johnson entries in shared memory
@@ -13,11 +13,22 @@
     X(4, 5, true) X(4, 10, true) X(4, 20, true) X(4, 0, true) X(4, 0, false)        \
     X(8, 0, true) X(8, 0, false)
 
+// Fast-path shapes (fsp_bound2.cuh): machines MT x record vectors NV
+// (stride 16 * NV bytes) x mask words NW, two nodes per thread.
+#define FSP_SHAPES2(X)                                                   \
+    X(5, 1, 1) X(5, 2, 1) X(5, 3, 1) X(5, 3, 2) X(5, 4, 2)                \
+    X(10, 1, 1) X(10, 2, 1) X(10, 3, 1) X(10, 3, 2) X(10, 4, 2)           \
+    X(20, 1, 1) X(20, 2, 1) X(20, 3, 1) X(20, 3, 2) X(20, 4, 2)
+#define FSP_NPT 2
+#define FSP_B2 128
+
 struct BoundShape {
-    int nw, mt;
+    int ver;  // 2: fast path (fsp_bound2.cuh), 1: any shape (fsp_common.cuh)
+    int nw, mt, nv;
     bool es;
     int B;
     BoundSmem L;
+    Bound2Smem L2;
 };
 
 // Pick the kernel shape and CTA size whose shared memory fits the device.

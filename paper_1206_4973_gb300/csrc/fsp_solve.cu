@@ -6,7 +6,7 @@
 // host only launches one iteration after another:
 //   K-select  one CTA: pops the deepest parents (top of the depth-first
 //             stack) while their children fit in the pool; writes the
-//             child -> (parent, rank) map.
+//             parents' first-child offsets.
 //   K2+K1     one thread per child: builds the child record (prefix + job,
 //             remaining set kept in increasing job order) and bounds it;
 //             complete schedules race for the incumbent with one 64-bit
@@ -42,7 +42,7 @@ struct SolveWs {
     long long cap;
     uint8_t *children;
     int32_t *lbs;
-    int2 *cmap;
+    int *poff;              // first child of each popped parent; poff[np] = children
     int *blk;
     uint8_t *inc;
     long long *trace;
@@ -54,7 +54,7 @@ struct SolveWs {
 struct SolveLayout {
     long long pool_max, max_children, cap, trace_cap;
     int max_blocks;
-    size_t off_ctl, off_stack, off_children, off_lbs, off_cmap, off_blk, off_inc, off_trace, bytes;
+    size_t off_ctl, off_stack, off_children, off_lbs, off_poff, off_blk, off_inc, off_trace, bytes;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -78,14 +78,15 @@ static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout
     L->pool_max = pmax;
     L->max_children = pmax + I->n;
     L->max_blocks = (int)((L->max_children + SOLVE_B - 1) / SOLVE_B);
-    L->cap = o->stack_capacity > 0 ? o->stack_capacity : (long long)I->n * (pmax + I->n);
+    const long long init = (o->init_nodes && o->init_count > 0) ? o->init_count : 0;
+    L->cap = o->stack_capacity > 0 ? o->stack_capacity : init + (long long)I->n * (pmax + I->n);
     L->trace_cap = (o->trace && o->trace_cap > 0) ? o->trace_cap : 0;
     size_t off = 0;
     L->off_ctl = off; off = align256(off + sizeof(SolveCtl));
     L->off_stack = off; off = align256(off + (size_t)L->cap * I->stride);
     L->off_children = off; off = align256(off + (size_t)L->max_children * I->stride);
     L->off_lbs = off; off = align256(off + (size_t)L->max_children * 4);
-    L->off_cmap = off; off = align256(off + (size_t)L->max_children * 8);
+    L->off_poff = off; off = align256(off + (size_t)(L->max_children + 2) * 4);
     L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 8);
     L->off_inc = off; off = align256(off + 256);
     L->off_trace = off; off = align256(off + (size_t)L->trace_cap * 32);
@@ -117,6 +118,51 @@ __global__ void k_solve_init(SolveWs ws, int n, int stride, int ub0)
         c.ub_iter = ub0;
         c.best_key = ~0ull;
         *ws.ctl = c;
+    }
+}
+
+// Start from caller records: validate each (a permutation, depth <= n-2) and
+// re-sort its remaining part by job index, the order branching relies on.
+__global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long count, int ub0)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) {
+        SolveCtl *c = ws.ctl;
+        c->stack_size = count;
+        c->s_pop = 0;
+        c->n_parents = 0;
+        c->n_children = 0;
+        c->best_key = ~0ull;
+        c->ub = ub0;
+        c->ub_iter = ub0;
+        for (int i = 0; i < 6; ++i) c->cnt[i] = 0;
+    }
+    if (t >= count) return;
+    uint8_t *r = ws.stack + t * stride;
+    const int d = r[n];
+    uint32_t seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t rem[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    bool bad = d > n - 2;
+    for (int i = 0; i < n; ++i) {
+        const int j = r[i];
+        if (j >= n) { bad = true; continue; }
+        const uint32_t bit = 1u << (j & 31);
+        if (seen[j >> 5] & bit) bad = true;
+        seen[j >> 5] |= bit;
+        if (i >= d) rem[j >> 5] |= bit;
+    }
+    if (bad) {
+        atomicExch(&ws.ctl->status, FSP_ERR_ARG);
+        return;
+    }
+    int o = d;
+    for (int w = 0; w < 8; ++w) {
+        uint32_t x = rem[w];
+        while (x) {
+            const int b = __ffs(x) - 1;
+            x &= x - 1;
+            r[o++] = (uint8_t)(w * 32 + b);
+        }
     }
 }
 
@@ -163,34 +209,54 @@ __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot)
 }
 
 // Selection (Sec. III): deepest pending nodes first, while their children fit.
+// The candidates are the top min(S, pool) records (every parent has at least
+// one child); each thread takes SEL_PER consecutive candidates per chunk.
+#define SEL_PER 8
 __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stride, long long pool)
 {
     __shared__ int warp_tot[32];
-    __shared__ int s_last;
+    __shared__ int s_taken, s_sum;
     SolveCtl *ctl = ws.ctl;
     const long long S = ctl->stack_size;
+    const long long cand = S < pool ? S : pool;
     long long running = 0, np = 0;
-    if (S > 0) {
-        for (long long base = 0; base < S; base += SELECT_B) {
-            const long long i = base + threadIdx.x;
-            const int r = i < S ? n - (int)ws.stack[(S - 1 - i) * stride + n] : 0;
-            const int incl = block_incl_scan(r, warp_tot);
-            const bool taken = i < S && (i == 0 || running + incl <= pool);
-            const int cnt = __syncthreads_count(taken);
-            if (taken) {
-                const long long c0 = running + (incl - r);
-                for (int ci = 0; ci < r; ++ci) ws.cmap[c0 + ci] = make_int2((int)i, ci);
-            }
-            if (cnt == 0) break;
-            if (threadIdx.x == cnt - 1) s_last = incl;
-            __syncthreads();
-            running += s_last;
-            np += cnt;
-            __syncthreads();
-            if (cnt < SELECT_B) break;
+    for (long long base = 0; base < cand; base += (long long)SELECT_B * SEL_PER) {
+        int r[SEL_PER];
+        int tsum = 0;
+#pragma unroll
+        for (int q = 0; q < SEL_PER; ++q) {
+            const long long i = base + (long long)threadIdx.x * SEL_PER + q;
+            r[q] = i < cand ? n - (int)ws.stack[(S - 1 - i) * stride + n] : 0;
+            tsum += r[q];
         }
+        const int excl = block_incl_scan(tsum, warp_tot) - tsum;
+        int taken = 0, tsum_taken = 0, run = excl;
+#pragma unroll
+        for (int q = 0; q < SEL_PER; ++q) {
+            const long long i = base + (long long)threadIdx.x * SEL_PER + q;
+            const bool t = i < cand && (i == 0 || running + run + r[q] <= pool);
+            if (t) {
+                ws.poff[i] = (int)(running + run);  // taken candidates are exactly 0..np-1
+                taken++;
+                tsum_taken += r[q];
+            }
+            run += r[q];
+        }
+        if (threadIdx.x == 0) { s_taken = 0; s_sum = 0; }
+        __syncthreads();
+        if (taken) {
+            atomicAdd(&s_taken, taken);
+            atomicAdd(&s_sum, tsum_taken);
+        }
+        __syncthreads();
+        const int ct = s_taken, cs = s_sum;
+        __syncthreads();
+        np += ct;
+        running += cs;
+        if (ct < SELECT_B * SEL_PER) break;
     }
     if (threadIdx.x == 0) {
+        ws.poff[np] = (int)running;
         ctl->best_key = ~0ull;
         ctl->ub_iter = ctl->ub;
         if (S - np + running > ws.cap) {  // could overflow: keep the stack intact
@@ -204,6 +270,18 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
             ctl->s_pop = S - np;
         }
     }
+}
+
+// Parent of child c: the last p with poff[p] <= c (poff increasing, poff[0] = 0).
+__device__ __forceinline__ int solve_parent_of(const int *__restrict__ poff, int np, long long c)
+{
+    int lo = 0, hi = np;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)__ldg(poff + mid) <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Branching + bounding, one thread per child.
@@ -228,9 +306,10 @@ __global__ void __launch_bounds__(256) k_branch_bound(DevInst I, SolveWs ws, Bou
     const long long c = (long long)blockIdx.x * B + tid;
     if (c >= nch) return;
     const int n = I.n, stride = I.stride, nvec = stride >> 4;
-    const int2 pc = ws.cmap[c];
-    const long long S = ctl->s_pop + ctl->n_parents;
-    const uint4 *src = reinterpret_cast<const uint4 *>(ws.stack + (S - 1 - pc.x) * stride);
+    const int np = (int)ctl->n_parents;
+    const int pi = solve_parent_of(ws.poff, np, c);
+    const long long S = ctl->s_pop + np;
+    const uint4 *src = reinterpret_cast<const uint4 *>(ws.stack + (S - 1 - pi) * stride);
     for (int v = 0; v < nvec; ++v) {
         const uint4 x = src[v];
         rec[(4 * v + 0) * B] = x.x;
@@ -241,7 +320,7 @@ __global__ void __launch_bounds__(256) k_branch_bound(DevInst I, SolveWs ws, Bou
     // Child of rank ci: prefix, then job par[d+ci], then par[d..n) without it
     // (the remaining set stays in increasing job order).
     const int d = (int)fsp_rec_byte(rec, B, n);
-    const int ci = pc.y;
+    const int ci = (int)(c - ws.poff[pi]);
     const uint32_t x = fsp_rec_byte(rec, B, d + ci);
     uint32_t prev = 0;
     for (int w = 0; w < (stride >> 2); ++w) {
@@ -376,6 +455,79 @@ __global__ void __launch_bounds__(SOLVE_B) k_push(SolveWs ws, int n, int stride)
     }
 }
 
+// Branching + bounding, fast path: NPT children per thread (fsp_bound2.cuh).
+template <int MT, int NV, int NW>
+__global__ void __launch_bounds__(FSP_B2) k_branch_bound2(DevInst I, SolveWs ws, Bound2Smem L)
+{
+    constexpr int NPT = FSP_NPT;
+    const SolveCtl *ctl = ws.ctl;
+    const long long nch = ctl->n_children;
+    const int B = blockDim.x, tid = threadIdx.x, SB = B * NPT;
+    if ((long long)blockIdx.x * SB >= nch) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    FspEntry *ent_s = reinterpret_cast<FspEntry *>(smem + L.ent_off);
+    int2 *pq_s = reinterpret_cast<int2 *>(smem + L.pq_off);
+    int32_t *cs = reinterpret_cast<int32_t *>(smem + L.cs_off);
+    int32_t *sq = reinterpret_cast<int32_t *>(smem + L.sq_off);
+    fsp_stage_pq(I, ent_s, pq_s);
+    const int n = I.n, stride = I.stride;
+    const int np = (int)ctl->n_parents;
+    const long long S = ctl->s_pop + np;
+    const int ub_iter = ctl->ub_iter;
+    int slot[NPT];
+    uint32_t Um[NPT][NW];
+    int32_t lb[NPT];
+    int dch[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        slot[j] = tid + j * B;
+        const long long c = (long long)blockIdx.x * SB + slot[j];
+        FspRec<NV> ch;
+        if (c < nch) {
+            const int pi = solve_parent_of(ws.poff, np, c);
+            const int ci = (int)(c - __ldg(ws.poff + pi));
+            FspRec<NV> par;
+            fsp_load_rec(par, ws.stack + (S - 1 - pi) * stride);
+            fsp_make_child(par, n, ci, ch);
+            fsp_store_rec(ch, ws.children + c * stride);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4 * NV; ++q) ch.w[q] = 0u;
+        }
+        dch[j] = (int)fsp_rec_byte_dyn(ch, n);
+        int32_t C[MT], SQ[MT];
+        bool bad;
+        fsp_prologue<MT, NV, NW>(ch, n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad);
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+            cs[k * SB + slot[j]] = C[k];
+            sq[k * SB + slot[j]] = SQ[k];
+        }
+    }
+    fsp_pair_scan<MT, NPT, NW>(n, ent_s, cs, sq, SB, slot, Um, lb);
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const long long c = (long long)blockIdx.x * SB + slot[j];
+        if (c < nch) {
+            ws.lbs[c] = lb[j];
+            if (dch[j] == n - 1 && lb[j] < ub_iter)
+                atomicMin(&ws.ctl->best_key,
+                          ((unsigned long long)(uint32_t)lb[j] << 32) | (unsigned long long)c);
+        }
+    }
+}
+
+typedef void (*BranchBound2Fn)(DevInst, SolveWs, Bound2Smem);
+
+static BranchBound2Fn pick_branch_bound2(int mt, int nv, int nw)
+{
+#define FSP_CASE2(MT_, NV_, NW_) \
+    if (mt == MT_ && nv == NV_ && nw == NW_) return &k_branch_bound2<MT_, NV_, NW_>;
+    FSP_SHAPES2(FSP_CASE2)
+#undef FSP_CASE2
+    return nullptr;
+}
+
 typedef void (*BranchBoundFn)(DevInst, SolveWs, BoundSmem);
 
 static BranchBoundFn pick_branch_bound(int nw, int mt, bool es)
@@ -400,10 +552,20 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
     if (rc != FSP_OK) return rc;
     BoundShape shp;
     if ((rc = fsp_bound_shape(I, &shp)) != FSP_OK) return rc;
-    BranchBoundFn bb = pick_branch_bound(shp.nw, shp.mt, shp.es);
-    if (!bb) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
-    FSP_CUDA(cudaFuncSetAttribute((const void *)bb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)shp.L.bytes));
+    BranchBoundFn bb = nullptr;
+    BranchBound2Fn bb2 = nullptr;
+    if (shp.ver == 2) {
+        bb2 = pick_branch_bound2(shp.mt, shp.nv, shp.nw);
+        if (!bb2) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
+        FSP_CUDA(cudaFuncSetAttribute((const void *)bb2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)shp.L2.bytes));
+    } else {
+        bb = pick_branch_bound(shp.nw, shp.mt, shp.es);
+        if (!bb) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
+        FSP_CUDA(cudaFuncSetAttribute((const void *)bb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)shp.L.bytes));
+    }
+    const int per_cta = shp.ver == 2 ? shp.B * FSP_NPT : shp.B;
     if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
         fsp_set_error("fsp_solve: workspace must be 256-byte aligned");
         return FSP_ERR_ARG;
@@ -422,7 +584,7 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
     ws.cap = L.cap;
     ws.children = base + L.off_children;
     ws.lbs = (int32_t *)(base + L.off_lbs);
-    ws.cmap = (int2 *)(base + L.off_cmap);
+    ws.poff = (int *)(base + L.off_poff);
     ws.blk = (int *)(base + L.off_blk);
     ws.inc = base + L.off_inc;
     ws.trace = (long long *)(base + L.off_trace);
@@ -431,7 +593,18 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
     ws.max_blocks = L.max_blocks;
     const DevInst D = dev_view(I);
 
+    if (o.init_nodes && o.init_count > 0) {
+        if (I->n < 2) { fsp_set_error("fsp_solve: init_nodes need n >= 2"); if (owned) cudaFree(base); return FSP_ERR_ARG; }
+        if (o.init_count > L.cap) {
+            fsp_set_error("fsp_solve: %lld init nodes exceed the stack capacity %lld",
+                          (long long)o.init_count, L.cap);
+            if (owned) cudaFree(base);
+            return FSP_ERR_CAPACITY;
+        }
+    }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
+    double t_sel = 0, t_bb = 0, t_cmp = 0;
     SolveCtl h;
     memset(&h, 0, sizeof h);
     cudaError_t e = cudaSuccess;
@@ -442,6 +615,8 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
     } while (0)
     TRY(cudaEventCreate(&ev0));
     TRY(cudaEventCreate(&ev1));
+    if (o.profile)
+        for (int i = 0; i < 4; ++i) TRY(cudaEventCreate(&pe[i]));
     TRY(cudaEventRecord(ev0, st));
     if (I->n == 1) {
         k_solve_single<<<1, 32, 0, st>>>(ws, I->d_p, I->m, ub0);
@@ -449,28 +624,52 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
         TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
     } else {
-        k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
+        if (o.init_nodes && o.init_count > 0) {
+            TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(SolveCtl), st));
+            TRY(cudaMemcpyAsync(ws.stack, o.init_nodes, (size_t)o.init_count * I->stride, cudaMemcpyDefault, st));
+            k_solve_init_nodes<<<(unsigned)((o.init_count + 255) / 256), 256, 0, st>>>(ws, I->n, I->stride,
+                                                                                         o.init_count, ub0);
+        } else {
+            k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
+        }
         TRY(cudaGetLastError());
         for (long long it = 0;; ++it) {
             TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
             TRY(cudaStreamSynchronize(st));
+            if (o.profile && it > 0) {
+                float a = 0, b = 0, c = 0;
+                TRY(cudaEventElapsedTime(&a, pe[0], pe[1]));
+                TRY(cudaEventElapsedTime(&b, pe[1], pe[2]));
+                TRY(cudaEventElapsedTime(&c, pe[2], pe[3]));
+                t_sel += a;
+                t_bb += b;
+                t_cmp += c;
+            }
             if (h.status != 0) {
                 rc = h.status;
                 fsp_set_error(rc == FSP_ERR_CAPACITY ? "fsp_solve: stack capacity exceeded"
-                                                     : "fsp_solve: device error");
+                              : rc == FSP_ERR_ARG ? "fsp_solve: malformed init node (not a permutation "
+                                                    "or depth > n-2)"
+                                                  : "fsp_solve: device error");
                 break;
             }
             if (h.stack_size == 0) break;
             if (o.node_budget > 0 && h.cnt[0] >= o.node_budget) { rc = FSP_INCOMPLETE; break; }
+            if (o.max_iterations > 0 && it >= o.max_iterations) { rc = FSP_INCOMPLETE; break; }
             long long pool = o.pool_size;
             if (o.schedule && o.schedule_len > 0)
                 pool = o.schedule[it < o.schedule_len ? it : o.schedule_len - 1];
             const int grid = (int)((pool + I->n + SOLVE_B - 1) / SOLVE_B);
-            const int grid_bb = (int)((pool + I->n + shp.B - 1) / shp.B);
+            const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
+            if (o.profile) TRY(cudaEventRecord(pe[0], st));
             k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool);
-            bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
+            if (o.profile) TRY(cudaEventRecord(pe[1], st));
+            if (bb2) bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
+            else bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
+            if (o.profile) TRY(cudaEventRecord(pe[2], st));
             k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
             k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
+            if (o.profile) TRY(cudaEventRecord(pe[3], st));
             TRY(cudaGetLastError());
         }
     }
@@ -489,7 +688,13 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
         if (rows > 0)
             TRY(cudaMemcpy(o.trace, ws.trace, (size_t)rows * 32, cudaMemcpyDeviceToHost));
     }
+    if (o.out_count) *o.out_count = h.stack_size;
+    if (o.out_nodes && h.stack_size > 0 && h.stack_size <= o.out_cap && I->n > 1)
+        TRY(cudaMemcpy(o.out_nodes, ws.stack, (size_t)h.stack_size * I->stride, cudaMemcpyDefault));
     if (stats) {
+        stats->select_ms = t_sel;
+        stats->bound_ms = t_bb;
+        stats->compact_ms = t_cmp;
         stats->nodes_bounded = h.cnt[0];
         stats->nodes_branched = h.cnt[1];
         stats->nodes_pruned = h.cnt[2];
@@ -504,6 +709,8 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
 out:
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    for (int i = 0; i < 4; ++i)
+        if (pe[i]) cudaEventDestroy(pe[i]);
     if (owned) cudaFree(base);
     return rc;
 }

@@ -38,7 +38,8 @@ class fsp_stats(ctypes.Structure):
     _fields_ = [("nodes_bounded", ctypes.c_int64), ("nodes_branched", ctypes.c_int64),
                 ("nodes_pruned", ctypes.c_int64), ("leaves", ctypes.c_int64),
                 ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64),
-                ("time_ms", ctypes.c_double)]
+                ("time_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
+                ("bound_ms", ctypes.c_double), ("compact_ms", ctypes.c_double)]
 
 
 class fsp_options(ctypes.Structure):
@@ -46,7 +47,11 @@ class fsp_options(ctypes.Structure):
                 ("stack_capacity", ctypes.c_int64), ("ub0_perm", ctypes.POINTER(ctypes.c_int32)),
                 ("trace", ctypes.POINTER(ctypes.c_int64)), ("trace_cap", ctypes.c_int64),
                 ("schedule", ctypes.POINTER(ctypes.c_int64)), ("schedule_len", ctypes.c_int64),
-                ("workspace", ctypes.c_void_p), ("stream", ctypes.c_void_p)]
+                ("workspace", ctypes.c_void_p), ("stream", ctypes.c_void_p),
+                ("init_nodes", ctypes.c_void_p), ("init_count", ctypes.c_int64),
+                ("max_iterations", ctypes.c_int64), ("out_nodes", ctypes.c_void_p),
+                ("out_cap", ctypes.c_int64), ("out_count", ctypes.POINTER(ctypes.c_int64)),
+                ("profile", ctypes.c_int)]
 
 
 _lib = None
@@ -175,14 +180,37 @@ def fsp_check_status(inst: Instance, stream=None) -> None:
     _check(load().fsp_check_status(inst.handle, _stream(stream)))
 
 
+def _ptr(buf):
+    """Address of a torch tensor (device or host) or a numpy array."""
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr()
+    return np.asarray(buf).ctypes.data
+
+
 def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
-             schedule=None, stream=None):
+             schedule=None, stream=None, init_nodes=None, init_count=None, max_iterations=0,
+             out_nodes=None, profile=False):
     o = fsp_options()
     load().fsp_default_options(ctypes.byref(o))
     o.pool_size = int(pool_size)
     o.node_budget = int(node_budget)
     o.stack_capacity = int(stack_capacity)
+    o.max_iterations = int(max_iterations)
+    o.profile = 1 if profile else 0
     keep = []
+    if init_nodes is not None:
+        if not hasattr(init_nodes, "data_ptr"):
+            init_nodes = np.ascontiguousarray(init_nodes, dtype=np.uint8)
+        keep.append(init_nodes)
+        o.init_nodes = _ptr(init_nodes)
+        o.init_count = int(init_nodes.shape[0] if init_count is None else init_count)
+    out_count = ctypes.c_int64(0)
+    keep.append(out_count)
+    o.out_count = ctypes.pointer(out_count)
+    if out_nodes is not None:
+        keep.append(out_nodes)
+        o.out_nodes = _ptr(out_nodes)
+        o.out_cap = int(out_nodes.shape[0])
     if ub0_perm is not None:
         a = np.ascontiguousarray(ub0_perm, dtype=np.int32)
         keep.append(a)
@@ -199,11 +227,11 @@ def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, tra
         o.schedule = s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         o.schedule_len = len(s)
     o.stream = _stream(stream)
-    return o, keep, trace
+    return o, keep, trace, out_count
 
 
 def fsp_solve_workspace_bytes(inst: Instance, **kw) -> int:
-    o, _keep, _ = _options(**kw)
+    o, _keep, _, _ = _options(**kw)
     return _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
 
 
@@ -212,13 +240,19 @@ STATS = ("nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iteration
 
 def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,
               stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
-              workspace=None):
+              workspace=None, init_nodes=None, init_count=None, max_iterations: int = 0,
+              out_nodes=None, profile: bool = False):
     """Exact B&B on the device.  The scratch is a torch uint8 tensor (allocated
-    here when `workspace` is None).  Returns a dict: status, cmax, perm (None
-    if the search found nothing better than ub0 and no ub0_perm was given),
-    the counters of STATS, time_ms and, if trace_cap > 0, the trace rows."""
+    here when `workspace` is None).  init_nodes (host array or device tensor of
+    records) starts the search from that stack; out_nodes (host array or
+    device tensor [cap, stride]) receives the stack left at the end.  Returns a
+    dict: status, cmax, perm (None if the search found nothing better than ub0
+    and no ub0_perm was given), the counters of STATS, time_ms, the phase
+    times when profile is set, stack_left and, if trace_cap > 0, the trace."""
     import torch
-    o, keep, trace = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap, schedule, stream)
+    o, keep, trace, out_count = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap,
+                                         schedule, stream, init_nodes, init_count, max_iterations,
+                                         out_nodes, profile)
     nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -232,7 +266,9 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
                                  perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(st),
                                  ctypes.byref(o)))
     res = {k: int(getattr(st, k)) for k in STATS}
-    res["time_ms"] = float(st.time_ms)
+    for k in ("time_ms", "select_ms", "bound_ms", "compact_ms"):
+        res[k] = float(getattr(st, k))
+    res["stack_left"] = int(out_count.value)
     res["status"] = rc
     res["cmax"] = int(cmax.value)
     res["perm"] = perm if perm[0] >= 0 else None

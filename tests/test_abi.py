@@ -59,3 +59,26 @@ def test_create_instance_rejects_bad_shapes_without_touching_the_device(lib):
 def test_library_is_built_for_sm_103a_only():
     # the build passes exactly one -gencode (sm_103a) to every nvcc call
     assert fsp_build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structs have the header's sizes and offsets."""
+    import subprocess
+    src = tmp_path / "layout.c"
+    fields = {"fsp_options": [f for f, _ in fsp.fsp_options._fields_],
+              "fsp_stats": [f for f, _ in fsp.fsp_stats._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fsp.h"', "int main(void){"]
+    for st, fl in fields.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fl:
+            lines.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0;}")
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.split("\n") if l)
+    for st, cls in (("fsp_options", fsp.fsp_options), ("fsp_stats", fsp.fsp_stats)):
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for f in fields[st]:
+            assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, f"{st}.{f}"

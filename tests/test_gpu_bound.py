@@ -126,3 +126,20 @@ def test_full_size_20x20_workload_sampled(F, count):
     assert np.array_equal(got[idx], want)
     # properties at any size: bounds are positive and never below the prefix makespan
     assert got.min() >= 1
+
+
+@pytest.mark.parametrize("n,m,seed", [(20, 20, 1), (12, 5, 0), (33, 10, 21), (50, 20, 7), (15, 10, 22),
+                                      (47, 5, 23), (63, 20, 24), (31, 20, 25)])
+def test_v1_and_v2_kernels_agree_with_oracle(F, n, m, seed, monkeypatch):
+    """The shapes with a fast-path kernel, bounded by both kernel families."""
+    import torch
+    p = inputs.instance(n, m, seed)
+    rec = edge_pool(n, 1500, seed + 77)
+    want = oracle.bound_pool(p, rec)
+    inst = F.fsp_create_instance(p)
+    nodes = torch.from_numpy(rec).cuda()
+    v2 = F.fsp_bound_pool(inst, nodes).cpu().numpy()
+    monkeypatch.setenv("FSP_BOUND_V1", "1")
+    v1 = F.fsp_bound_pool(inst, nodes).cpu().numpy()
+    assert np.array_equal(v2, want)
+    assert np.array_equal(v1, want)

@@ -134,3 +134,80 @@ def test_caller_workspace_and_stream(F):
     got = F.fsp_solve(inst, pool_size=32, workspace=ws, stream=s)
     ref = oracle.solve(p, pool=32)
     assert got["cmax"] == ref["cmax"] and got["nodes_bounded"] == ref["bounded"]
+
+
+def canon(rec, n):
+    """Records as (prefix, sorted remaining set, depth): equal up to the order
+    in which a record lists its remaining jobs."""
+    out = []
+    for r in rec:
+        d = int(r[n])
+        out.append((tuple(r[:d]), tuple(sorted(r[d:n])), d))
+    return out
+
+
+def frontier_20x20(count):
+    n = 20
+    p, ub_perm, rec = inputs.pool_workload(n, 20, 1, count)
+    return p, ub_perm, rec[rec[:, n] <= n - 2]
+
+
+@pytest.mark.parametrize("pool,iters", [(4096, 3), (2**15, 1), (100, 7)])
+def test_start_from_frontier_matches_oracle(F, pool, iters):
+    """The bench step: a frontier of random 20 x 20 prefixes as the starting
+    stack, UB = makespan of a random permutation, a few iterations."""
+    import torch
+    n = 20
+    p, ub_perm, rec = frontier_20x20(40000)
+    ub = oracle.makespan(p, ub_perm)
+    ref = oracle.solve(p, ub0=ub, pool=pool, init_nodes=rec, max_iterations=iters, trace_cap=16,
+                       export_stack=True)
+    inst = F.fsp_create_instance(p)
+    for init in (rec, torch.from_numpy(rec).cuda()):
+        out = np.zeros((len(rec) + pool * iters, 32), np.uint8)
+        got = F.fsp_solve(inst, ub0=ub, pool_size=pool, init_nodes=init, max_iterations=iters,
+                          trace_cap=16, out_nodes=out, profile=True)
+        same(got, ref)
+        assert got["stack_left"] == ref["stack_left"]
+        assert canon(out[: got["stack_left"]], n) == canon(ref["stack"], n)
+        assert got["bound_ms"] > 0 and got["select_ms"] > 0 and got["compact_ms"] > 0
+
+
+@pytest.mark.parametrize("pool,cut", [(1, 5), (16, 3), (256, 2)])
+def test_resume_on_gpu(F, pool, cut):
+    p = inputs.instance(9, 4, 151)
+    inst = F.fsp_create_instance(p)
+    full = F.fsp_solve(inst, pool_size=pool)
+    out = np.zeros((4096, 16), np.uint8)
+    a = F.fsp_solve(inst, pool_size=pool, max_iterations=cut, out_nodes=out)
+    assert a["status"] == F.INCOMPLETE and a["iterations"] == cut
+    b = F.fsp_solve(inst, ub0=a["cmax"], ub0_perm=a["perm"], pool_size=pool,
+                    init_nodes=out[: a["stack_left"]])
+    assert b["cmax"] == full["cmax"] == oracle.bruteforce(p)[0]
+    for k in ("nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iterations"):
+        assert a[k] + b[k] == full[k], k
+    assert list(b["perm"]) == list(full["perm"])
+
+
+def test_init_nodes_validated_on_gpu(F):
+    p = inputs.instance(6, 3, 161)
+    inst = F.fsp_create_instance(p)
+    rec = np.zeros((2, 16), np.uint8)
+    rec[:, :6] = [0, 1, 2, 3, 4, 5]
+    rec[:, 6] = 2
+    rec[1, 6] = 5  # depth n-1
+    with pytest.raises(F.FspError) as e:
+        F.fsp_solve(inst, init_nodes=rec)
+    assert e.value.code == F.ERR_ARG
+    got = F.fsp_solve(inst, init_nodes=rec[:1])
+    ref = oracle.solve(p, init_nodes=rec[:1])
+    assert got["cmax"] == ref["cmax"] and got["nodes_bounded"] == ref["bounded"]
+
+
+@pytest.mark.parametrize("n,m,seed,pool", [(12, 5, 0, 1024), (9, 20, 88, 64), (10, 10, 87, 7)])
+def test_v1_search_kernels_match_oracle(F, n, m, seed, pool, monkeypatch):
+    monkeypatch.setenv("FSP_BOUND_V1", "1")
+    p = inputs.instance(n, m, seed)
+    ref = oracle.solve(p, pool=pool, trace_cap=100000)
+    got = F.fsp_solve(F.fsp_create_instance(p), pool_size=pool, trace_cap=100000)
+    same(got, ref)

@@ -326,3 +326,33 @@ def test_golden_files_reproduce():
             p, _, nodes = inputs.pool_workload(g["n"], g["m"], g["seed"], g["count"])
             lbs = oracle.bound_pool(p, nodes)
             assert lbs.tolist() == g["lb"]
+
+
+# ---------------------------------------------------- checkpoint/resume ---
+@pytest.mark.parametrize("pool,cut", [(1, 5), (16, 3), (256, 2)])
+def test_resume_from_exported_stack_completes_the_search(pool, cut):
+    """Stopping after `cut` iterations and resuming from the stack left, with
+    the incumbent as ub0, reaches the same optimum with the same total work."""
+    p = inputs.instance(9, 4, 151)
+    full = oracle.solve(p, pool=pool)
+    a = oracle.solve(p, pool=pool, max_iterations=cut, export_stack=True)
+    assert a["status"] == oracle.INCOMPLETE and a["iterations"] == cut
+    assert len(a["stack"]) == a["stack_left"] > 0
+    b = oracle.solve(p, ub0=a["cmax"], pool=pool, init_nodes=a["stack"], ub0_perm=a["perm"])
+    assert b["cmax"] == full["cmax"] == oracle.bruteforce(p)[0]
+    for k in ("bounded", "branched", "pruned", "leaves", "iterations"):
+        assert a[k] + b[k] == full[k], k
+    assert list(b["perm"]) == list(full["perm"])
+
+
+def test_init_nodes_are_validated():
+    p = inputs.instance(6, 3, 161)
+    rec = np.zeros((1, 16), np.uint8)
+    rec[0, :6] = [0, 1, 2, 3, 4, 5]
+    rec[0, 6] = 5  # depth n-1: a complete schedule, not a pending node
+    with pytest.raises(ValueError):
+        oracle.solve(p, init_nodes=rec)
+    rec[0, 6] = 2
+    rec[0, 1] = 0  # repeated job
+    with pytest.raises(ValueError):
+        oracle.solve(p, init_nodes=rec)
