@@ -169,6 +169,34 @@ int64_t fsp_solve_workspace_bytes(const fsp_instance *inst, const fsp_options *o
 int fsp_solve(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
               const fsp_options *opt);
 
+/* Bytes of the fixed scratch array fsp_solve_noalloc uses (16 MiB). */
+#define FSP_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* fsp_solve without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc while they
+ * run -- processes whose device memory is reserved up front by a pool or a
+ * fixed budget, plugins handed only their input and output buffers, and
+ * paths where cudaMalloc's implicit synchronisation of the device is not
+ * acceptable.  It runs the same search as fsp_solve, with the same
+ * arguments, options and results, but its scratch is a device array of
+ * FSP_NOALLOC_SCRATCH_BYTES that the library defines at file scope; every
+ * device that loads the library holds that array until the process exits.
+ *   - It allocates nothing (no cudaMalloc, cudaFree, CUDA events or other
+ *     allocating call) and therefore reports time_ms and the phase times as
+ *     0; opt->profile has no effect.  opt->workspace must be NULL.
+ *   - The instance's device must be current.  The first call on a device
+ *     looks up the array's device address (cudaGetSymbolAddress) and keeps
+ *     it; make that first call before any stream capture on that device.
+ *   - A search whose scratch (fsp_solve_workspace_bytes) exceeds
+ *     FSP_NOALLOC_SCRATCH_BYTES is rejected with FSP_ERR_CAPACITY and a
+ *     message; nothing runs.
+ *   - All calls share the one array: it keeps the last call's contents
+ *     (every search initialises what it reads), and calls whose work overlaps
+ *     on the GPU -- on different streams or host threads -- race on it.
+ *     Serialise them. */
+int fsp_solve_noalloc(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
+                      const fsp_options *opt);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fsp_last_error(void);
 

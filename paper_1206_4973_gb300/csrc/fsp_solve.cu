@@ -18,6 +18,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "fsp_bound.cuh"
 
 #define SOLVE_B 256        // threads per block of the per-child kernels
@@ -541,43 +543,69 @@ static BranchBoundFn pick_branch_bound(int nw, int mt, bool es)
 
 // ------------------------------------------------------------------ host --
 
-extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
-                         const fsp_options *opt)
+// Options, workspace layout and kernels of one search.
+struct SolvePlan {
+    fsp_options o;
+    SolveLayout L;
+    BoundShape shp;
+    BranchBoundFn bb;
+    BranchBound2Fn bb2;
+    int per_cta;
+};
+
+static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fsp_options *opt, SolvePlan *P)
 {
     if (!I || !cmax || !perm) { fsp_set_error("fsp_solve: NULL argument"); return FSP_ERR_ARG; }
-    fsp_options o;
-    if (opt) o = *opt; else fsp_default_options(&o);
-    SolveLayout L;
-    int rc = solve_layout(I, &o, &L);
+    if (opt) P->o = *opt; else fsp_default_options(&P->o);
+    const fsp_options &o = P->o;
+    int rc = solve_layout(I, &o, &P->L);
     if (rc != FSP_OK) return rc;
-    BoundShape shp;
-    if ((rc = fsp_bound_shape(I, &shp)) != FSP_OK) return rc;
-    BranchBoundFn bb = nullptr;
-    BranchBound2Fn bb2 = nullptr;
+    if ((rc = fsp_bound_shape(I, &P->shp)) != FSP_OK) return rc;
+    const BoundShape &shp = P->shp;
+    P->bb = nullptr;
+    P->bb2 = nullptr;
     if (shp.ver == 2) {
-        bb2 = pick_branch_bound2(shp.mt, shp.nv, shp.nw);
-        if (!bb2) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
-        FSP_CUDA(cudaFuncSetAttribute((const void *)bb2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        P->bb2 = pick_branch_bound2(shp.mt, shp.nv, shp.nw);
+        if (!P->bb2) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
+        FSP_CUDA(cudaFuncSetAttribute((const void *)P->bb2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)shp.L2.bytes));
     } else {
-        bb = pick_branch_bound(shp.nw, shp.mt, shp.es);
-        if (!bb) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
-        FSP_CUDA(cudaFuncSetAttribute((const void *)bb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        P->bb = pick_branch_bound(shp.nw, shp.mt, shp.es);
+        if (!P->bb) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
+        FSP_CUDA(cudaFuncSetAttribute((const void *)P->bb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)shp.L.bytes));
     }
-    const int per_cta = shp.ver == 2 ? shp.B * FSP_NPT : shp.B;
+    P->per_cta = shp.ver == 2 ? shp.B * FSP_NPT : shp.B;
     if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
         fsp_set_error("fsp_solve: workspace must be 256-byte aligned");
         return FSP_ERR_ARG;
     }
-
-    cudaStream_t st = (cudaStream_t)o.stream;
-    uint8_t *base = (uint8_t *)o.workspace;
-    bool owned = false;
-    if (!base) {
-        FSP_CUDA(cudaMalloc(&base, L.bytes));
-        owned = true;
+    if (o.init_nodes && o.init_count > 0) {
+        if (I->n < 2) { fsp_set_error("fsp_solve: init_nodes need n >= 2"); return FSP_ERR_ARG; }
+        if (o.init_count > P->L.cap) {
+            fsp_set_error("fsp_solve: %lld init nodes exceed the stack capacity %lld",
+                          (long long)o.init_count, P->L.cap);
+            return FSP_ERR_CAPACITY;
+        }
     }
+    return FSP_OK;
+}
+
+// One search with its scratch at `base` (P->L.bytes bytes, 256-byte aligned).
+// timed: CUDA events give time_ms and, with opt->profile, the phase times;
+// without it the search creates no event and reports zero times.
+static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
+                     const SolvePlan *P, uint8_t *base, bool timed)
+{
+    const fsp_options &o = P->o;
+    const SolveLayout &L = P->L;
+    const BoundShape &shp = P->shp;
+    const BranchBoundFn bb = P->bb;
+    const BranchBound2Fn bb2 = P->bb2;
+    const int per_cta = P->per_cta;
+    const bool prof = timed && o.profile;
+    int rc = FSP_OK;
+    cudaStream_t st = (cudaStream_t)o.stream;
     SolveWs ws;
     ws.ctl = (SolveCtl *)(base + L.off_ctl);
     ws.stack = base + L.off_stack;
@@ -593,15 +621,6 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
     ws.max_blocks = L.max_blocks;
     const DevInst D = dev_view(I);
 
-    if (o.init_nodes && o.init_count > 0) {
-        if (I->n < 2) { fsp_set_error("fsp_solve: init_nodes need n >= 2"); if (owned) cudaFree(base); return FSP_ERR_ARG; }
-        if (o.init_count > L.cap) {
-            fsp_set_error("fsp_solve: %lld init nodes exceed the stack capacity %lld",
-                          (long long)o.init_count, L.cap);
-            if (owned) cudaFree(base);
-            return FSP_ERR_CAPACITY;
-        }
-    }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
     double t_sel = 0, t_bb = 0, t_cmp = 0;
@@ -613,11 +632,13 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
         e = (call);                                                    \
         if (e != cudaSuccess) { rc = fsp_cuda_fail(e, #call); goto out; } \
     } while (0)
-    TRY(cudaEventCreate(&ev0));
-    TRY(cudaEventCreate(&ev1));
-    if (o.profile)
+    if (timed) {
+        TRY(cudaEventCreate(&ev0));
+        TRY(cudaEventCreate(&ev1));
+    }
+    if (prof)
         for (int i = 0; i < 4; ++i) TRY(cudaEventCreate(&pe[i]));
-    TRY(cudaEventRecord(ev0, st));
+    if (timed) TRY(cudaEventRecord(ev0, st));
     if (I->n == 1) {
         k_solve_single<<<1, 32, 0, st>>>(ws, I->d_p, I->m, ub0);
         TRY(cudaGetLastError());
@@ -636,7 +657,7 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
         for (long long it = 0;; ++it) {
             TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
             TRY(cudaStreamSynchronize(st));
-            if (o.profile && it > 0) {
+            if (prof && it > 0) {
                 float a = 0, b = 0, c = 0;
                 TRY(cudaEventElapsedTime(&a, pe[0], pe[1]));
                 TRY(cudaEventElapsedTime(&b, pe[1], pe[2]));
@@ -661,20 +682,24 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
                 pool = o.schedule[it < o.schedule_len ? it : o.schedule_len - 1];
             const int grid = (int)((pool + I->n + SOLVE_B - 1) / SOLVE_B);
             const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
-            if (o.profile) TRY(cudaEventRecord(pe[0], st));
+            if (prof) TRY(cudaEventRecord(pe[0], st));
             k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool);
-            if (o.profile) TRY(cudaEventRecord(pe[1], st));
+            if (prof) TRY(cudaEventRecord(pe[1], st));
             if (bb2) bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             else bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
-            if (o.profile) TRY(cudaEventRecord(pe[2], st));
+            if (prof) TRY(cudaEventRecord(pe[2], st));
             k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
             k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
-            if (o.profile) TRY(cudaEventRecord(pe[3], st));
+            if (prof) TRY(cudaEventRecord(pe[3], st));
             TRY(cudaGetLastError());
         }
     }
-    TRY(cudaEventRecord(ev1, st));
-    TRY(cudaEventSynchronize(ev1));
+    if (timed) {
+        TRY(cudaEventRecord(ev1, st));
+        TRY(cudaEventSynchronize(ev1));
+    } else {
+        TRY(cudaStreamSynchronize(st));
+    }
     *cmax = h.ub;
     if (h.cnt[5] > 0) {
         uint8_t pb[FSP_MAX_JOBS + 1];
@@ -702,7 +727,7 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
         stats->iterations = h.cnt[4];
         stats->incumbent_updates = h.cnt[5];
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev0, ev1);
+        if (timed) cudaEventElapsedTime(&ms, ev0, ev1);
         stats->time_ms = ms;
     }
 #undef TRY
@@ -711,6 +736,86 @@ out:
     if (ev1) cudaEventDestroy(ev1);
     for (int i = 0; i < 4; ++i)
         if (pe[i]) cudaEventDestroy(pe[i]);
+    return rc;
+}
+
+extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
+                         const fsp_options *opt)
+{
+    SolvePlan P;
+    int rc = solve_prepare(I, cmax, perm, opt, &P);
+    if (rc != FSP_OK) return rc;
+    uint8_t *base = (uint8_t *)P.o.workspace;
+    bool owned = false;
+    if (!base) {
+        FSP_CUDA(cudaMalloc(&base, P.L.bytes));
+        owned = true;
+    }
+    rc = solve_run(I, ub0, cmax, perm, stats, &P, base, true);
     if (owned) cudaFree(base);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// fsp_solve_noalloc: the same search with its scratch in a fixed device array
+// of this library instead of memory allocated per call.  For callers that
+// must not allocate device memory while they run (their device memory is
+// reserved up front by a pool or a fixed budget, or they are plugins handed
+// only input and output buffers, or cudaMalloc's implicit synchronisation of
+// the whole device is unacceptable on their path).  The array occupies
+// FSP_NOALLOC_SCRATCH_BYTES on every device that loads this library, until
+// the process exits.
+// ---------------------------------------------------------------------------
+#define FSP_NOALLOC_MAX_DEVICES 64
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[FSP_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[FSP_NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name only stands for the symbol; the usable address comes from
+// cudaGetSymbolAddress, looked up once per device with that device current.
+static int noalloc_scratch(int dev, uint8_t **out)
+{
+    if (dev < 0 || dev >= FSP_NOALLOC_MAX_DEVICES) {
+        fsp_set_error("fsp_solve_noalloc: device %d out of range", dev);
+        return FSP_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return fsp_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = (uint8_t *)g_noalloc_addr[dev];
+    return FSP_OK;
+}
+
+extern "C" int fsp_solve_noalloc(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
+                                 const fsp_options *opt)
+{
+    if (opt && opt->workspace) {
+        fsp_set_error("fsp_solve_noalloc: takes no workspace (it uses its fixed scratch)");
+        return FSP_ERR_ARG;
+    }
+    SolvePlan P;
+    int rc = solve_prepare(I, cmax, perm, opt, &P);
+    if (rc != FSP_OK) return rc;
+    if (P.L.bytes > (size_t)FSP_NOALLOC_SCRATCH_BYTES) {
+        fsp_set_error("fsp_solve_noalloc: this search needs %zu bytes of scratch, the fixed scratch holds %zu "
+                      "(lower pool_size, stack_capacity, trace_cap or init_count, or use fsp_solve)",
+                      P.L.bytes, (size_t)FSP_NOALLOC_SCRATCH_BYTES);
+        return FSP_ERR_CAPACITY;
+    }
+    int dev = -1;
+    FSP_CUDA(cudaGetDevice(&dev));
+    if (dev != I->device) {
+        fsp_set_error("fsp_solve_noalloc: make the instance's device (%d) current (current: %d)", I->device, dev);
+        return FSP_ERR_ARG;
+    }
+    uint8_t *base = nullptr;
+    if ((rc = noalloc_scratch(dev, &base)) != FSP_OK) return rc;
+    return solve_run(I, ub0, cmax, perm, stats, &P, base, false);
 }

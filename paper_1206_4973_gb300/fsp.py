@@ -25,7 +25,8 @@ _NAMES = {ERR_ARG: "FSP_ERR_ARG", ERR_CUDA: "FSP_ERR_CUDA", ERR_OOM: "FSP_ERR_OO
 # Every symbol include/fsp.h declares.
 EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp_destroy_instance",
            "fsp_instance_tables", "fsp_bound_pool", "fsp_check_status", "fsp_solve_workspace_bytes",
-           "fsp_solve", "fsp_last_error")
+           "fsp_solve", "fsp_solve_noalloc", "fsp_last_error")
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class FspError(RuntimeError):
@@ -83,6 +84,8 @@ def load(path: str | None = None):
         "fsp_solve_workspace_bytes": (i64, [vp, ctypes.POINTER(fsp_options)]),
         "fsp_solve": (ctypes.c_int, [vp, ctypes.c_int32, i32p, i32p, ctypes.POINTER(fsp_stats),
                                      ctypes.POINTER(fsp_options)]),
+        "fsp_solve_noalloc": (ctypes.c_int, [vp, ctypes.c_int32, i32p, i32p, ctypes.POINTER(fsp_stats),
+                                             ctypes.POINTER(fsp_options)]),
         "fsp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -272,6 +275,33 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     res["status"] = rc
     res["cmax"] = int(cmax.value)
     res["perm"] = perm if perm[0] >= 0 else None
+    if trace is not None:
+        res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
+    del keep
+    return res
+
+
+def fsp_solve_noalloc(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,
+                      stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
+                      init_nodes=None, init_count=None, max_iterations: int = 0, out_nodes=None):
+    """fsp_solve through the entry point that allocates no device memory (its
+    scratch is the library's fixed array of NOALLOC_SCRATCH_BYTES).  For
+    callers that cannot allocate during a call; overlapping calls race on the
+    shared array, so serialise them.  Same results as fsp_solve, times 0."""
+    o, keep, trace, out_count = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap,
+                                         schedule, stream, init_nodes, init_count, max_iterations,
+                                         out_nodes, False)
+    perm = np.full(inst.n, -1, np.int32)
+    cmax = ctypes.c_int32(0)
+    st = fsp_stats()
+    rc = _check(load().fsp_solve_noalloc(inst.handle, int(ub0), ctypes.byref(cmax),
+                                         perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(st),
+                                         ctypes.byref(o)))
+    res = {k: int(getattr(st, k)) for k in STATS}
+    res["status"] = rc
+    res["cmax"] = int(cmax.value)
+    res["perm"] = perm if perm[0] >= 0 else None
+    res["stack_left"] = int(out_count.value)
     if trace is not None:
         res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
     del keep
