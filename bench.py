@@ -171,6 +171,35 @@ def cpu_baseline(p, ub, frontier, budget_s=12.0):
                       f"({dt:.1f} s, serial C oracle, one host core)"}
 
 
+SOLVES = (  # (n, m, seed, pool): 0 = tuned while searching
+    (12, 5, 0, 1024), (20, 5, 2, 0), (50, 5, 3, 0), (100, 5, 4, 0), (20, 10, 5, 0))
+SOLVE_BUDGET = 1_000_000_000
+
+
+def solve_times(fsp, budget=SOLVE_BUDGET):
+    """Time to optimality of the exact solves (12x5 from UB = +inf with pool 1024;
+    20x5, 50x5, 100x5, 20x10 from the device NEH makespan with the tuned pool),
+    each stopped by a node budget."""
+    from paper_1206_4973_gb300 import inputs
+    out = []
+    for n, m, seed, pool in SOLVES:
+        p = inputs.instance(n, m, seed)
+        inst = fsp.fsp_create_instance(p)
+        t0 = time.perf_counter()
+        if pool == 0:
+            ub0, perm0 = fsp.fsp_neh(inst)
+        else:
+            ub0, perm0 = fsp.UB_INF, None
+        r = fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=budget)
+        dt = time.perf_counter() - t0
+        out.append({"instance": f"{n}x{m} seed {seed}", "ub0": None if pool else ub0, "cmax": r["cmax"],
+                    "optimal": r["status"] == fsp.OK, "time_s": dt, "nodes_bounded": r["nodes_bounded"],
+                    "iterations": r["iterations"], "pool": r["tuned_pool"] if pool == 0 else pool,
+                    "nodes_per_s": r["nodes_bounded"] / dt})
+        inst.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -323,6 +352,7 @@ def main():
             "bound_pool": bp,
             "phase_ms": {"select": r["select_ms"], "branch_bound": r["bound_ms"], "compact": r["compact_ms"]},
             "wall_s": t_wall,
+            "solves": solve_times(fsp),
         }
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p, ub, frontier)

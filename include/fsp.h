@@ -76,11 +76,16 @@ typedef struct {
     double select_ms;          /* device time in selection (opt->profile)  */
     double bound_ms;           /* device time in branching + bounding      */
     double compact_ms;         /* device time in elimination + compaction  */
+    int64_t tuned_pool;        /* pool size the tuner settled on (pool_size = 0), else the pool */
 } fsp_stats;
 
 /* Options of fsp_solve; fsp_default_options() fills the defaults. */
 typedef struct {
-    int64_t pool_size;      /* children bounded per iteration (Sec. III pool); default 1024 */
+    int64_t pool_size;      /* children bounded per iteration (Sec. III pool); default 1024;
+                               0 = tune it while searching (Sec. III, Algorithm 1): start at
+                               (nodes per CTA) x (SM count), double every tune_window iterations
+                               while it improves the measured nodes bounded per second and stays
+                               within SMs x 2048, then refine around the best and keep it */
     int64_t node_budget;    /* stop (FSP_INCOMPLETE) before an iteration once this many
                                nodes are bounded; 0 = no limit */
     int64_t stack_capacity; /* node records in the device stack; 0 = init_count + n * (pool + n) */
@@ -106,6 +111,10 @@ typedef struct {
     int64_t out_cap;
     int64_t *out_count;     /* host or NULL: records left on the stack */
     int profile;            /* nonzero: fill the *_ms phase times of fsp_stats */
+    int64_t tune_window;    /* iterations per tuning trial (pool_size = 0); 0 = 8 */
+    int64_t *schedule_out;  /* host or NULL: pool size used by each iteration (replayable
+                               through `schedule`), up to schedule_out_cap entries */
+    int64_t schedule_out_cap;
 } fsp_options;
 
 /* Fill *opt with the defaults (pool 1024, no budget, default capacity). */
@@ -196,6 +205,24 @@ int fsp_solve(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp
  *     Serialise them. */
 int fsp_solve_noalloc(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
                       const fsp_options *opt);
+
+/* NEH insertion heuristic on the device (an initial UB; the paper starts
+ * from a given UB and has no counterpart): jobs by decreasing total time
+ * (ties: smaller index first), each inserted at the position of smallest
+ * partial makespan (ties: earliest position).  cmax: host, the makespan;
+ * perm: host, n int32.  Synchronous. */
+int fsp_neh(fsp_instance *inst, int32_t *cmax, int32_t *perm);
+
+/* The pool-size tuner of fsp_solve (pool_size = 0; Sec. III, Algorithm 1)
+ * run against a score function instead of measured throughput: trial k uses
+ * pools_out[k] (host, up to cap entries) and receives score(pool, user).
+ * Starts at nodes_per_cta x sms, doubles while the score improves and the
+ * pool stays <= max_pool, then binary-searches around the best.  Returns the
+ * number of trials (<= 64) and the best pool in *best_out (may be NULL), or
+ * FSP_ERR_ARG.  Pure host code. */
+int64_t fsp_tune_simulate(int64_t nodes_per_cta, int sms, int64_t max_pool,
+                          double (*score)(int64_t pool, void *user), void *user, int64_t *pools_out,
+                          int64_t cap, int64_t *best_out);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fsp_last_error(void);

@@ -18,6 +18,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <mutex>
 
 #include "fsp_bound.cuh"
@@ -61,9 +62,12 @@ struct SolveLayout {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Largest pool the tuner may try: SMs x 2048 resident threads (Sec. III).
+static long long tuner_max_pool(const fsp_instance *I) { return (long long)I->sm_count * 2048; }
+
 static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout *L)
 {
-    long long pool = o->pool_size;
+    long long pool = o->pool_size == 0 ? tuner_max_pool(I) : o->pool_size;
     if (pool < 1 || pool > (1LL << 26)) {
         fsp_set_error("pool_size %lld outside 1..2^26", pool);
         return FSP_ERR_ARG;
@@ -543,6 +547,90 @@ static BranchBoundFn pick_branch_bound(int nw, int mt, bool es)
 
 // ------------------------------------------------------------------ host --
 
+// Pool-size tuning while searching (Sec. III, Algorithm 1), on measured
+// throughput: a trial runs `window` iterations at one pool size and scores
+// nodes bounded per second of wall time.  The first pool is (nodes per CTA)
+// x (SM count); it doubles while the score improves and the pool stays
+// within SMs x 2048; then a binary search between the neighbours of the
+// best pool (halving the interval each round, a few rounds) refines it, and
+// the best pool is kept for the rest of the search.
+struct PoolTuner {
+    bool on = false;
+    int phase = 0;  // 0 doubling, 1 refining, 2 settled
+    long long unit = 256, max_pool = 0, cur = 0, best = 0, lo = 0, hi = 0;
+    double best_eff = -1e300;  // no trial yet
+    long long window = 8, it_in = 0, b0 = 0;
+    double t0 = 0.0;
+    long long cand[2] = {0, 0};
+    int ncand = 0, icand = 0, rounds = 0;
+
+    long long round_unit(long long x) const
+    {
+        x = (x + unit / 2) / unit * unit;
+        if (x < unit) x = unit;
+        if (x > max_pool) x = max_pool;
+        return x;
+    }
+    void start(long long unit_, long long sms, long long maxp, long long win)
+    {
+        on = true;
+        unit = unit_ > 0 ? unit_ : 256;
+        max_pool = maxp / unit * unit;
+        if (max_pool < unit) max_pool = unit;
+        cur = round_unit(unit * sms);
+        best = cur;
+        window = win > 0 ? win : 8;
+    }
+    bool next_candidates()
+    {
+        ncand = icand = 0;
+        if (rounds >= 3 || hi - lo <= 2 * unit) return false;
+        const long long a = round_unit((lo + best) / 2), b = round_unit((best + hi) / 2);
+        if (a != best && a != lo) cand[ncand++] = a;
+        if (b != best && b != hi && b != a) cand[ncand++] = b;
+        rounds++;
+        return ncand > 0;
+    }
+    void decide(double eff)
+    {
+        const long long tried = cur;
+        if (eff > best_eff) { best_eff = eff; best = tried; }
+        if (phase == 0) {
+            if (best == tried && tried * 2 <= max_pool) { cur = tried * 2; return; }
+            phase = 1;
+            lo = round_unit(best / 2);
+            hi = round_unit(best * 2);
+        } else {
+            if (++icand < ncand) { cur = cand[icand]; return; }
+            // shrink the interval around the best of this round
+            if (best < lo || best > hi) { lo = round_unit(best / 2); hi = round_unit(best * 2); }
+            const long long half = (hi - lo) / 4;
+            lo = round_unit(best - half > lo ? best - half : lo);
+            hi = round_unit(best + half < hi ? best + half : hi);
+        }
+        if (next_candidates()) cur = cand[0];
+        else { phase = 2; cur = best; }
+    }
+    // Called before each iteration with the nodes bounded so far.
+    void observe(long long bounded, double now)
+    {
+        if (!on || phase == 2) return;
+        if (it_in == window) {
+            const double dt = now - t0;
+            decide(dt > 0 ? (double)(bounded - b0) / dt : 0.0);
+            it_in = 0;
+        }
+        if (phase == 2) return;
+        if (it_in == 0) { t0 = now; b0 = bounded; }
+        it_in++;
+    }
+};
+
+static double wall_seconds()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 // Options, workspace layout and kernels of one search.
 struct SolvePlan {
     fsp_options o;
@@ -624,6 +712,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
     double t_sel = 0, t_bb = 0, t_cmp = 0;
+    PoolTuner tuner;
     SolveCtl h;
     memset(&h, 0, sizeof h);
     cudaError_t e = cudaSuccess;
@@ -639,6 +728,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     if (prof)
         for (int i = 0; i < 4; ++i) TRY(cudaEventCreate(&pe[i]));
     if (timed) TRY(cudaEventRecord(ev0, st));
+    if (o.pool_size == 0) tuner.start(per_cta, I->sm_count, tuner_max_pool(I), o.tune_window);
     if (I->n == 1) {
         k_solve_single<<<1, 32, 0, st>>>(ws, I->d_p, I->m, ub0);
         TRY(cudaGetLastError());
@@ -680,6 +770,11 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             long long pool = o.pool_size;
             if (o.schedule && o.schedule_len > 0)
                 pool = o.schedule[it < o.schedule_len ? it : o.schedule_len - 1];
+            else if (tuner.on) {
+                tuner.observe(h.cnt[0], wall_seconds());
+                pool = tuner.cur;
+            }
+            if (o.schedule_out && it < o.schedule_out_cap) o.schedule_out[it] = pool;
             const int grid = (int)((pool + I->n + SOLVE_B - 1) / SOLVE_B);
             const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
             if (prof) TRY(cudaEventRecord(pe[0], st));
@@ -726,6 +821,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         stats->leaves = h.cnt[3];
         stats->iterations = h.cnt[4];
         stats->incumbent_updates = h.cnt[5];
+        stats->tuned_pool = tuner.on ? tuner.best : o.pool_size;
         float ms = 0.f;
         if (timed) cudaEventElapsedTime(&ms, ev0, ev1);
         stats->time_ms = ms;
@@ -818,4 +914,25 @@ extern "C" int fsp_solve_noalloc(fsp_instance *I, int32_t ub0, int32_t *cmax, in
     uint8_t *base = nullptr;
     if ((rc = noalloc_scratch(dev, &base)) != FSP_OK) return rc;
     return solve_run(I, ub0, cmax, perm, stats, &P, base, false);
+}
+
+// The tuner's decisions against a caller-supplied score (no GPU involved).
+extern "C" int64_t fsp_tune_simulate(int64_t nodes_per_cta, int sms, int64_t max_pool,
+                                     double (*score)(int64_t pool, void *user), void *user, int64_t *pools_out,
+                                     int64_t cap, int64_t *best_out)
+{
+    if (nodes_per_cta < 1 || sms < 1 || max_pool < 1 || !score || (cap > 0 && !pools_out)) {
+        fsp_set_error("fsp_tune_simulate: invalid argument");
+        return FSP_ERR_ARG;
+    }
+    PoolTuner t;
+    t.start(nodes_per_cta, sms, max_pool, 1);
+    int64_t k = 0;
+    while (t.phase != 2 && k < 64) {
+        if (k < cap) pools_out[k] = t.cur;
+        ++k;
+        t.decide(score(t.cur, user));
+    }
+    if (best_out) *best_out = t.best;
+    return k;
 }

@@ -25,7 +25,8 @@ _NAMES = {ERR_ARG: "FSP_ERR_ARG", ERR_CUDA: "FSP_ERR_CUDA", ERR_OOM: "FSP_ERR_OO
 # Every symbol include/fsp.h declares.
 EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp_destroy_instance",
            "fsp_instance_tables", "fsp_bound_pool", "fsp_check_status", "fsp_solve_workspace_bytes",
-           "fsp_solve", "fsp_solve_noalloc", "fsp_last_error")
+           "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_last_error")
+SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -40,7 +41,8 @@ class fsp_stats(ctypes.Structure):
                 ("nodes_pruned", ctypes.c_int64), ("leaves", ctypes.c_int64),
                 ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64),
                 ("time_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
-                ("bound_ms", ctypes.c_double), ("compact_ms", ctypes.c_double)]
+                ("bound_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
+                ("tuned_pool", ctypes.c_int64)]
 
 
 class fsp_options(ctypes.Structure):
@@ -52,7 +54,8 @@ class fsp_options(ctypes.Structure):
                 ("init_nodes", ctypes.c_void_p), ("init_count", ctypes.c_int64),
                 ("max_iterations", ctypes.c_int64), ("out_nodes", ctypes.c_void_p),
                 ("out_cap", ctypes.c_int64), ("out_count", ctypes.POINTER(ctypes.c_int64)),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("tune_window", ctypes.c_int64),
+                ("schedule_out", ctypes.POINTER(ctypes.c_int64)), ("schedule_out_cap", ctypes.c_int64)]
 
 
 _lib = None
@@ -86,6 +89,9 @@ def load(path: str | None = None):
                                      ctypes.POINTER(fsp_options)]),
         "fsp_solve_noalloc": (ctypes.c_int, [vp, ctypes.c_int32, i32p, i32p, ctypes.POINTER(fsp_stats),
                                              ctypes.POINTER(fsp_options)]),
+        "fsp_neh": (ctypes.c_int, [vp, i32p, i32p]),
+        "fsp_tune_simulate": (i64, [i64, ctypes.c_int, i64, SCORE_FN, vp, ctypes.POINTER(ctypes.c_int64), i64,
+                                    ctypes.POINTER(ctypes.c_int64)]),
         "fsp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -190,12 +196,32 @@ def _ptr(buf):
     return np.asarray(buf).ctypes.data
 
 
+def fsp_neh(inst: Instance):
+    """NEH on the device: (makespan, permutation as int32 array)."""
+    perm = np.zeros(inst.n, np.int32)
+    c = ctypes.c_int32(0)
+    _check(load().fsp_neh(inst.handle, ctypes.byref(c), perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+    return int(c.value), perm
+
+
+def fsp_tune_simulate(nodes_per_cta: int, sms: int, max_pool: int, score):
+    """Run the pool tuner against score(pool) -> float; returns (pools tried, best)."""
+    cb = SCORE_FN(lambda pool, _u: float(score(int(pool))))
+    out = np.zeros(64, np.int64)
+    best = ctypes.c_int64(0)
+    k = _check(int(load().fsp_tune_simulate(int(nodes_per_cta), int(sms), int(max_pool), cb, None,
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 64,
+                                            ctypes.byref(best))))
+    return out[:k].tolist(), int(best.value)
+
+
 def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
              schedule=None, stream=None, init_nodes=None, init_count=None, max_iterations=0,
-             out_nodes=None, profile=False):
+             out_nodes=None, profile=False, tune_window=0, schedule_out=None):
     o = fsp_options()
     load().fsp_default_options(ctypes.byref(o))
     o.pool_size = int(pool_size)
+    o.tune_window = int(tune_window)
     o.node_budget = int(node_budget)
     o.stack_capacity = int(stack_capacity)
     o.max_iterations = int(max_iterations)
@@ -207,6 +233,10 @@ def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, tra
         keep.append(init_nodes)
         o.init_nodes = _ptr(init_nodes)
         o.init_count = int(init_nodes.shape[0] if init_count is None else init_count)
+    if schedule_out is not None:
+        keep.append(schedule_out)
+        o.schedule_out = schedule_out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        o.schedule_out_cap = len(schedule_out)
     out_count = ctypes.c_int64(0)
     keep.append(out_count)
     o.out_count = ctypes.pointer(out_count)
@@ -244,7 +274,7 @@ STATS = ("nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iteration
 def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,
               stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
               workspace=None, init_nodes=None, init_count=None, max_iterations: int = 0,
-              out_nodes=None, profile: bool = False):
+              out_nodes=None, profile: bool = False, tune_window: int = 0, schedule_cap: int = 0):
     """Exact B&B on the device.  The scratch is a torch uint8 tensor (allocated
     here when `workspace` is None).  init_nodes (host array or device tensor of
     records) starts the search from that stack; out_nodes (host array or
@@ -253,9 +283,10 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     and no ub0_perm was given), the counters of STATS, time_ms, the phase
     times when profile is set, stack_left and, if trace_cap > 0, the trace."""
     import torch
+    sched_out = np.zeros(schedule_cap, np.int64) if schedule_cap > 0 else None
     o, keep, trace, out_count = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap,
                                          schedule, stream, init_nodes, init_count, max_iterations,
-                                         out_nodes, profile)
+                                         out_nodes, profile, tune_window, sched_out)
     nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -275,8 +306,11 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     res["status"] = rc
     res["cmax"] = int(cmax.value)
     res["perm"] = perm if perm[0] >= 0 else None
+    res["tuned_pool"] = int(st.tuned_pool)
     if trace is not None:
         res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
+    if sched_out is not None:
+        res["schedule"] = sched_out[: min(res["iterations"], schedule_cap)].copy()
     del keep
     return res
 

@@ -1,0 +1,47 @@
+"""Host logic of the pool-size tuner (Sec. III, Algorithm 1 restated on
+measured throughput), driven by synthetic throughput curves: no GPU."""
+import pytest
+
+from paper_1206_4973_gb300 import build as fsp_build
+from paper_1206_4973_gb300 import fsp
+
+UNIT, SMS, MAXP = 256, 152, 152 * 2048
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    fsp_build.build()
+    fsp.load()
+
+
+def test_doubles_from_sms_blocks_while_improving_then_stops_at_the_limit():
+    pools, best = fsp.fsp_tune_simulate(UNIT, SMS, MAXP, lambda p: float(p))
+    assert pools[0] == UNIT * SMS
+    doubling = [UNIT * SMS * 2**i for i in range(4)]
+    assert pools[:4] == doubling  # 38912 .. 311296 = the device limit
+    assert best == MAXP
+    assert all(UNIT <= q <= MAXP and q % UNIT == 0 for q in pools)
+
+
+@pytest.mark.parametrize("peak", [60000, 100000, 150000, 250000])
+def test_refines_around_a_peaked_curve(peak):
+    score = lambda p: 1.0 / (1.0 + abs(p - peak) / peak)  # noqa: E731
+    pools, best = fsp.fsp_tune_simulate(UNIT, SMS, MAXP, score)
+    tried = set(pools)
+    assert best in tried
+    assert score(best) == max(score(q) for q in tried)
+    assert abs(best - peak) <= 0.35 * peak
+    assert len(pools) <= 16
+
+
+def test_stops_doubling_as_soon_as_the_score_drops():
+    start = UNIT * SMS
+    pools, best = fsp.fsp_tune_simulate(UNIT, SMS, MAXP, lambda p: -float(p))
+    assert pools[:2] == [start, 2 * start]
+    assert 4 * start not in pools
+    assert best < start  # the refinement found smaller pools better
+
+
+def test_rejects_bad_arguments():
+    with pytest.raises(fsp.FspError):
+        fsp.fsp_tune_simulate(0, SMS, MAXP, lambda p: 1.0)
