@@ -77,7 +77,13 @@ typedef struct {
     double bound_ms;           /* device time in branching + bounding      */
     double compact_ms;         /* device time in elimination + compaction  */
     int64_t tuned_pool;        /* pool size the tuner settled on (pool_size = 0), else the pool */
+    int64_t early_pruned;      /* children cut by their predicted pairs alone (order = learned) */
 } fsp_stats;
+
+#define FSP_ORDER_PLAIN 0   /* every child gets its full bound */
+#define FSP_ORDER_LEARNED 1 /* predicted pairs first; survivors get the full bound */
+
+typedef struct fsp_mlp fsp_mlp;
 
 /* Options of fsp_solve; fsp_default_options() fills the defaults. */
 typedef struct {
@@ -115,6 +121,19 @@ typedef struct {
     int64_t *schedule_out;  /* host or NULL: pool size used by each iteration (replayable
                                through `schedule`), up to schedule_out_cap entries */
     int64_t schedule_out_cap;
+    int order;              /* FSP_ORDER_PLAIN (default) or FSP_ORDER_LEARNED: each parent's
+                               features go through `model`; its children first evaluate
+                               only the `topk` best-scored machine pairs, and a child whose
+                               partial bound already reaches the UB of the iteration is cut;
+                               the others get the full bound.  Cuts, survivors, counters and
+                               the incumbent are those of the plain order.  Shapes without a
+                               fast-path kernel run the plain order. */
+    int topk;               /* pairs evaluated first (1..8); 0 = 4 */
+    fsp_mlp *model;         /* network with 2m+1 inputs and m(m-1)/2 outputs (order = learned) */
+    uint8_t *log_nodes;     /* device or NULL: the children of each iteration are appended
+                               here (training data) until log_cap records are stored */
+    int64_t log_cap;
+    int64_t *log_count;     /* host or NULL: records stored in log_nodes */
 } fsp_options;
 
 /* Fill *opt with the defaults (pool 1024, no budget, default capacity). */
@@ -192,7 +211,8 @@ int fsp_solve(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp
  * device that loads the library holds that array until the process exits.
  *   - It allocates nothing (no cudaMalloc, cudaFree, CUDA events or other
  *     allocating call) and therefore reports time_ms and the phase times as
- *     0; opt->profile has no effect.  opt->workspace must be NULL.
+ *     0; opt->profile has no effect.  opt->workspace must be NULL; the
+ *     learned order and node logging are refused (FSP_ERR_ARG).
  *   - The instance's device must be current.  The first call on a device
  *     looks up the array's device address (cudaGetSymbolAddress) and keeps
  *     it; make that first call before any stream capture on that device.
@@ -223,6 +243,44 @@ int fsp_neh(fsp_instance *inst, int32_t *cmax, int32_t *perm);
 int64_t fsp_tune_simulate(int64_t nodes_per_cta, int sms, int64_t max_pool,
                           double (*score)(int64_t pool, void *user), void *user, int64_t *pools_out,
                           int64_t cap, int64_t *best_out);
+
+/* ---------------------------------------------------------------------
+ * Learned pair ordering (not in the paper; see fsp_options.order).  A small MLP scores the m(m-1)/2
+ * machine pairs of a node from its features so that the pair most likely to
+ * give the node's largest two-machine bound is evaluated first.
+ * Features of a node (2m+1 float32): C_k / T, S_k / T for k < m (release
+ * times, remaining work), d / n, with T = float32(total time) / float32(m).
+ * Label: the first pair (k-major) whose two-machine bound is the largest.
+ * Network: x -> relu(x W1 + b1) -> relu(. W2 + b2) -> . W3 + b3; the weights
+ * are used as bf16 (nearest even) and every product accumulates in fp32 on
+ * the tensor cores; inputs, hidden activations and back-propagated errors
+ * are rounded to bf16 where they enter a product.  Parameters (fp32 master
+ * copy, flat): W1 [F][H], b1 [H], W2 [H][H], b2 [H], W3 [H][P], b3 [P].
+ * --------------------------------------------------------------------- */
+
+/* Features (x: device, count x (2m+1) float32) and labels (label: device,
+ * count int32, may be NULL) of count node records (device).  Asynchronous. */
+int fsp_node_features(fsp_instance *inst, const uint8_t *nodes, int64_t count, float *x, int32_t *label,
+                      void *stream);
+
+/* A network with F inputs, H hidden units per layer, P outputs; weights
+ * Glorot-uniform from a hash of (seed, index), biases 0.  Synchronous. */
+int fsp_mlp_create(int in_dim, int hidden, int out_dim, uint64_t seed, fsp_mlp **out);
+void fsp_mlp_destroy(fsp_mlp *mlp);
+int64_t fsp_mlp_num_params(const fsp_mlp *mlp);
+/* Copy the fp32 parameters out (host) / in (host; resets the optimiser). */
+int fsp_mlp_get_params(const fsp_mlp *mlp, float *host);
+int fsp_mlp_set_params(fsp_mlp *mlp, const float *host);
+/* scores (device, B x P) = network(X) for X (device, B x F float32).  Async. */
+int fsp_mlp_forward(fsp_mlp *mlp, const float *X, int64_t B, float *scores, void *stream);
+/* Mean softmax cross-entropy of X (device, B x F) against labels (device, B)
+ * and its gradient: loss (host, may be NULL; synchronises), grad (device or
+ * host, num_params floats, may be NULL). */
+int fsp_mlp_loss_grad(fsp_mlp *mlp, const float *X, const int32_t *labels, int64_t B, float *loss, float *grad,
+                      void *stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss; loss (host, may be NULL). */
+int fsp_mlp_train_step(fsp_mlp *mlp, const float *X, const int32_t *labels, int64_t B, float lr, float *loss,
+                       void *stream);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fsp_last_error(void);

@@ -36,6 +36,7 @@ struct fsp_instance {
     int device;
     int sm_count;
     int smem_optin;  // max dynamic shared memory per block
+    long long total; // sum of all processing times
     int32_t *d_p;    // [n][m] processing times
     int32_t *d_q;    // [n][m] tails: sum of p[j][h] for h > k
     int32_t *d_lag;  // [P][n]
@@ -262,4 +263,32 @@ __device__ __forceinline__ int32_t fsp_node_bound(const DevInst &I, const FspEnt
         }
     }
     return lb;
+}
+
+// Learned-order features of a node record r (2m+1 floats at xo): C_k / T,
+// S_k / T, d / n; also returns the remaining set (U, 8 words), C, S and the
+// smallest tails Q (0x7fffffff when none) for callers that need them.
+__device__ __forceinline__ void fsp_features(const DevInst &I, const uint8_t *r, float T, float *xo, uint32_t *U,
+                                             int32_t *C, int32_t *S, int32_t *Q)
+{
+    const int n = I.n, m = I.m;
+    const int d = r[n] <= n ? r[n] : n;
+    for (int w = 0; w < 8; ++w) U[w] = 0u;
+    for (int k = 0; k < m; ++k) { C[k] = 0; S[k] = 0; Q[k] = 0x7fffffff; }
+    for (int i = 0; i < n; ++i) {
+        const int j = r[i] < n ? r[i] : 0;
+        const int32_t *row = I.p + j * m;
+        if (i < d) {
+            C[0] += row[0];
+            for (int k = 1; k < m; ++k) C[k] = max(C[k], C[k - 1]) + row[k];
+        } else {
+            U[j >> 5] |= 1u << (j & 31);
+            for (int k = 0; k < m; ++k) { S[k] += row[k]; Q[k] = min(Q[k], I.q[j * m + k]); }
+        }
+    }
+    for (int k = 0; k < m; ++k) {
+        xo[k] = __fdiv_rn((float)C[k], T);
+        xo[m + k] = __fdiv_rn((float)S[k], T);
+    }
+    xo[2 * m] = __fdiv_rn((float)d, (float)n);
 }

@@ -134,6 +134,7 @@ extern "C" int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance 
     I->P = m * (m - 1) / 2;
     I->stride = fsp_node_stride(n);
     I->mp = (m % 2 == 0) ? m + 1 : m;
+    for (long i = 0; i < (long)n * m; ++i) I->total += p[i];
     int rc = FSP_OK;
     cudaError_t e;
 #define TRY(call)                                              \

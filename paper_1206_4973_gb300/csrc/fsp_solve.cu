@@ -36,7 +36,9 @@ struct SolveCtl {
     int ub_iter;            // upper bound at the start of the iteration
     int status;             // FSP_ERR_* raised on the device, 0 if none
     int pad0;
-    long long cnt[6];       // bounded, branched, pruned, leaves, iterations, updates
+    long long cnt[7];       // bounded, branched, pruned, leaves, iterations, updates, early cuts
+    long long n_list;       // learned order: children left for the full bound
+    long long early;        // learned order: children cut by their predicted pairs
 };
 
 struct SolveWs {
@@ -52,13 +54,25 @@ struct SolveWs {
     long long trace_cap;
     long long max_children;
     int max_blocks;
+    // learned order
+    int *list;              // children left for the full bound
+    float *px;              // parent features [max_parents][2m+1]
+    float *pscore;          // parent pair scores [max_parents][P]
+    int16_t *topk;          // best pairs of each parent [max_parents][K]
+    long long max_parents;
 };
 
 struct SolveLayout {
-    long long pool_max, max_children, cap, trace_cap;
-    int max_blocks;
+    long long pool_max, max_children, cap, trace_cap, max_parents;
+    int max_blocks, topk;
+    bool learned;
     size_t off_ctl, off_stack, off_children, off_lbs, off_poff, off_blk, off_inc, off_trace, bytes;
+    size_t off_list, off_px, off_pscore, off_topk;
 };
+
+int fsp_mlp_dims(const fsp_mlp *M, int *F, int *H, int *P);
+int fsp_mlp_forward_dev(fsp_mlp *M, const float *X, const long long *Bdev, int64_t Bmax, float *scores,
+                        cudaStream_t st);
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -96,6 +110,30 @@ static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout
     L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 8);
     L->off_inc = off; off = align256(off + 256);
     L->off_trace = off; off = align256(off + (size_t)L->trace_cap * 32);
+    L->learned = o->order == FSP_ORDER_LEARNED;
+    L->topk = o->topk > 0 ? o->topk : 4;
+    L->max_parents = pmax / 2 + 2;  // stacked nodes have depth <= n-2: >= 2 children each
+    L->off_list = L->off_px = L->off_pscore = L->off_topk = off;
+    if (L->learned) {
+        if (o->order != FSP_ORDER_LEARNED || !o->model || L->topk > 8) {
+            fsp_set_error("learned order needs a model and 1 <= topk <= 8");
+            return FSP_ERR_ARG;
+        }
+        int F = 0, H = 0, P = 0;
+        fsp_mlp_dims(o->model, &F, &H, &P);
+        if (F != 2 * I->m + 1 || P != I->P) {
+            fsp_set_error("model has %d inputs and %d outputs; this instance needs %d and %d", F, P,
+                          2 * I->m + 1, I->P);
+            return FSP_ERR_ARG;
+        }
+        L->off_list = off; off = align256(off + (size_t)L->max_children * 4);
+        L->off_px = off; off = align256(off + (size_t)L->max_parents * F * 4);
+        L->off_pscore = off; off = align256(off + (size_t)L->max_parents * P * 4);
+        L->off_topk = off; off = align256(off + (size_t)L->max_parents * L->topk * 2);
+    } else if (o->order != FSP_ORDER_PLAIN) {
+        fsp_set_error("unknown order %d", o->order);
+        return FSP_ERR_ARG;
+    }
     L->bytes = off;
     return FSP_OK;
 }
@@ -141,7 +179,7 @@ __global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long coun
         c->best_key = ~0ull;
         c->ub = ub0;
         c->ub_iter = ub0;
-        for (int i = 0; i < 6; ++i) c->cnt[i] = 0;
+        for (int i = 0; i < 7; ++i) c->cnt[i] = 0;
     }
     if (t >= count) return;
     uint8_t *r = ws.stack + t * stride;
@@ -263,6 +301,8 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
     }
     if (threadIdx.x == 0) {
         ws.poff[np] = (int)running;
+        ctl->n_list = 0;
+        ctl->early = 0;
         ctl->best_key = ~0ull;
         ctl->ub_iter = ctl->ub;
         if (S - np + running > ws.cap) {  // could overflow: keep the stack intact
@@ -449,6 +489,7 @@ __global__ void __launch_bounds__(SOLVE_B) k_push(SolveWs ws, int n, int stride)
             ctl->cnt[3] += leaves;
             ctl->cnt[4] = it + 1;
             if (improved) ctl->cnt[5] += 1;
+            ctl->cnt[6] += ctl->early;
             ctl->ub = ubn;
             ctl->stack_size = s_pop + total;
             if (it < ws.trace_cap) {
@@ -529,6 +570,193 @@ static BranchBound2Fn pick_branch_bound2(int mt, int nv, int nw)
 {
 #define FSP_CASE2(MT_, NV_, NW_) \
     if (mt == MT_ && nv == NV_ && nw == NW_) return &k_branch_bound2<MT_, NV_, NW_>;
+    FSP_SHAPES2(FSP_CASE2)
+#undef FSP_CASE2
+    return nullptr;
+}
+
+// ---------------------------------------------------------- learned order --
+
+// Features of the popped parents (parent t = stack[S - 1 - t]).
+__global__ void k_parent_features(DevInst I, SolveWs ws, float T)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const SolveCtl *ctl = ws.ctl;
+    if (t >= ctl->n_parents) return;
+    const long long S = ctl->s_pop + ctl->n_parents;
+    int32_t C[FSP_MAX_MACHINES], Sr[FSP_MAX_MACHINES], Q[FSP_MAX_MACHINES];
+    uint32_t U[8];
+    fsp_features(I, ws.stack + (S - 1 - t) * I.stride, T, ws.px + t * (2 * I.m + 1), U, C, Sr, Q);
+}
+
+// The K best-scored pairs of each parent, best first (ties: lower pair index).
+__global__ void k_topk(SolveWs ws, int P, int K)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ws.ctl->n_parents) return;
+    const float *sc = ws.pscore + t * P;
+    int16_t *out = ws.topk + t * K;
+    uint32_t taken[FSP_MAX_MACHINES * (FSP_MAX_MACHINES - 1) / 2 / 32 + 1];
+    for (int w = 0; w < (P + 31) / 32; ++w) taken[w] = 0u;
+    for (int j = 0; j < K; ++j) {
+        int best = -1;
+        float bv = 0.f;
+        for (int q = 0; q < P; ++q) {
+            if (taken[q >> 5] & (1u << (q & 31))) continue;
+            const float v = sc[q];
+            if (best < 0 || v > bv) { best = q; bv = v; }
+        }
+        if (best < 0) best = 0;
+        taken[best >> 5] |= 1u << (best & 31);
+        out[j] = (int16_t)best;
+    }
+}
+
+// Phase 1: branch, then evaluate each child's K predicted pairs; a child
+// whose partial bound reaches the iteration's UB is cut (its full bound is
+// at least as large), the others go to the list for the full bound.
+template <int MT, int NV, int NW>
+__global__ void __launch_bounds__(128) k_branch_learned(DevInst I, SolveWs ws, Bound2Smem L, int K)
+{
+    const SolveCtl *ctl = ws.ctl;
+    const long long nch = ctl->n_children;
+    const int B = blockDim.x, tid = threadIdx.x;
+    if ((long long)blockIdx.x * B >= nch) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    FspEntry *ent_s = reinterpret_cast<FspEntry *>(smem + L.ent_off);
+    int2 *pq_s = reinterpret_cast<int2 *>(smem + L.pq_off);
+    int32_t *cs = reinterpret_cast<int32_t *>(smem + L.cs_off);
+    int32_t *sq = reinterpret_cast<int32_t *>(smem + L.sq_off);
+    fsp_stage_pq(I, ent_s, pq_s);
+    const int n = I.n, stride = I.stride;
+    const int np = (int)ctl->n_parents;
+    const long long S = ctl->s_pop + np;
+    const int ub_iter = ctl->ub_iter;
+    const long long c = (long long)blockIdx.x * B + tid;
+    bool listed = false, cut = false;
+    if (c < nch) {
+        const int pi = solve_parent_of(ws.poff, np, c);
+        const int ci = (int)(c - __ldg(ws.poff + pi));
+        FspRec<NV> par, ch;
+        fsp_load_rec(par, ws.stack + (S - 1 - pi) * stride);
+        fsp_make_child(par, n, ci, ch);
+        fsp_store_rec(ch, ws.children + c * stride);
+        uint32_t Um[NW];
+        int32_t C[MT], SQ[MT], lb;
+        bool bad;
+        fsp_prologue<MT, NV, NW>(ch, n, pq_s, I.mp, Um, C, SQ, lb, bad);
+#pragma unroll
+        for (int k = 0; k < MT; ++k) {
+            cs[k * B + tid] = C[k];
+            sq[k * B + tid] = SQ[k];
+        }
+        for (int j = 0; j < K; ++j) {
+            const int kl = __ldg(ws.topk + (long long)pi * K + j);
+            int k = 0, rem = kl;  // pair index -> (k, l), k-major
+            while (rem >= MT - 1 - k) { rem -= MT - 1 - k; ++k; }
+            const int l = k + 1 + rem;
+            const int4 *e = reinterpret_cast<const int4 *>(ent_s + (size_t)kl * n);
+            int32_t E = 0, M = FSP_NEG;
+            for (int pos = 0; pos < n; ++pos) {
+                const int4 t = e[pos];
+                if (fsp_member<NW>(Um, t)) {
+                    M = __viaddmax_s32(E, t.x, M);
+                    E += t.y;
+                }
+            }
+            lb = __viaddmax_s32(sq[l * B + tid], __viaddmax_s32(cs[k * B + tid], M, cs[l * B + tid]), lb);
+        }
+        if (lb >= ub_iter) {
+            ws.lbs[c] = lb;
+            cut = true;
+        } else {
+            listed = true;
+        }
+    }
+    // warp-aggregated append to the list, and the count of cuts
+    const unsigned lm = __ballot_sync(0xffffffffu, listed);
+    const unsigned cm = __ballot_sync(0xffffffffu, cut);
+    const int lane = tid & 31;
+    int base = 0;
+    if (lane == 0 && lm) base = (int)atomicAdd((unsigned long long *)&ws.ctl->n_list, (unsigned long long)__popc(lm));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (listed) ws.list[base + __popc(lm & ((1u << lane) - 1u))] = (int)c;
+    if (lane == 0 && cm) atomicAdd((unsigned long long *)&ws.ctl->early, (unsigned long long)__popc(cm));
+}
+
+// Phase 2: the full bound of the listed children (persistent grid).
+template <int MT, int NV, int NW>
+__global__ void __launch_bounds__(FSP_B2) k_bound_list(DevInst I, SolveWs ws, Bound2Smem L)
+{
+    constexpr int NPT = FSP_NPT;
+    const SolveCtl *ctl = ws.ctl;
+    const long long cnt = ctl->n_list;
+    const int B = blockDim.x, tid = threadIdx.x, SB = B * NPT;
+    if ((long long)blockIdx.x * SB >= cnt) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    FspEntry *ent_s = reinterpret_cast<FspEntry *>(smem + L.ent_off);
+    int2 *pq_s = reinterpret_cast<int2 *>(smem + L.pq_off);
+    int32_t *cs = reinterpret_cast<int32_t *>(smem + L.cs_off);
+    int32_t *sq = reinterpret_cast<int32_t *>(smem + L.sq_off);
+    fsp_stage_pq(I, ent_s, pq_s);
+    const int n = I.n, stride = I.stride;
+    const int ub_iter = ctl->ub_iter;
+    int slot[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) slot[j] = tid + j * B;
+    for (long long base = (long long)blockIdx.x * SB; base < cnt; base += (long long)gridDim.x * SB) {
+        uint32_t Um[NPT][NW];
+        int32_t lb[NPT];
+        int dch[NPT];
+        long long cc[NPT];
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const long long s2 = base + slot[j];
+            cc[j] = s2 < cnt ? (long long)ws.list[s2] : -1;
+            FspRec<NV> r;
+            if (cc[j] >= 0) {
+                fsp_load_rec(r, ws.children + cc[j] * stride);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4 * NV; ++q) r.w[q] = 0u;
+            }
+            dch[j] = (int)fsp_rec_byte_dyn(r, n);
+            int32_t C[MT], SQ[MT];
+            bool bad;
+            fsp_prologue<MT, NV, NW>(r, n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad);
+#pragma unroll
+            for (int k = 0; k < MT; ++k) {
+                cs[k * SB + slot[j]] = C[k];
+                sq[k * SB + slot[j]] = SQ[k];
+            }
+        }
+        fsp_pair_scan<MT, NPT, NW>(n, ent_s, cs, sq, SB, slot, Um, lb);
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            if (cc[j] < 0) continue;
+            ws.lbs[cc[j]] = lb[j];
+            if (dch[j] == n - 1 && lb[j] < ub_iter)
+                atomicMin(&ws.ctl->best_key, ((unsigned long long)(uint32_t)lb[j] << 32) | (unsigned long long)cc[j]);
+        }
+    }
+}
+
+typedef void (*BranchLearnedFn)(DevInst, SolveWs, Bound2Smem, int);
+typedef void (*BoundListFn)(DevInst, SolveWs, Bound2Smem);
+
+static BranchLearnedFn pick_branch_learned(int mt, int nv, int nw)
+{
+#define FSP_CASE2(MT_, NV_, NW_) \
+    if (mt == MT_ && nv == NV_ && nw == NW_) return &k_branch_learned<MT_, NV_, NW_>;
+    FSP_SHAPES2(FSP_CASE2)
+#undef FSP_CASE2
+    return nullptr;
+}
+
+static BoundListFn pick_bound_list(int mt, int nv, int nw)
+{
+#define FSP_CASE2(MT_, NV_, NW_) \
+    if (mt == MT_ && nv == NV_ && nw == NW_) return &k_bound_list<MT_, NV_, NW_>;
     FSP_SHAPES2(FSP_CASE2)
 #undef FSP_CASE2
     return nullptr;
@@ -638,7 +866,10 @@ struct SolvePlan {
     BoundShape shp;
     BranchBoundFn bb;
     BranchBound2Fn bb2;
+    BranchLearnedFn bl;  // learned order (NULL: plain)
+    BoundListFn blist;
     int per_cta;
+    int list_grid;       // persistent grid of the list kernel
 };
 
 static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fsp_options *opt, SolvePlan *P)
@@ -664,6 +895,21 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
                                       (int)shp.L.bytes));
     }
     P->per_cta = shp.ver == 2 ? shp.B * FSP_NPT : shp.B;
+    P->bl = nullptr;
+    P->blist = nullptr;
+    P->list_grid = 0;
+    if (P->L.learned && shp.ver == 2) {  // other shapes run the plain order
+        P->bl = pick_branch_learned(shp.mt, shp.nv, shp.nw);
+        P->blist = pick_bound_list(shp.mt, shp.nv, shp.nw);
+        if (!P->bl || !P->blist) { fsp_set_error("fsp_solve: no learned kernel for this shape"); return FSP_ERR_ARG; }
+        FSP_CUDA(cudaFuncSetAttribute((const void *)P->bl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)shp.L2.bytes));
+        FSP_CUDA(cudaFuncSetAttribute((const void *)P->blist, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)shp.L2.bytes));
+        int per_sm = 0;
+        FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P->blist, shp.B, shp.L2.bytes));
+        P->list_grid = I->sm_count * (per_sm > 0 ? per_sm : 1);
+    }
     if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
         fsp_set_error("fsp_solve: workspace must be 256-byte aligned");
         return FSP_ERR_ARG;
@@ -707,7 +953,14 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     ws.trace_cap = L.trace_cap;
     ws.max_children = L.max_children;
     ws.max_blocks = L.max_blocks;
+    ws.list = (int *)(base + L.off_list);
+    ws.px = (float *)(base + L.off_px);
+    ws.pscore = (float *)(base + L.off_pscore);
+    ws.topk = (int16_t *)(base + L.off_topk);
+    ws.max_parents = L.max_parents;
     const DevInst D = dev_view(I);
+    const float T = (float)I->total / (float)I->m;
+    long long logged = 0;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -764,6 +1017,12 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                                                   : "fsp_solve: device error");
                 break;
             }
+            if (o.log_nodes && it > 0 && logged < o.log_cap && h.n_children > 0) {
+                const long long k = h.n_children < o.log_cap - logged ? h.n_children : o.log_cap - logged;
+                TRY(cudaMemcpyAsync(o.log_nodes + logged * I->stride, ws.children, (size_t)k * I->stride,
+                                    cudaMemcpyDeviceToDevice, st));
+                logged += k;
+            }
             if (h.stack_size == 0) break;
             if (o.node_budget > 0 && h.cnt[0] >= o.node_budget) { rc = FSP_INCOMPLETE; break; }
             if (o.max_iterations > 0 && it >= o.max_iterations) { rc = FSP_INCOMPLETE; break; }
@@ -780,8 +1039,22 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if (prof) TRY(cudaEventRecord(pe[0], st));
             k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool);
             if (prof) TRY(cudaEventRecord(pe[1], st));
-            if (bb2) bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
-            else bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
+            if (P->bl) {
+                const long long npar = pool / 2 + 2;  // stacked nodes have >= 2 children
+                const int F = 2 * I->m + 1;
+                k_parent_features<<<(unsigned)((npar + 127) / 128), 128, 0, st>>>(D, ws, T);
+                int frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
+                if (frc != FSP_OK) { rc = frc; goto out; }
+                k_topk<<<(unsigned)((npar + 127) / 128), 128, 0, st>>>(ws, I->P, L.topk);
+                (void)F;
+                const int grid_l = (int)((pool + I->n + 127) / 128);
+                P->bl<<<grid_l, 128, shp.L2.bytes, st>>>(D, ws, shp.L2, L.topk);
+                P->blist<<<P->list_grid, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
+            } else if (bb2) {
+                bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
+            } else {
+                bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
+            }
             if (prof) TRY(cudaEventRecord(pe[2], st));
             k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
             k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
@@ -809,6 +1082,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             TRY(cudaMemcpy(o.trace, ws.trace, (size_t)rows * 32, cudaMemcpyDeviceToHost));
     }
     if (o.out_count) *o.out_count = h.stack_size;
+    if (o.log_count) *o.log_count = logged;
     if (o.out_nodes && h.stack_size > 0 && h.stack_size <= o.out_cap && I->n > 1)
         TRY(cudaMemcpy(o.out_nodes, ws.stack, (size_t)h.stack_size * I->stride, cudaMemcpyDefault));
     if (stats) {
@@ -822,6 +1096,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         stats->iterations = h.cnt[4];
         stats->incumbent_updates = h.cnt[5];
         stats->tuned_pool = tuner.on ? tuner.best : o.pool_size;
+        stats->early_pruned = h.cnt[6];
         float ms = 0.f;
         if (timed) cudaEventElapsedTime(&ms, ev0, ev1);
         stats->time_ms = ms;
@@ -894,6 +1169,10 @@ extern "C" int fsp_solve_noalloc(fsp_instance *I, int32_t ub0, int32_t *cmax, in
 {
     if (opt && opt->workspace) {
         fsp_set_error("fsp_solve_noalloc: takes no workspace (it uses its fixed scratch)");
+        return FSP_ERR_ARG;
+    }
+    if (opt && (opt->order != FSP_ORDER_PLAIN || opt->log_nodes)) {
+        fsp_set_error("fsp_solve_noalloc: the learned order and node logging are not available without allocation");
         return FSP_ERR_ARG;
     }
     SolvePlan P;

@@ -25,7 +25,10 @@ _NAMES = {ERR_ARG: "FSP_ERR_ARG", ERR_CUDA: "FSP_ERR_CUDA", ERR_OOM: "FSP_ERR_OO
 # Every symbol include/fsp.h declares.
 EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp_destroy_instance",
            "fsp_instance_tables", "fsp_bound_pool", "fsp_check_status", "fsp_solve_workspace_bytes",
-           "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_last_error")
+           "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_node_features",
+           "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
+           "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
+           "fsp_last_error")
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -42,7 +45,7 @@ class fsp_stats(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64),
                 ("time_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
                 ("bound_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
-                ("tuned_pool", ctypes.c_int64)]
+                ("tuned_pool", ctypes.c_int64), ("early_pruned", ctypes.c_int64)]
 
 
 class fsp_options(ctypes.Structure):
@@ -55,7 +58,11 @@ class fsp_options(ctypes.Structure):
                 ("max_iterations", ctypes.c_int64), ("out_nodes", ctypes.c_void_p),
                 ("out_cap", ctypes.c_int64), ("out_count", ctypes.POINTER(ctypes.c_int64)),
                 ("profile", ctypes.c_int), ("tune_window", ctypes.c_int64),
-                ("schedule_out", ctypes.POINTER(ctypes.c_int64)), ("schedule_out_cap", ctypes.c_int64)]
+                ("schedule_out", ctypes.POINTER(ctypes.c_int64)), ("schedule_out_cap", ctypes.c_int64),
+                ("order", ctypes.c_int), ("topk", ctypes.c_int), ("model", ctypes.c_void_p),
+                ("log_nodes", ctypes.c_void_p), ("log_cap", ctypes.c_int64),
+                ("log_count", ctypes.POINTER(ctypes.c_int64))]
+ORDER_PLAIN, ORDER_LEARNED = 0, 1
 
 
 _lib = None
@@ -92,6 +99,17 @@ def load(path: str | None = None):
         "fsp_neh": (ctypes.c_int, [vp, i32p, i32p]),
         "fsp_tune_simulate": (i64, [i64, ctypes.c_int, i64, SCORE_FN, vp, ctypes.POINTER(ctypes.c_int64), i64,
                                     ctypes.POINTER(ctypes.c_int64)]),
+        "fsp_node_features": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
+        "fsp_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                          ctypes.POINTER(vp)]),
+        "fsp_mlp_destroy": (None, [vp]),
+        "fsp_mlp_num_params": (i64, [vp]),
+        "fsp_mlp_get_params": (ctypes.c_int, [vp, vp]),
+        "fsp_mlp_set_params": (ctypes.c_int, [vp, vp]),
+        "fsp_mlp_forward": (ctypes.c_int, [vp, vp, i64, vp, vp]),
+        "fsp_mlp_loss_grad": (ctypes.c_int, [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_float), vp, vp]),
+        "fsp_mlp_train_step": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                              vp]),
         "fsp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -217,11 +235,16 @@ def fsp_tune_simulate(nodes_per_cta: int, sms: int, max_pool: int, score):
 
 def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
              schedule=None, stream=None, init_nodes=None, init_count=None, max_iterations=0,
-             out_nodes=None, profile=False, tune_window=0, schedule_out=None):
+             out_nodes=None, profile=False, tune_window=0, schedule_out=None, model=None, topk=0,
+             log_nodes=None):
     o = fsp_options()
     load().fsp_default_options(ctypes.byref(o))
     o.pool_size = int(pool_size)
     o.tune_window = int(tune_window)
+    if model is not None:
+        o.order = ORDER_LEARNED
+        o.model = model.handle
+        o.topk = int(topk)
     o.node_budget = int(node_budget)
     o.stack_capacity = int(stack_capacity)
     o.max_iterations = int(max_iterations)
@@ -239,6 +262,13 @@ def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, tra
         o.schedule_out_cap = len(schedule_out)
     out_count = ctypes.c_int64(0)
     keep.append(out_count)
+    log_count = ctypes.c_int64(0)
+    keep.append(log_count)
+    o.log_count = ctypes.pointer(log_count)
+    if log_nodes is not None:
+        keep.append(log_nodes)
+        o.log_nodes = log_nodes.data_ptr()
+        o.log_cap = int(log_nodes.shape[0])
     o.out_count = ctypes.pointer(out_count)
     if out_nodes is not None:
         keep.append(out_nodes)
@@ -260,6 +290,7 @@ def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, tra
         o.schedule = s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
         o.schedule_len = len(s)
     o.stream = _stream(stream)
+    o._log_count = log_count
     return o, keep, trace, out_count
 
 
@@ -274,7 +305,8 @@ STATS = ("nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iteration
 def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,
               stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
               workspace=None, init_nodes=None, init_count=None, max_iterations: int = 0,
-              out_nodes=None, profile: bool = False, tune_window: int = 0, schedule_cap: int = 0):
+              out_nodes=None, profile: bool = False, tune_window: int = 0, schedule_cap: int = 0,
+              model=None, topk: int = 0, log_nodes=None):
     """Exact B&B on the device.  The scratch is a torch uint8 tensor (allocated
     here when `workspace` is None).  init_nodes (host array or device tensor of
     records) starts the search from that stack; out_nodes (host array or
@@ -286,7 +318,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     sched_out = np.zeros(schedule_cap, np.int64) if schedule_cap > 0 else None
     o, keep, trace, out_count = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap,
                                          schedule, stream, init_nodes, init_count, max_iterations,
-                                         out_nodes, profile, tune_window, sched_out)
+                                         out_nodes, profile, tune_window, sched_out, model, topk, log_nodes)
     nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -307,6 +339,8 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     res["cmax"] = int(cmax.value)
     res["perm"] = perm if perm[0] >= 0 else None
     res["tuned_pool"] = int(st.tuned_pool)
+    res["early_pruned"] = int(st.early_pruned)
+    res["logged"] = int(o._log_count.value)
     if trace is not None:
         res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
     if sched_out is not None:
@@ -340,3 +374,86 @@ def fsp_solve_noalloc(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, 
         res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
     del keep
     return res
+
+
+# ------------------------------------------------------------ learned order --
+
+def fsp_node_features(inst: Instance, nodes, x=None, label=None, stream=None):
+    """Features (CUDA float32 [count, 2m+1]) and labels (CUDA int32 [count]) of
+    node records (CUDA uint8 [count, stride])."""
+    import torch
+    count = nodes.shape[0]
+    F = 2 * inst.m + 1
+    if x is None:
+        x = torch.empty((count, F), dtype=torch.float32, device=nodes.device)
+    if label is None:
+        label = torch.empty(count, dtype=torch.int32, device=nodes.device)
+    _check(load().fsp_node_features(inst.handle, nodes.data_ptr(), count, x.data_ptr(), label.data_ptr(),
+                                    _stream(stream)))
+    return x, label
+
+
+class Mlp:
+    """Handle of a device-resident pair-scoring network."""
+
+    def __init__(self, in_dim: int, hidden: int, out_dim: int, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().fsp_mlp_create(int(in_dim), int(hidden), int(out_dim), int(seed), ctypes.byref(h)))
+        self.handle, self.F, self.H, self.P = h, in_dim, hidden, out_dim
+
+    def close(self):
+        if self.handle:
+            load().fsp_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def num_params(self) -> int:
+        return int(load().fsp_mlp_num_params(self.handle))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.num_params(), np.float32)
+        _check(load().fsp_mlp_get_params(self.handle, out.ctypes.data))
+        return out
+
+    def set_params(self, w) -> None:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        if w.size != self.num_params():
+            raise ValueError("wrong number of parameters")
+        _check(load().fsp_mlp_set_params(self.handle, w.ctypes.data))
+
+    def split(self, flat):
+        """Flat parameters -> dict W1, b1, W2, b2, W3, b3 (numpy views)."""
+        F, H, P = self.F, self.H, self.P
+        o, out = 0, {}
+        for name, shape in (("W1", (F, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (H, P)),
+                            ("b3", (P,))):
+            size = int(np.prod(shape))
+            out[name] = flat[o:o + size].reshape(shape)
+            o += size
+        return out
+
+    def forward(self, X, scores=None, stream=None):
+        import torch
+        if scores is None:
+            scores = torch.empty((X.shape[0], self.P), dtype=torch.float32, device=X.device)
+        _check(load().fsp_mlp_forward(self.handle, X.data_ptr(), X.shape[0], scores.data_ptr(), _stream(stream)))
+        return scores
+
+    def loss_grad(self, X, y, stream=None):
+        import torch
+        g = torch.empty(self.num_params(), dtype=torch.float32, device=X.device)
+        loss = ctypes.c_float(0)
+        _check(load().fsp_mlp_loss_grad(self.handle, X.data_ptr(), y.data_ptr(), X.shape[0], ctypes.byref(loss),
+                                        g.data_ptr(), _stream(stream)))
+        return float(loss.value), g
+
+    def train_step(self, X, y, lr: float, stream=None) -> float:
+        loss = ctypes.c_float(0)
+        _check(load().fsp_mlp_train_step(self.handle, X.data_ptr(), y.data_ptr(), X.shape[0], float(lr),
+                                         ctypes.byref(loss), _stream(stream)))
+        return float(loss.value)

@@ -1,0 +1,100 @@
+"""GPU parity of the learned-order network with its oracle (oracle/mlp.py):
+features and labels exact, forward scores and gradients within bounds derived
+from bf16 rounding, and training that lowers the loss."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as om
+from paper_1206_4973_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    from paper_1206_4973_gb300 import build, fsp
+    build.build()
+    fsp.load()
+    assert torch.cuda.is_available()
+    return fsp
+
+
+@pytest.mark.parametrize("n,m,seed,count", [(20, 20, 6, 700), (50, 20, 7, 300), (12, 5, 0, 500), (9, 3, 2, 200)])
+def test_features_and_labels_match_oracle(F, n, m, seed, count):
+    import torch
+    p = inputs.instance(n, m, seed)
+    rng = inputs.SplitMix64(seed + 1000)
+    rec = inputs.random_prefix_pool(n, count, rng)
+    rec[::5, n] = 0
+    inst = F.fsp_create_instance(p)
+    x, y = F.fsp_node_features(inst, torch.from_numpy(rec).cuda())
+    x, y = x.cpu().numpy(), y.cpu().numpy()
+    for t in range(count):
+        xo, yo = om.features(p, rec[t, :n], rec[t, n])
+        assert np.array_equal(x[t], xo), t
+        assert y[t] == yo, t
+
+
+def params_dict(mlp, flat):
+    return {k: om.bf16(v) if k.startswith("W") else v.astype(np.float64) for k, v in mlp.split(flat).items()}
+
+
+def product_bound(a, w):
+    """|error| allowed in a @ w: two bf16 ulps (2^-7 relative) on each operand
+    term, plus fp32 accumulation."""
+    return 2.0**-7 * (np.abs(a) @ np.abs(w)) + 1e-5
+
+
+@pytest.mark.parametrize("F_,H,P,B", [(41, 128, 190, 256), (11, 128, 10, 100), (101, 128, 190, 77)])
+def test_forward_matches_oracle(F, F_, H, P, B):
+    import torch
+    mlp = F.Mlp(F_, H, P, seed=3)
+    rng = np.random.default_rng(7)
+    X = rng.uniform(0, 2, size=(B, F_)).astype(np.float32)
+    got = mlp.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    prm = params_dict(mlp, mlp.get_params())
+    a = om.forward(prm, X)
+    tol = product_bound(a["H2"], prm["W3"])
+    assert np.all(np.abs(got - a["L"]) <= tol), float(np.max(np.abs(got - a["L"]) - tol))
+
+
+def test_gradients_match_oracle(F):
+    import torch
+    F_, H, P, B = 41, 128, 190, 64
+    mlp = F.Mlp(F_, H, P, seed=11)
+    rng = np.random.default_rng(13)
+    X = rng.uniform(0, 2, size=(B, F_)).astype(np.float32)
+    y = rng.integers(0, P, size=B).astype(np.int32)
+    loss, g = mlp.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda())
+    g = mlp.split(g.cpu().numpy())
+    prm = params_dict(mlp, mlp.get_params())
+    loss0, g0 = om.loss_and_grads(prm, X, y)
+    assert abs(loss - loss0) <= 1e-3 * max(1.0, abs(loss0))
+    for k in g0:
+        err = np.linalg.norm(g[k] - g0[k]) / max(np.linalg.norm(g0[k]), 1e-12)
+        # a bf16 rounding flip moves one term by 2^-8 relative; allow a few of them
+        assert err <= 2.0**-5, (k, err)
+
+
+def test_training_lowers_the_loss_on_solver_nodes(F):
+    """Random 20 x 20 nodes, their features and labels, 200 Adam steps."""
+    import torch
+    n, m = 20, 20
+    p = inputs.instance(n, m, 6)
+    inst = F.fsp_create_instance(p)
+    rec = inputs.random_prefix_pool(n, 8192, inputs.SplitMix64(66))
+    x, y = F.fsp_node_features(inst, torch.from_numpy(rec).cuda())
+    P = m * (m - 1) // 2
+    mlp = F.Mlp(2 * m + 1, 128, P, seed=1)
+    first = mlp.train_step(x[:1024], y[:1024], lr=2e-3)
+    for it in range(200):
+        s = (it * 1024) % 8192
+        mlp.train_step(x[s:s + 1024], y[s:s + 1024], lr=2e-3)
+    l_end, _ = mlp.loss_grad(x, y)
+    assert l_end < first * 0.8, (first, l_end)
+    # it beats the best constant prediction (the label frequencies): their entropy
+    freq = np.bincount(y.cpu().numpy(), minlength=P) / len(y)
+    entropy = -np.sum(freq[freq > 0] * np.log(freq[freq > 0]))
+    assert l_end < entropy, (l_end, entropy)

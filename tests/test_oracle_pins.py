@@ -356,3 +356,54 @@ def test_init_nodes_are_validated():
     rec[0, 1] = 0  # repeated job
     with pytest.raises(ValueError):
         oracle.solve(p, init_nodes=rec)
+
+
+# ------------------------------------------------ learned-order network ---
+def test_mlp_oracle_gradients_match_finite_differences():
+    """With the bf16 rounding switched off the oracle's analytic gradients
+    equal central differences of its loss (fp64): pins every backward term."""
+    from oracle import mlp as om
+    rng = np.random.default_rng(5)
+    F, H, P, B = 7, 6, 5, 9
+    params = {"W1": rng.normal(size=(F, H)), "b1": rng.normal(size=H) * 0.1, "W2": rng.normal(size=(H, H)),
+              "b2": rng.normal(size=H) * 0.1, "W3": rng.normal(size=(H, P)), "b3": rng.normal(size=P) * 0.1}
+    X = rng.normal(size=(B, F))
+    y = rng.integers(0, P, size=B)
+    _, g = om.loss_and_grads(params, X, y, rnd=om._same)
+    eps = 1e-6
+    for name, w in params.items():
+        num = np.zeros_like(w)
+        for idx in np.ndindex(*w.shape):
+            old = w[idx]
+            w[idx] = old + eps
+            lp = om.loss(params, X, y, rnd=om._same)
+            w[idx] = old - eps
+            lm = om.loss(params, X, y, rnd=om._same)
+            w[idx] = old
+            num[idx] = (lp - lm) / (2 * eps)
+        assert np.allclose(g[name], num, rtol=1e-5, atol=1e-7), name
+
+
+def test_mlp_oracle_bf16_rounding_is_nearest_even():
+    from oracle import mlp as om
+    # 1 + 2^-8 is halfway between 1 and 1 + 2^-7: ties go to the even significand (1)
+    vals = np.array([1.0, 1 + 2**-8, 1 + 3 * 2**-8, -(2 + 2**-7), 1e-3, 65504.0])
+    out = om.bf16(vals)
+    assert out[0] == 1.0 and out[1] == 1.0 and out[2] == 1 + 2**-6 and out[3] == -2.0
+    assert abs(out[4] - 1e-3) <= 1e-3 * 2**-8 and out[5] == 65536.0
+
+
+@pytest.mark.parametrize("n,m,seed", [(7, 4, 171), (9, 6, 172)])
+def test_feature_label_is_the_pair_that_gives_the_bound(n, m, seed):
+    """The pair bounds dominate the one-machine bounds, so the labelled pair's
+    bound is the node's bound; features are C/T, S/T, d/n."""
+    from oracle import mlp as om
+    p = inputs.instance(n, m, seed)
+    T = np.float32(p.sum()) / np.float32(m)
+    for perm, d in rand_nodes(n, 12, seed + 9):
+        x, y = om.features(p, perm, d)
+        lb, lb1, pv = oracle.lb_parts(p, perm, d)
+        assert pv[y] == lb >= lb1 and y == int(np.flatnonzero(pv == pv.max())[0])
+        assert x.dtype == np.float32 and x.shape == (2 * m + 1,)
+        assert np.array_equal(x[:m], (oracle.release_times(p, perm, d).astype(np.float32) / T))
+        assert x[2 * m] == np.float32(d) / np.float32(n)
