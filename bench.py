@@ -200,6 +200,62 @@ def solve_times(fsp, budget=SOLVE_BUDGET):
     return out
 
 
+LEARNED = ((20, 20, 6), (50, 20, 7))
+LEARNED_POOL, LEARNED_BUDGET, LOG_NODES = 2**17, 1_000_000_000, 1_000_000
+
+
+def learned_vs_plain(fsp, budget=LEARNED_BUDGET):
+    """Learned pair order vs the plain order on the 20x20 (seed 6) and 50x20
+    (seed 7) instances: a network trained on 1e6 children a plain search logs,
+    then both orders run the same depth-first search (device NEH UB, pool
+    2^17, same node budget); the search must be identical, only the time may
+    differ."""
+    import torch
+    from paper_1206_4973_gb300 import inputs
+    out = []
+    for n, m, seed in LEARNED:
+        P = m * (m - 1) // 2
+        p = inputs.instance(n, m, seed)
+        inst = fsp.fsp_create_instance(p)
+        ub0, perm0 = fsp.fsp_neh(inst)
+        kw = dict(ub0=ub0, ub0_perm=perm0, pool_size=LEARNED_POOL)
+        t0 = time.perf_counter()
+        log = torch.zeros((LOG_NODES, inst.stride), dtype=torch.uint8, device="cuda")
+        fsp.fsp_solve(inst, node_budget=LOG_NODES, log_nodes=log, **kw)
+        x, y = fsp.fsp_node_features(inst, log)
+        mlp = fsp.Mlp(2 * m + 1, 128, P, seed=seed)
+        perm = torch.randperm(LOG_NODES, generator=torch.Generator().manual_seed(seed)).cuda()
+        x, y = x[perm].contiguous(), y[perm].contiguous()
+        B = 4096
+        steps = 3 * LOG_NODES // B
+        for it in range(steps):
+            s = (it * B) % (LOG_NODES - B)
+            loss = mlp.train_step(x[s:s + B], y[s:s + B], lr=1e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        res, phases = {}, {}
+        for name, extra in (("plain", {}), ("learned", {"model": mlp, "topk": 4})):
+            fsp.fsp_solve(inst, node_budget=budget // 100, **kw, **extra)  # warm-up
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            r = fsp.fsp_solve(inst, node_budget=budget, trace_cap=1, **kw, **extra)
+            res[name] = (r, time.perf_counter() - t1)
+            q = fsp.fsp_solve(inst, node_budget=budget // 20, profile=True, **kw, **extra)  # phase times
+            phases[name] = {k: round(q[k] / max(1, q["iterations"]) * 1e3, 1)
+                            for k in ("select_ms", "infer_ms", "bound_ms", "compact_ms")}
+        (a, ta), (b, tb) = res["plain"], res["learned"]
+        same = all(a[k] == b[k] for k in ("cmax", "nodes_bounded", "nodes_branched", "nodes_pruned", "leaves",
+                                          "iterations", "incumbent_updates", "stack_left"))
+        out.append({"instance": f"{n}x{m} seed {seed}", "nodes_bounded": a["nodes_bounded"],
+                    "plain_nodes_per_s": a["nodes_bounded"] / ta, "learned_nodes_per_s": b["nodes_bounded"] / tb,
+                    "speedup": ta / tb, "identical_search": same, "cmax": a["cmax"],
+                    "optimal": a["status"] == fsp.OK, "early_cut_fraction": b["early_pruned"] / max(1, b["nodes_bounded"]),
+                    "train_s": t_train, "train_final_loss": loss,
+                    "us_per_iteration": phases})
+        inst.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -209,6 +265,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--profile-case", action="store_true",
                     help="one B&B step and one 2^18-node bounding launch, nothing else (for ncu)")
+    ap.add_argument("--profile-learned", action="store_true",
+                    help="three plain then three learned iterations (untrained network) from the 20x20 frontier, for ncu")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_init(args)
@@ -226,6 +284,17 @@ def main():
     fsp_build.build()
     fsp.load()
     dev = torch.device("cuda", local)
+    if args.profile_learned:
+        p1, _, _, fr = workload()
+        inst1 = fsp.fsp_create_instance(p1)
+        ub1, _ = fsp.fsp_neh(inst1)
+        mlp = fsp.Mlp(41, 128, 190, seed=6)
+        fr_dev = torch.from_numpy(fr).to(dev)
+        for order in ({}, {"model": mlp, "topk": 4}):
+            r = fsp.fsp_solve(inst1, ub0=ub1, pool_size=LEARNED_POOL, max_iterations=3, init_nodes=fr_dev, **order)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_learned": True, "bounded": r["nodes_bounded"], "early": r["early_pruned"]}))
+        return
 
     # Rank r runs the same workload on its own GPU (independent replicas).
     p, ub_perm, pool_nodes, frontier = workload()
@@ -353,6 +422,7 @@ def main():
             "phase_ms": {"select": r["select_ms"], "branch_bound": r["bound_ms"], "compact": r["compact_ms"]},
             "wall_s": t_wall,
             "solves": solve_times(fsp),
+            "learned_order": learned_vs_plain(fsp),
         }
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p, ub, frontier)

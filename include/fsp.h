@@ -78,6 +78,7 @@ typedef struct {
     double compact_ms;         /* device time in elimination + compaction  */
     int64_t tuned_pool;        /* pool size the tuner settled on (pool_size = 0), else the pool */
     int64_t early_pruned;      /* children cut by their predicted pairs alone (order = learned) */
+    double infer_ms;           /* device time in the network + top-K (learned, opt->profile) */
 } fsp_stats;
 
 #define FSP_ORDER_PLAIN 0   /* every child gets its full bound */
@@ -281,6 +282,14 @@ int fsp_mlp_loss_grad(fsp_mlp *mlp, const float *X, const int32_t *labels, int64
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) on that loss; loss (host, may be NULL). */
 int fsp_mlp_train_step(fsp_mlp *mlp, const float *X, const int32_t *labels, int64_t B, float lr, float *loss,
                        void *stream);
+
+/* The k (1..8) best-scored machine pairs of each of count node records
+ * (device) by the network (128 hidden units, 2m+1 inputs, m(m-1)/2 outputs,
+ * m in {5, 10, 20}), best first, ties to the lower pair index: topk (device, count x k
+ * int16), pair numbering k-major.  The fused tensor-core kernel the learned
+ * search uses on its parents.  Synchronous. */
+int fsp_pair_order(fsp_instance *inst, fsp_mlp *mlp, const uint8_t *nodes, int64_t count, int k, int16_t *topk,
+                   void *stream);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fsp_last_error(void);

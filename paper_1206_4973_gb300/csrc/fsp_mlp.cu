@@ -159,6 +159,8 @@ struct fsp_mlp {
     int64_t oW1, ob1, oW2, ob2, oW3, ob3;  // offsets in the flat fp32 arrays
     float *w, *g, *m1, *m2;    // master weights, gradients, Adam moments (device)
     bf16_t *wb;                // bf16 weights W1 | W2 | W3 (device)
+    bf16_t *wt;                // transposed bf16 weights W1^T | W2^T | W3^T (n-major, k contiguous)
+    bf16_t *w1p;               // W1^T zero-padded to [H][48] rows (16-byte copies), when F <= 48
     int64_t step;
     int64_t cap;               // rows the activation buffers hold
     bf16_t *h1, *h2;           // [cap][H]
@@ -199,14 +201,23 @@ __global__ void k_mlp_init(float *w, int64_t np, int64_t oW1, int64_t ob1, int64
     w[i] = (float)((2.0 * u - 1.0) * a);
 }
 
-// bf16 copies of W1, W2, W3 (packed back to back).
-__global__ void k_mlp_to_bf16(const float *w, bf16_t *wb, int64_t oW1, int64_t nW1, int64_t oW2, int64_t nW2,
-                              int64_t oW3, int64_t nW3)
+// bf16 copies of W1, W2, W3 (packed back to back), row-major and transposed.
+__global__ void k_mlp_to_bf16(const float *w, bf16_t *wb, bf16_t *wt, bf16_t *w1p, int64_t oW1, int64_t nW1,
+                              int64_t oW2, int64_t nW2, int64_t oW3, int64_t nW3, int F, int H, int P)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nW1) wb[i] = __float2bfloat16_rn(w[oW1 + i]);
-    else if (i < nW1 + nW2) wb[i] = __float2bfloat16_rn(w[oW2 + i - nW1]);
-    else if (i < nW1 + nW2 + nW3) wb[i] = __float2bfloat16_rn(w[oW3 + i - nW1 - nW2]);
+    int64_t o, base;
+    int rows, cols;  // the matrix is rows x cols, row-major
+    if (i < nW1) { o = oW1; base = 0; rows = F; cols = H; }
+    else if (i < nW1 + nW2) { o = oW2; base = nW1; rows = H; cols = H; }
+    else if (i < nW1 + nW2 + nW3) { o = oW3; base = nW1 + nW2; rows = H; cols = P; }
+    else return;
+    const int64_t e = i - base;
+    const bf16_t v = __float2bfloat16_rn(w[o + e]);
+    wb[i] = v;
+    const int r = (int)(e / cols), c = (int)(e - (int64_t)r * cols);
+    wt[base + (int64_t)c * rows + r] = v;
+    if (w1p && i < nW1) w1p[(int64_t)c * 48 + r] = v;  // padding columns stay zero
 }
 
 // Row-wise softmax cross-entropy: loss (summed / B) and dL = (softmax - onehot) / B.
@@ -276,7 +287,8 @@ static int mlp_refresh_bf16(fsp_mlp *M, cudaStream_t st)
 {
     const int64_t nW1 = (int64_t)M->F * M->H, nW2 = (int64_t)M->H * M->H, nW3 = (int64_t)M->H * M->P;
     const int64_t tot = nW1 + nW2 + nW3;
-    k_mlp_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M->w, M->wb, M->oW1, nW1, M->oW2, nW2, M->oW3, nW3);
+    k_mlp_to_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(M->w, M->wb, M->wt, M->w1p, M->oW1, nW1, M->oW2,
+                                                                  nW2, M->oW3, nW3, M->F, M->H, M->P);
     FSP_CUDA(cudaGetLastError());
     return FSP_OK;
 }
@@ -284,7 +296,8 @@ static int mlp_refresh_bf16(fsp_mlp *M, cudaStream_t st)
 static void mlp_free(fsp_mlp *M)
 {
     if (!M) return;
-    cudaFree(M->w); cudaFree(M->g); cudaFree(M->m1); cudaFree(M->m2); cudaFree(M->wb);
+    cudaFree(M->w); cudaFree(M->g); cudaFree(M->m1); cudaFree(M->m2); cudaFree(M->wb); cudaFree(M->wt);
+    cudaFree(M->w1p);
     cudaFree(M->h1); cudaFree(M->h2); cudaFree(M->L); cudaFree(M->dL); cudaFree(M->dz2); cudaFree(M->dz1);
     cudaFree(M->loss);
     free(M);
@@ -311,6 +324,11 @@ extern "C" int fsp_mlp_create(int in_dim, int hidden, int out_dim, uint64_t seed
     TRYM(cudaMalloc(&M->m1, nb));
     TRYM(cudaMalloc(&M->m2, nb));
     TRYM(cudaMalloc(&M->wb, nwb));
+    TRYM(cudaMalloc(&M->wt, nwb));
+    if (M->F <= 48) {
+        TRYM(cudaMalloc(&M->w1p, (size_t)M->H * 48 * sizeof(bf16_t)));
+        TRYM(cudaMemset(M->w1p, 0, (size_t)M->H * 48 * sizeof(bf16_t)));
+    }
     TRYM(cudaMalloc(&M->loss, sizeof(float)));
     TRYM(cudaMemset(M->m1, 0, nb));
     TRYM(cudaMemset(M->m2, 0, nb));
@@ -504,4 +522,296 @@ extern "C" int fsp_node_features(fsp_instance *I, const uint8_t *nodes, int64_t 
                                                                                        x, label);
     FSP_CUDA(cudaGetLastError());
     return FSP_OK;
+}
+
+
+// ------------------------------------------- fused inference for the search --
+// One CTA scores RM parents: their features, the three layers on the tensor
+// cores with the (transposed, bf16) weights and the activations in shared
+// memory, and the K best pairs of each parent.  Each warp owns 16 rows end
+// to end, so layers only need a warp barrier.  H = 128, P <= 192, F <= 48.
+#define FM_RM 64
+#define FM_H 128
+#define FM_KP 48   // padded input width
+#define FM_NP 192  // padded output width
+#define FM_S 8     // row padding (bf16) against bank conflicts
+
+struct FusedSmem {
+    size_t w1, w2, w3, x, h1, h2, sc, pq, bytes;
+};
+
+static inline FusedSmem fused_layout(const fsp_instance *I)
+{
+    FusedSmem L;
+    size_t o = 0;
+    L.w1 = o; o += (size_t)FM_H * (FM_KP + FM_S) * 2;
+    L.w2 = o; o += (size_t)FM_H * (FM_H + FM_S) * 2;
+    L.w3 = o; o += (size_t)FM_NP * (FM_H + FM_S) * 2;
+    L.x = o; o += (size_t)FM_RM * (FM_KP + FM_S) * 2;
+    L.h1 = o; o += (size_t)FM_RM * (FM_H + FM_S) * 2;
+    L.h2 = o; o += (size_t)FM_RM * (FM_H + FM_S) * 2;
+    L.sc = o; o += (size_t)FM_RM * FM_NP * 4;
+    L.pq = o; o += (size_t)I->n * I->mp * 8;
+    L.bytes = o;
+    return L;
+}
+
+// acc[nt][4] += A(16 x K, rows r0.., stride lda) x Bt(n-major, stride ldb) for NT n-tiles of 8.
+template <int NT, int K>
+__device__ __forceinline__ void fm_warp_gemm(const bf16_t *A, int lda, const bf16_t *Bt, int ldb, float (&acc)[NT][4],
+                                             int g, int t)
+{
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t *>(A + g * lda + k0 + 2 * t);
+        a[1] = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + k0 + 2 * t);
+        a[2] = *reinterpret_cast<const uint32_t *>(A + g * lda + k0 + 8 + 2 * t);
+        a[3] = *reinterpret_cast<const uint32_t *>(A + (g + 8) * lda + k0 + 8 + 2 * t);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+            const bf16_t *b = Bt + (nt * 8 + g) * ldb + k0 + 2 * t;
+            const uint32_t b0 = *reinterpret_cast<const uint32_t *>(b);
+            const uint32_t b1 = *reinterpret_cast<const uint32_t *>(b + 8);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(acc[nt][0]), "+f"(acc[nt][1]), "+f"(acc[nt][2]), "+f"(acc[nt][3])
+                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+        }
+    }
+}
+
+__device__ __forceinline__ void fm_cp16(void *dst_smem, const void *src_gmem)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src_gmem));
+}
+
+// Features of one node with the machine count known at compile time: the
+// arrays stay in registers and p / tails come from shared memory ({p, q}
+// rows of odd stride mp).  Same values as fsp_features.
+template <int MT>
+__device__ __forceinline__ void fm_features(const uint8_t *r, int n, const int2 *pq, int mp, float T, float *x)
+{
+    const int d = r[n] <= n ? r[n] : n;
+    int32_t C[MT], S[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) { C[k] = 0; S[k] = 0; }
+    for (int i = 0; i < n; ++i) {
+        const int j = r[i] < n ? r[i] : 0;
+        const int2 *row = pq + j * mp;
+        if (i < d) {
+            C[0] += row[0].x;
+#pragma unroll
+            for (int k = 1; k < MT; ++k) C[k] = max(C[k], C[k - 1]) + row[k].x;
+        } else {
+#pragma unroll
+            for (int k = 0; k < MT; ++k) S[k] += row[k].x;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < MT; ++k) {
+        x[k] = __fdiv_rn((float)C[k], T);
+        x[MT + k] = __fdiv_rn((float)S[k], T);
+    }
+    x[2 * MT] = __fdiv_rn((float)d, (float)n);
+}
+
+template <int MT>
+__global__ void __launch_bounds__(128) k_mlp_topk_parents(DevInst I, const uint8_t *__restrict__ stack,
+                                                          const long long *__restrict__ s_pop,
+                                                          const long long *__restrict__ n_parents, float T,
+                                                          const bf16_t *__restrict__ wt, const bf16_t *__restrict__ w1p,
+                                                          const float *__restrict__ w, int64_t ob1, int64_t ob2,
+                                                          int64_t ob3, int F, int P, int K,
+                                                          int16_t *__restrict__ topk, FusedSmem L, int reversed)
+{
+    const long long np = *n_parents;
+    if ((long long)blockIdx.x * FM_RM >= np) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16_t *w1s = reinterpret_cast<bf16_t *>(smem + L.w1);
+    bf16_t *w2s = reinterpret_cast<bf16_t *>(smem + L.w2);
+    bf16_t *w3s = reinterpret_cast<bf16_t *>(smem + L.w3);
+    bf16_t *xs = reinterpret_cast<bf16_t *>(smem + L.x);
+    bf16_t *h1s = reinterpret_cast<bf16_t *>(smem + L.h1);
+    bf16_t *h2s = reinterpret_cast<bf16_t *>(smem + L.h2);
+    float *scs = reinterpret_cast<float *>(smem + L.sc);
+    int2 *pq = reinterpret_cast<int2 *>(smem + L.pq);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
+    const bf16_t zero = __float2bfloat16_rn(0.f);
+    // weights, once per CTA, as 16-byte asynchronous copies:
+    // W1^T [H][48] (zero-padded copy), W2^T [H][H], W3^T [P][H] -> [FM_NP][H]
+    const bf16_t *g2 = wt + (size_t)F * FM_H, *g3 = g2 + (size_t)FM_H * FM_H;
+    for (int e = tid; e < FM_H * (FM_KP / 8); e += 128) {
+        const int nn = e / (FM_KP / 8), q = e - nn * (FM_KP / 8);
+        fm_cp16(w1s + nn * (FM_KP + FM_S) + q * 8, w1p + (size_t)nn * FM_KP + q * 8);
+    }
+    for (int e = tid; e < FM_H * 16; e += 128) {
+        const int nn = e >> 4, q = e & 15;
+        fm_cp16(w2s + nn * (FM_H + FM_S) + q * 8, g2 + (size_t)nn * FM_H + q * 8);
+    }
+    for (int e = tid; e < FM_NP * 16; e += 128) {
+        const int nn = e >> 4, q = e & 15;
+        if (nn < P) fm_cp16(w3s + nn * (FM_H + FM_S) + q * 8, g3 + (size_t)nn * FM_H + q * 8);
+        else *reinterpret_cast<uint4 *>(w3s + nn * (FM_H + FM_S) + q * 8) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+    for (int i = tid; i < I.n * MT; i += 128) {
+        const int j = i / MT, k = i - j * MT;
+        pq[j * I.mp + k] = make_int2(__ldg(I.p + i), __ldg(I.q + i));
+    }
+    asm volatile("cp.async.wait_all;\n" ::);
+    (void)zero;
+    const long long S = *s_pop + np;
+    for (long long r0 = (long long)blockIdx.x * FM_RM; r0 < np; r0 += (long long)gridDim.x * FM_RM) {
+        __syncthreads();  // weights staged / previous block's rows consumed
+        if (tid < FM_RM) {  // features of the block's parents (the search's sit top down)
+            const long long r = r0 + tid;
+            float x[2 * MT + 1];
+            if (r < np) {
+                const long long at = reversed ? S - 1 - r : r;
+                fm_features<MT>(stack + at * I.stride, I.n, pq, I.mp, T, x);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 2 * MT + 1; ++k) x[k] = 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < FM_KP; ++k)
+                xs[tid * (FM_KP + FM_S) + k] = k < 2 * MT + 1 ? __float2bfloat16_rn(x[k]) : __float2bfloat16_rn(0.f);
+        }
+        __syncthreads();
+        const int rw = warp * 16;  // the warp's rows within the block
+        {
+            float acc[16][4];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+            fm_warp_gemm<16, FM_KP>(xs + rw * (FM_KP + FM_S), FM_KP + FM_S, w1s, FM_KP + FM_S, acc, g, t);
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int row = rw + g + (c >= 2 ? 8 : 0), col = nt * 8 + 2 * t + (c & 1);
+                    h1s[row * (FM_H + FM_S) + col] = __float2bfloat16_rn(fmaxf(acc[nt][c] + w[ob1 + col], 0.f));
+                }
+        }
+        __syncwarp();
+        {
+            float acc[16][4];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+            fm_warp_gemm<16, FM_H>(h1s + rw * (FM_H + FM_S), FM_H + FM_S, w2s, FM_H + FM_S, acc, g, t);
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int row = rw + g + (c >= 2 ? 8 : 0), col = nt * 8 + 2 * t + (c & 1);
+                    h2s[row * (FM_H + FM_S) + col] = __float2bfloat16_rn(fmaxf(acc[nt][c] + w[ob2 + col], 0.f));
+                }
+        }
+        __syncwarp();
+        for (int half = 0; half < 2; ++half) {  // 192 output columns in two passes of 96
+            float acc[12][4];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+            fm_warp_gemm<12, FM_H>(h2s + rw * (FM_H + FM_S), FM_H + FM_S, w3s + half * 96 * (FM_H + FM_S),
+                                   FM_H + FM_S, acc, g, t);
+#pragma unroll
+            for (int nt = 0; nt < 12; ++nt)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int row = rw + g + (c >= 2 ? 8 : 0), col = half * 96 + nt * 8 + 2 * t + (c & 1);
+                    scs[row * FM_NP + col] = col < P ? acc[nt][c] + w[ob3 + col] : -INFINITY;
+                }
+        }
+        __syncwarp();
+        // top-K of the warp's 16 rows, one row at a time across the warp:
+        // best first, ties to the lower pair index
+        for (int rr = 0; rr < 16; ++rr) {
+            const long long r = r0 + rw + rr;
+            if (r >= np) break;
+            const float *sc = scs + (rw + rr) * FM_NP;
+            uint32_t taken = 0u;  // bit q: pair lane + 32 q already chosen
+            for (int j = 0; j < K; ++j) {
+                float bv = -INFINITY;
+                int bq = 0x7fffffff;
+#pragma unroll
+                for (int q = 0; q < FM_NP / 32; ++q) {
+                    const int pq = lane + 32 * q;
+                    const float v = sc[pq];
+                    if (pq < P && !(taken & (1u << q)) && (v > bv || (v == bv && pq < bq))) { bv = v; bq = pq; }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
+                    if (ov > bv || (ov == bv && oq < bq)) { bv = ov; bq = oq; }
+                }
+                if (bq == 0x7fffffff) bq = 0;
+                if ((bq & 31) == lane) taken |= 1u << (bq >> 5);
+                if (lane == 0) topk[r * K + j] = (int16_t)bq;
+            }
+        }
+    }
+}
+
+// Scores and top-K pairs of the search's parents with the fused kernel
+// (H = 128, P <= 192, F <= 48); returns FSP_ERR_ARG for other shapes.
+static int mlp_topk(fsp_mlp *M, const fsp_instance *I, const uint8_t *stack, const long long *s_pop,
+                    const long long *n_parents, long long max_parents, int K, int16_t *topk, cudaStream_t st,
+                    int reversed)
+{
+    if (M->H != FM_H || M->P > FM_NP || M->F > FM_KP || !M->w1p) return FSP_ERR_ARG;
+    typedef void (*Fn)(DevInst, const uint8_t *, const long long *, const long long *, float, const bf16_t *,
+                       const bf16_t *, const float *, int64_t, int64_t, int64_t, int, int, int, int16_t *, FusedSmem,
+                       int);
+    Fn fn = I->m == 5 ? (Fn)k_mlp_topk_parents<5> : I->m == 10 ? (Fn)k_mlp_topk_parents<10>
+          : I->m == 20 ? (Fn)k_mlp_topk_parents<20> : nullptr;
+    if (!fn) return FSP_ERR_ARG;
+    const FusedSmem L = fused_layout(I);
+    if ((int)L.bytes > I->smem_optin) return FSP_ERR_ARG;
+    FSP_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes));
+    const float T = (float)I->total / (float)I->m;
+    unsigned grid = (unsigned)((max_parents + FM_RM - 1) / FM_RM);
+    if (grid > (unsigned)I->sm_count) grid = (unsigned)I->sm_count;  // persistent: weights staged once per CTA
+    fn<<<grid, 128, L.bytes, st>>>(dev_view(I), stack, s_pop, n_parents, T, M->wt, M->w1p, M->w, M->ob1, M->ob2,
+                                   M->ob3, M->F, M->P, K, topk, L, reversed);
+    FSP_CUDA(cudaGetLastError());
+    return FSP_OK;
+}
+
+int fsp_mlp_topk_parents(fsp_mlp *M, const fsp_instance *I, const uint8_t *stack, const long long *s_pop,
+                         const long long *n_parents, long long max_parents, int K, int16_t *topk, cudaStream_t st)
+{
+    return mlp_topk(M, I, stack, s_pop, n_parents, max_parents, K, topk, st, 1);
+}
+
+extern "C" int fsp_pair_order(fsp_instance *I, fsp_mlp *M, const uint8_t *nodes, int64_t count, int k,
+                              int16_t *topk, void *stream)
+{
+    if (!I || !M || count < 0 || k < 1 || k > 8 || (count > 0 && (!nodes || !topk))) {
+        fsp_set_error("fsp_pair_order: invalid argument");
+        return FSP_ERR_ARG;
+    }
+    if (M->F != 2 * I->m + 1 || M->P != I->P) {
+        fsp_set_error("fsp_pair_order: the network does not match the instance");
+        return FSP_ERR_ARG;
+    }
+    if (M->H != FM_H || (I->m != 5 && I->m != 10 && I->m != 20)) {
+        fsp_set_error("fsp_pair_order: needs 128 hidden units and m in {5, 10, 20}");
+        return FSP_ERR_ARG;
+    }
+    if (count == 0) return FSP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    long long *d = nullptr;  // {0, count}: the records play the stack with nothing below them
+    const long long h[2] = {0, count};
+    FSP_CUDA(cudaMalloc(&d, sizeof h));
+    cudaError_t e = cudaMemcpyAsync(d, h, sizeof h, cudaMemcpyHostToDevice, st);
+    int rc = e == cudaSuccess ? mlp_topk(M, I, nodes, d, d + 1, count, k, topk, st, 0) : fsp_cuda_fail(e, "fsp_pair_order");
+    if (rc == FSP_OK) {
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = fsp_cuda_fail(e, "fsp_pair_order");
+    }
+    cudaFree(d);
+    return rc;
 }

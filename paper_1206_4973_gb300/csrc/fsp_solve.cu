@@ -71,6 +71,8 @@ struct SolveLayout {
 };
 
 int fsp_mlp_dims(const fsp_mlp *M, int *F, int *H, int *P);
+int fsp_mlp_topk_parents(fsp_mlp *M, const fsp_instance *I, const uint8_t *stack, const long long *s_pop,
+                         const long long *n_parents, long long max_parents, int K, int16_t *topk, cudaStream_t st);
 int fsp_mlp_forward_dev(fsp_mlp *M, const float *X, const long long *Bdev, int64_t Bmax, float *scores,
                         cudaStream_t st);
 
@@ -616,7 +618,7 @@ __global__ void k_topk(SolveWs ws, int P, int K)
 // whose partial bound reaches the iteration's UB is cut (its full bound is
 // at least as large), the others go to the list for the full bound.
 template <int MT, int NV, int NW>
-__global__ void __launch_bounds__(128) k_branch_learned(DevInst I, SolveWs ws, Bound2Smem L, int K)
+__global__ void __launch_bounds__(256) k_branch_learned(DevInst I, SolveWs ws, Bound2Smem L, int K)
 {
     const SolveCtl *ctl = ws.ctl;
     const long long nch = ctl->n_children;
@@ -963,8 +965,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     long long logged = 0;
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
-    double t_sel = 0, t_bb = 0, t_cmp = 0;
+    cudaEvent_t pe[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    double t_sel = 0, t_bb = 0, t_cmp = 0, t_inf = 0;
     PoolTuner tuner;
     SolveCtl h;
     memset(&h, 0, sizeof h);
@@ -979,7 +981,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         TRY(cudaEventCreate(&ev1));
     }
     if (prof)
-        for (int i = 0; i < 4; ++i) TRY(cudaEventCreate(&pe[i]));
+        for (int i = 0; i < 5; ++i) TRY(cudaEventCreate(&pe[i]));
     if (timed) TRY(cudaEventRecord(ev0, st));
     if (o.pool_size == 0) tuner.start(per_cta, I->sm_count, tuner_max_pool(I), o.tune_window);
     if (I->n == 1) {
@@ -1008,6 +1010,11 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 t_sel += a;
                 t_bb += b;
                 t_cmp += c;
+                if (P->bl) {
+                    float d = 0;
+                    TRY(cudaEventElapsedTime(&d, pe[1], pe[4]));
+                    t_inf += d;
+                }
             }
             if (h.status != 0) {
                 rc = h.status;
@@ -1041,14 +1048,17 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if (prof) TRY(cudaEventRecord(pe[1], st));
             if (P->bl) {
                 const long long npar = pool / 2 + 2;  // stacked nodes have >= 2 children
-                const int F = 2 * I->m + 1;
-                k_parent_features<<<(unsigned)((npar + 127) / 128), 128, 0, st>>>(D, ws, T);
-                int frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
+                int frc = fsp_mlp_topk_parents(o.model, I, ws.stack, &ws.ctl->s_pop, &ws.ctl->n_parents, npar,
+                                               L.topk, ws.topk, st);
+                if (frc == FSP_ERR_ARG) {  // network shape without the fused kernel
+                    k_parent_features<<<(unsigned)((npar + 127) / 128), 128, 0, st>>>(D, ws, T);
+                    frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
+                    if (frc == FSP_OK) k_topk<<<(unsigned)((npar + 127) / 128), 128, 0, st>>>(ws, I->P, L.topk);
+                }
                 if (frc != FSP_OK) { rc = frc; goto out; }
-                k_topk<<<(unsigned)((npar + 127) / 128), 128, 0, st>>>(ws, I->P, L.topk);
-                (void)F;
-                const int grid_l = (int)((pool + I->n + 127) / 128);
-                P->bl<<<grid_l, 128, shp.L2.bytes, st>>>(D, ws, shp.L2, L.topk);
+                if (prof) TRY(cudaEventRecord(pe[4], st));
+                const int grid_l = (int)((pool + I->n + 255) / 256);
+                P->bl<<<grid_l, 256, shp.L2.bytes, st>>>(D, ws, shp.L2, L.topk);
                 P->blist<<<P->list_grid, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             } else if (bb2) {
                 bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
@@ -1097,6 +1107,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         stats->incumbent_updates = h.cnt[5];
         stats->tuned_pool = tuner.on ? tuner.best : o.pool_size;
         stats->early_pruned = h.cnt[6];
+        stats->infer_ms = t_inf;
         float ms = 0.f;
         if (timed) cudaEventElapsedTime(&ms, ev0, ev1);
         stats->time_ms = ms;
@@ -1105,7 +1116,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
 out:
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 5; ++i)
         if (pe[i]) cudaEventDestroy(pe[i]);
     return rc;
 }

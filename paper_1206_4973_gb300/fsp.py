@@ -28,7 +28,7 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp
            "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_node_features",
            "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
-           "fsp_last_error")
+           "fsp_pair_order", "fsp_last_error")
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -45,7 +45,7 @@ class fsp_stats(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64),
                 ("time_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
                 ("bound_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
-                ("tuned_pool", ctypes.c_int64), ("early_pruned", ctypes.c_int64)]
+                ("tuned_pool", ctypes.c_int64), ("early_pruned", ctypes.c_int64), ("infer_ms", ctypes.c_double)]
 
 
 class fsp_options(ctypes.Structure):
@@ -110,6 +110,7 @@ def load(path: str | None = None):
         "fsp_mlp_loss_grad": (ctypes.c_int, [vp, vp, vp, i64, ctypes.POINTER(ctypes.c_float), vp, vp]),
         "fsp_mlp_train_step": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
                                               vp]),
+        "fsp_pair_order": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_int, vp, vp]),
         "fsp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -332,7 +333,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
                                  perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(st),
                                  ctypes.byref(o)))
     res = {k: int(getattr(st, k)) for k in STATS}
-    for k in ("time_ms", "select_ms", "bound_ms", "compact_ms"):
+    for k in ("time_ms", "select_ms", "bound_ms", "compact_ms", "infer_ms"):
         res[k] = float(getattr(st, k))
     res["stack_left"] = int(out_count.value)
     res["status"] = rc
@@ -457,3 +458,13 @@ class Mlp:
         _check(load().fsp_mlp_train_step(self.handle, X.data_ptr(), y.data_ptr(), X.shape[0], float(lr),
                                          ctypes.byref(loss), _stream(stream)))
         return float(loss.value)
+
+
+def fsp_pair_order(inst: Instance, mlp: Mlp, nodes, k: int = 4, stream=None):
+    """The k best-scored pairs of each node record (CUDA uint8 [count, stride]):
+    CUDA int16 [count, k], best first."""
+    import torch
+    out = torch.empty((nodes.shape[0], k), dtype=torch.int16, device=nodes.device)
+    _check(load().fsp_pair_order(inst.handle, mlp.handle, nodes.data_ptr(), nodes.shape[0], int(k), out.data_ptr(),
+                                 _stream(stream)))
+    return out

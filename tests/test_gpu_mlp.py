@@ -98,3 +98,28 @@ def test_training_lowers_the_loss_on_solver_nodes(F):
     freq = np.bincount(y.cpu().numpy(), minlength=P) / len(y)
     entropy = -np.sum(freq[freq > 0] * np.log(freq[freq > 0]))
     assert l_end < entropy, (l_end, entropy)
+
+
+@pytest.mark.parametrize("m,n,k", [(20, 20, 4), (10, 15, 8), (5, 12, 2), (20, 50, 1)])
+def test_fused_pair_order_matches_oracle_scores(F, m, n, k):
+    """The fused kernel's top-k pairs are the oracle's best-scored pairs, up to
+    scores closer than the forward tolerance."""
+    import torch
+    P = m * (m - 1) // 2
+    p = inputs.instance(n, m, 40 + m)
+    inst = F.fsp_create_instance(p)
+    rec = inputs.random_prefix_pool(n, 300, inputs.SplitMix64(77 + m))
+    mlp = F.Mlp(2 * m + 1, 128, P, seed=m)
+    top = F.fsp_pair_order(inst, mlp, torch.from_numpy(rec).cuda(), k=k).cpu().numpy()
+    prm = params_dict(mlp, mlp.get_params())
+    X = np.stack([om.features(p, rec[t, :n], rec[t, n])[0] for t in range(len(rec))])
+    a = om.forward(prm, X)
+    tol = product_bound(a["H2"], prm["W3"]) * 2 + 1e-4
+    for t in range(len(rec)):
+        sc = a["L"][t]
+        assert len(set(top[t].tolist())) == k and top[t].max() < P
+        kth = np.sort(sc)[::-1][k - 1]
+        for j, q in enumerate(top[t]):
+            assert sc[q] >= kth - tol[t].max(), (t, j, q)
+        # best first
+        assert np.all(np.diff(sc[top[t]]) <= tol[t].max())
