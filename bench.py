@@ -256,6 +256,55 @@ def learned_vs_plain(fsp, budget=LEARNED_BUDGET):
     return out
 
 
+BATCH_COUNT, BATCH_BUDGET, LEFTOVER_BUDGET = 256, 5_000_000, 200_000_000
+
+
+def batch_solve(fsp):
+    """256 instances of mixed shape (n in {12,15,20,50}, m in {5,10}, seeds
+    100-355): pools tuned per shape, one persistent launch (CUDA graph) with a
+    per-instance node budget, then the instances the budget stopped are
+    finished by the full-GPU search from the batch's incumbent."""
+    import torch
+    from paper_1206_4973_gb300 import inputs
+    shapes = inputs.batch_shapes(BATCH_COUNT, first_seed=100)
+    instances = [inputs.instance(n, m, sd) for n, m, sd in shapes]
+    t0 = time.perf_counter()
+    pools = fsp.fsp_batch_tune_pools(instances, probe_budget=100_000)
+    t_tune = time.perf_counter() - t0
+    B = fsp.Batch(instances, pools, np.full(BATCH_COUNT, BATCH_BUDGET, np.int64))
+    B.run()
+    B.results()  # warm-up launch
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    B.run()
+    res = B.results()
+    t_batch = time.perf_counter() - t1
+    solved = sum(r["status"] == fsp.OK for r in res)
+    nodes = sum(r["nodes_bounded"] for r in res)
+    t2 = time.perf_counter()
+    finished, left_nodes = 0, 0
+    for i, r in enumerate(res):
+        if r["status"] == fsp.OK:
+            continue
+        inst = fsp.fsp_create_instance(instances[i])
+        q = fsp.fsp_solve(inst, ub0=r["cmax"], ub0_perm=r["perm"], pool_size=0, node_budget=LEFTOVER_BUDGET)
+        finished += q["status"] == fsp.OK
+        left_nodes += q["nodes_bounded"]
+        inst.close()
+    t_left = time.perf_counter() - t2
+    per_shape = {}
+    for (n, m, _), r in zip(shapes, res):
+        d = per_shape.setdefault(f"{n}x{m}", {"pool": r["pool"], "solved": 0, "count": 0})
+        d["count"] += 1
+        d["solved"] += r["status"] == fsp.OK
+    B.close()
+    return {"instances": BATCH_COUNT, "solved_in_batch": solved, "batch_s": t_batch,
+            "batch_nodes_bounded": nodes, "batch_nodes_per_s": nodes / t_batch, "tune_s": t_tune,
+            "node_budget_per_instance": BATCH_BUDGET, "leftovers": BATCH_COUNT - solved,
+            "leftovers_finished": finished, "leftover_s": t_left, "leftover_nodes": left_nodes,
+            "leftover_budget_each": LEFTOVER_BUDGET, "per_shape": per_shape}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -423,6 +472,7 @@ def main():
             "wall_s": t_wall,
             "solves": solve_times(fsp),
             "learned_order": learned_vs_plain(fsp),
+            "batch": batch_solve(fsp),
         }
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p, ub, frontier)

@@ -291,6 +291,48 @@ int fsp_mlp_train_step(fsp_mlp *mlp, const float *X, const int32_t *labels, int6
 int fsp_pair_order(fsp_instance *inst, fsp_mlp *mlp, const uint8_t *nodes, int64_t count, int k, int16_t *topk,
                    void *stream);
 
+/* ---------------------------------------------------------------------
+ * Batches: many instances of mixed shape solved in one persistent launch
+ * (not in the paper, which solves one instance at a time).  Each CTA takes
+ * the next instance from a device work queue and runs the whole search of
+ * fsp_solve for it (same rules, the instance's own pool size) with the
+ * NEH makespan as initial UB (or the given ub0), under the instance's node
+ * budget.  The queue reset and the kernel are one CUDA graph, captured at
+ * creation and replayed by fsp_batch_run.  Shapes: m = 5 or 10 with
+ * n <= 15, 16..31 or 48..63 jobs, and m = 20 with 16..31 jobs.
+ * --------------------------------------------------------------------- */
+typedef struct fsp_batch fsp_batch;
+
+typedef struct {
+    int32_t cmax;              /* best makespan found (the optimum when status = FSP_OK) */
+    int32_t status;            /* FSP_OK, FSP_INCOMPLETE (budget) or FSP_ERR_CAPACITY */
+    int64_t nodes_bounded, nodes_branched, nodes_pruned, leaves, iterations, incumbent_updates;
+    int64_t pool;              /* pool size used */
+} fsp_batch_result;
+
+/* count instances: shapes (host, count x {n, m}), p_flat (host, the n*m
+ * job-major times of each instance back to back), pools (host, count, 1..4096),
+ * budgets (host or NULL: nodes; 0 = none), ub0 (host or NULL: initial UB;
+ * 0 = NEH).  Uploads the data, sizes the per-CTA scratch and captures the
+ * graph.  Errors: FSP_ERR_ARG (shape, pool or time out of range), FSP_ERR_OOM,
+ * FSP_ERR_CUDA. */
+int fsp_batch_create(int count, const int32_t *shapes, const int32_t *p_flat, const int64_t *pools,
+                     const int64_t *budgets, const int32_t *ub0, fsp_batch **out);
+void fsp_batch_destroy(fsp_batch *batch);
+/* Launch the captured graph on `stream` (asynchronous); every launch solves
+ * all instances again from scratch. */
+int fsp_batch_run(fsp_batch *batch, void *stream);
+/* Synchronise `stream` and copy the results out: res (host, count), perms
+ * (host or NULL, count x 255 int32: instance i's permutation at i*255; valid
+ * when the UB came from NEH or improved). */
+int fsp_batch_results(fsp_batch *batch, fsp_batch_result *res, int32_t *perms, void *stream);
+/* Pool size per shape on measured throughput (Algorithm 1's purpose, per
+ * shape): up to 8 instances of each shape run with pools 128 .. 4096 under
+ * probe_budget nodes each; the fastest pool (nodes bounded per second) is
+ * written for every instance of that shape to pools_out (host, count). */
+int fsp_batch_tune_pools(int count, const int32_t *shapes, const int32_t *p_flat, int64_t probe_budget,
+                         int64_t *pools_out);
+
 /* Message of the last error on this thread ("" if none). */
 const char *fsp_last_error(void);
 

@@ -81,7 +81,7 @@ struct BoundSmem {
     size_t ent_off, p_off, q_off, rec_off, cs_off, sq_off, ss_off, bytes;
 };
 
-static inline size_t fsp_align16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ static inline size_t fsp_align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 static inline BoundSmem bound_smem_layout(const fsp_instance *I, int B, bool ent_smem, int MT)
 {

@@ -1,0 +1,63 @@
+// fsp_solve.cuh -- state shared by the search kernels (fsp_solve.cu) and the
+// learned-order kernels (fsp_learned.cu).
+#pragma once
+
+#include "fsp_bound.cuh"
+
+struct SolveCtl {
+    long long stack_size;   // records on the stack
+    long long s_pop;        // stack size after this iteration's pops
+    long long n_parents;
+    long long n_children;
+    unsigned long long best_key;  // (bound << 32) | child index of the best leaf
+    int ub;                 // current upper bound
+    int ub_iter;            // upper bound at the start of the iteration
+    int status;             // FSP_ERR_* raised on the device, 0 if none
+    int pad0;
+    long long cnt[7];       // bounded, branched, pruned, leaves, iterations, updates, early cuts
+    long long n_list;       // learned order: children left for the full bound
+    long long early;        // learned order: children cut by their predicted pairs
+};
+
+struct SolveWs {
+    SolveCtl *ctl;
+    uint8_t *stack;
+    long long cap;
+    uint8_t *children;
+    int32_t *lbs;
+    int *poff;              // first child of each popped parent; poff[np] = children
+    int *blk;
+    uint8_t *inc;
+    long long *trace;
+    long long trace_cap;
+    long long max_children;
+    int max_blocks;
+    // learned order
+    int *list;              // children left for the full bound
+    float *px;              // parent features [max_parents][2m+1]
+    float *pscore;          // parent pair scores [max_parents][P]
+    int16_t *topk;          // best pairs of each parent [max_parents][K]
+    long long max_parents;
+};
+
+
+// Parent of child c: the last p with poff[p] <= c (poff increasing, poff[0] = 0).
+__device__ __forceinline__ int solve_parent_of(const int *__restrict__ poff, int np, long long c)
+{
+    int lo = 0, hi = np;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)__ldg(poff + mid) <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+typedef void (*BranchLearnedFn)(DevInst, SolveWs, Bound2Smem, int);
+typedef void (*BoundListFn)(DevInst, SolveWs, Bound2Smem);
+
+// Learned-order kernels (fsp_learned.cu).
+BranchLearnedFn pick_branch_learned(int mt, int nv, int nw);
+BoundListFn pick_bound_list(int mt, int nv, int nw);
+void launch_parent_features(const DevInst &D, const SolveWs &ws, float T, long long npar, cudaStream_t st);
+void launch_topk(const SolveWs &ws, int P, int K, long long npar, cudaStream_t st);

@@ -28,7 +28,8 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp
            "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_node_features",
            "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
-           "fsp_pair_order", "fsp_last_error")
+           "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
+           "fsp_batch_tune_pools", "fsp_last_error")
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -111,6 +112,11 @@ def load(path: str | None = None):
         "fsp_mlp_train_step": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
                                               vp]),
         "fsp_pair_order": (ctypes.c_int, [vp, vp, vp, i64, ctypes.c_int, vp, vp]),
+        "fsp_batch_create": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+        "fsp_batch_destroy": (None, [vp]),
+        "fsp_batch_run": (ctypes.c_int, [vp, vp]),
+        "fsp_batch_results": (ctypes.c_int, [vp, vp, vp, vp]),
+        "fsp_batch_tune_pools": (ctypes.c_int, [ctypes.c_int, vp, vp, i64, vp]),
         "fsp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -468,3 +474,68 @@ def fsp_pair_order(inst: Instance, mlp: Mlp, nodes, k: int = 4, stream=None):
     _check(load().fsp_pair_order(inst.handle, mlp.handle, nodes.data_ptr(), nodes.shape[0], int(k), out.data_ptr(),
                                  _stream(stream)))
     return out
+
+
+# ------------------------------------------------------------------ batches --
+
+class fsp_batch_result(ctypes.Structure):
+    _fields_ = [("cmax", ctypes.c_int32), ("status", ctypes.c_int32), ("nodes_bounded", ctypes.c_int64),
+                ("nodes_branched", ctypes.c_int64), ("nodes_pruned", ctypes.c_int64), ("leaves", ctypes.c_int64),
+                ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64), ("pool", ctypes.c_int64)]
+
+
+def _flatten(instances):
+    shapes = np.array([[p.shape[0], p.shape[1]] for p in instances], dtype=np.int32)
+    flat = np.concatenate([np.ascontiguousarray(p, dtype=np.int32).ravel() for p in instances]).astype(np.int32)
+    return shapes, flat
+
+
+def fsp_batch_tune_pools(instances, probe_budget: int = 200000):
+    """Pool size per shape on measured throughput; returns one pool per instance."""
+    shapes, flat = _flatten(instances)
+    out = np.zeros(len(instances), np.int64)
+    _check(load().fsp_batch_tune_pools(len(instances), shapes.ctypes.data, flat.ctypes.data, int(probe_budget),
+                                       out.ctypes.data))
+    return out
+
+
+class Batch:
+    """Instances of mixed shape solved in one persistent launch (a CUDA graph)."""
+
+    def __init__(self, instances, pools, budgets=None, ub0=None):
+        shapes, flat = _flatten(instances)
+        self.count = len(instances)
+        self.n = shapes[:, 0].copy()
+        pools = np.ascontiguousarray(pools, dtype=np.int64)
+        bud = None if budgets is None else np.ascontiguousarray(budgets, dtype=np.int64)
+        ub = None if ub0 is None else np.ascontiguousarray(ub0, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(load().fsp_batch_create(self.count, shapes.ctypes.data, flat.ctypes.data, pools.ctypes.data,
+                                       None if bud is None else bud.ctypes.data,
+                                       None if ub is None else ub.ctypes.data, ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().fsp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, stream=None):
+        _check(load().fsp_batch_run(self.handle, _stream(stream)))
+
+    def results(self, stream=None):
+        res = (fsp_batch_result * self.count)()
+        perms = np.zeros((self.count, 255), np.int32)
+        _check(load().fsp_batch_results(self.handle, ctypes.addressof(res), perms.ctypes.data, _stream(stream)))
+        out = []
+        for i in range(self.count):
+            r = {k: int(getattr(res[i], k)) for k, _ in fsp_batch_result._fields_}
+            r["perm"] = perms[i, : self.n[i]].copy()
+            out.append(r)
+        return out

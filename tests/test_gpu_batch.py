@@ -1,0 +1,95 @@
+"""The batched solver (one persistent launch, device work queue, CUDA graph)
+against the oracle: every instance's search equals oracle.solve with the
+same pool, the NEH UB and the same node budget, bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_4973_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    from paper_1206_4973_gb300 import build, fsp
+    build.build()
+    fsp.load()
+    assert torch.cuda.is_available()
+    return fsp
+
+
+def check(F, instances, res, pools, budgets, ub0=None):
+    for i, (p, r) in enumerate(zip(instances, res)):
+        if ub0 is None:
+            u, perm0 = oracle.neh(p)
+        else:
+            u, perm0 = int(ub0[i]), None
+        ref = oracle.solve(p, ub0=u, pool=int(pools[i]), node_budget=int(budgets[i]), ub0_perm=perm0)
+        assert r["status"] == ref["status"], i
+        assert r["cmax"] == ref["cmax"], i
+        for k in ("bounded", "branched", "pruned", "leaves", "iterations", "incumbent_updates"):
+            key = "nodes_" + k if k in ("bounded", "branched", "pruned") else k
+            assert r[key] == ref[k], (i, k)
+        if ref["perm"] is not None:
+            assert list(r["perm"]) == list(ref["perm"]), i
+
+
+def test_mixed_batch_matches_oracle(F):
+    shapes = inputs.batch_shapes(24, first_seed=100)
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    pools = np.array([(64, 256, 1024)[i % 3] for i in range(24)], np.int64)
+    budgets = np.full(24, 20000, np.int64)
+    B = F.Batch(instances, pools, budgets)
+    B.run()
+    res = B.results()
+    check(F, instances, res, pools, budgets)
+    B.run()  # the graph replays: same results
+    again = B.results()
+    for a, b in zip(again, res):
+        assert {k: v for k, v in a.items() if k != "perm"} == {k: v for k, v in b.items() if k != "perm"}
+        assert list(a["perm"]) == list(b["perm"])
+
+
+def test_small_instances_solved_to_optimality(F):
+    shapes = [(9, 5, 1), (10, 10, 2), (16, 20, 3), (12, 5, 4), (7, 5, 5), (11, 10, 6), (2, 5, 7), (3, 10, 8)]
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    pools = np.array([32, 512, 100, 1, 7, 2048, 4, 16], np.int64)
+    budgets = np.array([0, 0, 30000, 0, 0, 0, 0, 0], np.int64)
+    B = F.Batch(instances, pools, budgets)
+    B.run()
+    res = B.results()
+    check(F, instances, res, pools, budgets)
+    for p, r in zip(instances, res):
+        if p.shape[0] <= 9:
+            assert r["cmax"] == oracle.bruteforce(p)[0] and r["status"] == F.OK
+
+
+def test_given_upper_bounds(F):
+    instances = [inputs.instance(10, 5, 31), inputs.instance(12, 10, 32)]
+    ub0 = np.array([oracle.neh(p)[0] + 5 for p in instances], np.int32)
+    pools, budgets = np.array([128, 64], np.int64), np.array([0, 5000], np.int64)
+    B = F.Batch(instances, pools, budgets, ub0=ub0)
+    B.run()
+    check(F, instances, B.results(), pools, budgets, ub0=ub0)
+
+
+def test_rejects_unsupported_shapes(F):
+    with pytest.raises(F.FspError):
+        F.Batch([inputs.instance(10, 7, 1)], [64])
+    with pytest.raises(F.FspError):
+        F.Batch([inputs.instance(40, 5, 1)], [64])
+    with pytest.raises(F.FspError):
+        F.Batch([inputs.instance(10, 5, 1)], [5000])
+
+
+def test_pool_tuning_per_shape(F):
+    shapes = inputs.batch_shapes(16, first_seed=100)
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    pools = F.fsp_batch_tune_pools(instances, probe_budget=20000)
+    assert set(pools.tolist()) <= {128, 256, 512, 1024, 2048, 4096}
+    for i in range(16):
+        for j in range(16):
+            if shapes[i][:2] == shapes[j][:2]:
+                assert pools[i] == pools[j]
