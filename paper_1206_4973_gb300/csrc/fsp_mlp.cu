@@ -530,14 +530,15 @@ extern "C" int fsp_node_features(fsp_instance *I, const uint8_t *nodes, int64_t 
 // cores with the (transposed, bf16) weights and the activations in shared
 // memory, and the K best pairs of each parent.  Each warp owns 16 rows end
 // to end, so layers only need a warp barrier.  H = 128, P <= 192, F <= 48.
-#define FM_RM 64
+#define FM_RM 128  // rows (parents) per CTA round: 8 warps x 16
+#define FM_T 256   // threads
 #define FM_H 128
 #define FM_KP 48   // padded input width
 #define FM_NP 192  // padded output width
 #define FM_S 8     // row padding (bf16) against bank conflicts
 
 struct FusedSmem {
-    size_t w1, w2, w3, x, h1, h2, sc, pq, bytes;
+    size_t w1, w2, w3, act, sc, pq, bytes;
 };
 
 static inline FusedSmem fused_layout(const fsp_instance *I)
@@ -547,14 +548,13 @@ static inline FusedSmem fused_layout(const fsp_instance *I)
     L.w1 = o; o += (size_t)FM_H * (FM_KP + FM_S) * 2;
     L.w2 = o; o += (size_t)FM_H * (FM_H + FM_S) * 2;
     L.w3 = o; o += (size_t)FM_NP * (FM_H + FM_S) * 2;
-    L.x = o; o += (size_t)FM_RM * (FM_KP + FM_S) * 2;
-    L.h1 = o; o += (size_t)FM_RM * (FM_H + FM_S) * 2;
-    L.h2 = o; o += (size_t)FM_RM * (FM_H + FM_S) * 2;
-    L.sc = o; o += (size_t)FM_RM * FM_NP * 4;
+    L.act = o; o += (size_t)FM_RM * (FM_H + FM_S) * 2;  // X, then H1, then H2 (per warp strip)
+    L.sc = o; o += (size_t)FM_RM * FM_NP * 2;            // scores (bf16) for the top-K
     L.pq = o; o += (size_t)I->n * I->mp * 8;
     L.bytes = o;
     return L;
 }
+
 
 // acc[nt][4] += A(16 x K, rows r0.., stride lda) x Bt(n-major, stride ldb) for NT n-tiles of 8.
 template <int NT, int K>
@@ -619,13 +619,13 @@ __device__ __forceinline__ void fm_features(const uint8_t *r, int n, const int2 
 }
 
 template <int MT>
-__global__ void __launch_bounds__(128) k_mlp_topk_parents(DevInst I, const uint8_t *__restrict__ stack,
-                                                          const long long *__restrict__ s_pop,
-                                                          const long long *__restrict__ n_parents, float T,
-                                                          const bf16_t *__restrict__ wt, const bf16_t *__restrict__ w1p,
-                                                          const float *__restrict__ w, int64_t ob1, int64_t ob2,
-                                                          int64_t ob3, int F, int P, int K,
-                                                          int16_t *__restrict__ topk, FusedSmem L, int reversed)
+__global__ void __launch_bounds__(FM_T) k_mlp_topk_parents(DevInst I, const uint8_t *__restrict__ stack,
+                                                           const long long *__restrict__ s_pop,
+                                                           const long long *__restrict__ n_parents, float T,
+                                                           const bf16_t *__restrict__ wt, const bf16_t *__restrict__ w1p,
+                                                           const float *__restrict__ w, int64_t ob1, int64_t ob2,
+                                                           int64_t ob3, int F, int P, int K,
+                                                           int16_t *__restrict__ topk, FusedSmem L, int reversed)
 {
     const long long np = *n_parents;
     if ((long long)blockIdx.x * FM_RM >= np) return;
@@ -633,113 +633,118 @@ __global__ void __launch_bounds__(128) k_mlp_topk_parents(DevInst I, const uint8
     bf16_t *w1s = reinterpret_cast<bf16_t *>(smem + L.w1);
     bf16_t *w2s = reinterpret_cast<bf16_t *>(smem + L.w2);
     bf16_t *w3s = reinterpret_cast<bf16_t *>(smem + L.w3);
-    bf16_t *xs = reinterpret_cast<bf16_t *>(smem + L.x);
-    bf16_t *h1s = reinterpret_cast<bf16_t *>(smem + L.h1);
-    bf16_t *h2s = reinterpret_cast<bf16_t *>(smem + L.h2);
-    float *scs = reinterpret_cast<float *>(smem + L.sc);
+    bf16_t *act = reinterpret_cast<bf16_t *>(smem + L.act);
     int2 *pq = reinterpret_cast<int2 *>(smem + L.pq);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, g = lane >> 2, t = lane & 3;
-    const bf16_t zero = __float2bfloat16_rn(0.f);
-    // weights, once per CTA, as 16-byte asynchronous copies:
-    // W1^T [H][48] (zero-padded copy), W2^T [H][H], W3^T [P][H] -> [FM_NP][H]
+    // weights, once per CTA, as 16-byte asynchronous copies
     const bf16_t *g2 = wt + (size_t)F * FM_H, *g3 = g2 + (size_t)FM_H * FM_H;
-    for (int e = tid; e < FM_H * (FM_KP / 8); e += 128) {
+    for (int e = tid; e < FM_H * (FM_KP / 8); e += FM_T) {
         const int nn = e / (FM_KP / 8), q = e - nn * (FM_KP / 8);
         fm_cp16(w1s + nn * (FM_KP + FM_S) + q * 8, w1p + (size_t)nn * FM_KP + q * 8);
     }
-    for (int e = tid; e < FM_H * 16; e += 128) {
+    for (int e = tid; e < FM_H * 16; e += FM_T) {
         const int nn = e >> 4, q = e & 15;
         fm_cp16(w2s + nn * (FM_H + FM_S) + q * 8, g2 + (size_t)nn * FM_H + q * 8);
     }
-    for (int e = tid; e < FM_NP * 16; e += 128) {
+    for (int e = tid; e < FM_NP * 16; e += FM_T) {
         const int nn = e >> 4, q = e & 15;
         if (nn < P) fm_cp16(w3s + nn * (FM_H + FM_S) + q * 8, g3 + (size_t)nn * FM_H + q * 8);
         else *reinterpret_cast<uint4 *>(w3s + nn * (FM_H + FM_S) + q * 8) = make_uint4(0u, 0u, 0u, 0u);
     }
     asm volatile("cp.async.commit_group;\n" ::);
-    for (int i = tid; i < I.n * MT; i += 128) {
+    for (int i = tid; i < I.n * MT; i += FM_T) {
         const int j = i / MT, k = i - j * MT;
         pq[j * I.mp + k] = make_int2(__ldg(I.p + i), __ldg(I.q + i));
     }
     asm volatile("cp.async.wait_all;\n" ::);
-    (void)zero;
     const long long S = *s_pop + np;
+    const int rw = warp * 16;                        // the warp's rows
+    bf16_t *strip = act + rw * (FM_H + FM_S);        // X (stride FM_KP + FM_S), then H1, H2 (stride FM_H + FM_S)
     for (long long r0 = (long long)blockIdx.x * FM_RM; r0 < np; r0 += (long long)gridDim.x * FM_RM) {
-        __syncthreads();  // weights staged / previous block's rows consumed
-        if (tid < FM_RM) {  // features of the block's parents (the search's sit top down)
+        __syncthreads();  // weights staged / previous rows done
+        if (tid < FM_RM) {  // features: thread tid -> row tid (warp tid/16's strip, row tid%16)
             const long long r = r0 + tid;
             float x[2 * MT + 1];
             if (r < np) {
-                const long long at = reversed ? S - 1 - r : r;
+                const long long at = reversed ? S - 1 - r : r;  // the search's parents sit top down
                 fm_features<MT>(stack + at * I.stride, I.n, pq, I.mp, T, x);
             } else {
 #pragma unroll
                 for (int k = 0; k < 2 * MT + 1; ++k) x[k] = 0.f;
             }
+            bf16_t *xr = act + (tid >> 4) * 16 * (FM_H + FM_S) + (tid & 15) * (FM_KP + FM_S);
 #pragma unroll
-            for (int k = 0; k < FM_KP; ++k)
-                xs[tid * (FM_KP + FM_S) + k] = k < 2 * MT + 1 ? __float2bfloat16_rn(x[k]) : __float2bfloat16_rn(0.f);
+            for (int k = 0; k < FM_KP; ++k) xr[k] = __float2bfloat16_rn(k < 2 * MT + 1 ? x[k] : 0.f);
         }
         __syncthreads();
-        const int rw = warp * 16;  // the warp's rows within the block
-        {
+        {   // layer 1: X (16 x 48) -> H1 (16 x 128), written over the strip once X is consumed
             float acc[16][4];
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-            fm_warp_gemm<16, FM_KP>(xs + rw * (FM_KP + FM_S), FM_KP + FM_S, w1s, FM_KP + FM_S, acc, g, t);
+            fm_warp_gemm<16, FM_KP>(strip, FM_KP + FM_S, w1s, FM_KP + FM_S, acc, g, t);
+            __syncwarp();
 #pragma unroll
             for (int nt = 0; nt < 16; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int row = rw + g + (c >= 2 ? 8 : 0), col = nt * 8 + 2 * t + (c & 1);
-                    h1s[row * (FM_H + FM_S) + col] = __float2bfloat16_rn(fmaxf(acc[nt][c] + w[ob1 + col], 0.f));
+                    const int row = g + (c >= 2 ? 8 : 0), col = nt * 8 + 2 * t + (c & 1);
+                    strip[row * (FM_H + FM_S) + col] = __float2bfloat16_rn(fmaxf(acc[nt][c] + w[ob1 + col], 0.f));
                 }
         }
         __syncwarp();
-        {
+        {   // layer 2: H1 -> H2 in place
             float acc[16][4];
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-            fm_warp_gemm<16, FM_H>(h1s + rw * (FM_H + FM_S), FM_H + FM_S, w2s, FM_H + FM_S, acc, g, t);
+            fm_warp_gemm<16, FM_H>(strip, FM_H + FM_S, w2s, FM_H + FM_S, acc, g, t);
+            __syncwarp();
 #pragma unroll
             for (int nt = 0; nt < 16; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int row = rw + g + (c >= 2 ? 8 : 0), col = nt * 8 + 2 * t + (c & 1);
-                    h2s[row * (FM_H + FM_S) + col] = __float2bfloat16_rn(fmaxf(acc[nt][c] + w[ob2 + col], 0.f));
+                    const int row = g + (c >= 2 ? 8 : 0), col = nt * 8 + 2 * t + (c & 1);
+                    strip[row * (FM_H + FM_S) + col] = __float2bfloat16_rn(fmaxf(acc[nt][c] + w[ob2 + col], 0.f));
                 }
         }
         __syncwarp();
-        for (int half = 0; half < 2; ++half) {  // 192 output columns in two passes of 96
+        // layer 3 in two halves of 96 columns, scores to shared memory (bf16: the
+        // order is a heuristic, the search stays exact whatever it is)
+        bf16_t *sc = reinterpret_cast<bf16_t *>(smem + L.sc) + rw * FM_NP;
+        for (int half = 0; half < 2; ++half) {
             float acc[12][4];
 #pragma unroll
             for (int i = 0; i < 12; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-            fm_warp_gemm<12, FM_H>(h2s + rw * (FM_H + FM_S), FM_H + FM_S, w3s + half * 96 * (FM_H + FM_S),
-                                   FM_H + FM_S, acc, g, t);
+            fm_warp_gemm<12, FM_H>(strip, FM_H + FM_S, w3s + half * 96 * (FM_H + FM_S), FM_H + FM_S, acc, g, t);
 #pragma unroll
             for (int nt = 0; nt < 12; ++nt)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    const int row = rw + g + (c >= 2 ? 8 : 0), col = half * 96 + nt * 8 + 2 * t + (c & 1);
-                    scs[row * FM_NP + col] = col < P ? acc[nt][c] + w[ob3 + col] : -INFINITY;
+                    const int row = g + (c >= 2 ? 8 : 0), col = half * 96 + nt * 8 + 2 * t + (c & 1);
+                    sc[row * FM_NP + col] = __float2bfloat16_rn(col < P ? acc[nt][c] + w[ob3 + col] : -INFINITY);
                 }
         }
         __syncwarp();
-        // top-K of the warp's 16 rows, one row at a time across the warp:
-        // best first, ties to the lower pair index
+        // top-K of each of the warp's 16 rows across the warp: best first, ties to the lower pair
+#pragma unroll 1
         for (int rr = 0; rr < 16; ++rr) {
             const long long r = r0 + rw + rr;
             if (r >= np) break;
-            const float *sc = scs + (rw + rr) * FM_NP;
-            uint32_t taken = 0u;  // bit q: pair lane + 32 q already chosen
+            const bf16_t *sr = sc + rr * FM_NP;
+            float v6[FM_NP / 32];
+#pragma unroll
+            for (int q = 0; q < FM_NP / 32; ++q) v6[q] = lane + 32 * q < P ? __bfloat162float(sr[lane + 32 * q]) : -INFINITY;
+            uint32_t taken = 0u;
+#pragma unroll 1
             for (int j = 0; j < K; ++j) {
                 float bv = -INFINITY;
                 int bq = 0x7fffffff;
 #pragma unroll
                 for (int q = 0; q < FM_NP / 32; ++q) {
-                    const int pq = lane + 32 * q;
-                    const float v = sc[pq];
-                    if (pq < P && !(taken & (1u << q)) && (v > bv || (v == bv && pq < bq))) { bv = v; bq = pq; }
+                    const int pq2 = lane + 32 * q;
+                    if (pq2 < P && !(taken & (1u << q)) && (v6[q] > bv || (v6[q] == bv && pq2 < bq))) {
+                        bv = v6[q];
+                        bq = pq2;
+                    }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
@@ -774,8 +779,8 @@ static int mlp_topk(fsp_mlp *M, const fsp_instance *I, const uint8_t *stack, con
     const float T = (float)I->total / (float)I->m;
     unsigned grid = (unsigned)((max_parents + FM_RM - 1) / FM_RM);
     if (grid > (unsigned)I->sm_count) grid = (unsigned)I->sm_count;  // persistent: weights staged once per CTA
-    fn<<<grid, 128, L.bytes, st>>>(dev_view(I), stack, s_pop, n_parents, T, M->wt, M->w1p, M->w, M->ob1, M->ob2,
-                                   M->ob3, M->F, M->P, K, topk, L, reversed);
+    fn<<<grid, FM_T, L.bytes, st>>>(dev_view(I), stack, s_pop, n_parents, T, M->wt, M->w1p, M->w, M->ob1, M->ob2,
+                                    M->ob3, M->F, M->P, K, topk, L, reversed);
     FSP_CUDA(cudaGetLastError());
     return FSP_OK;
 }

@@ -133,6 +133,43 @@ __global__ void k_solve_init(SolveWs ws, int n, int stride, int ub0)
 
 // Start from caller records: validate each (a permutation, depth <= n-2) and
 // re-sort its remaining part by job index, the order branching relies on.
+// n <= 63: the record and the job masks stay in registers.
+template <int NV>
+__device__ __forceinline__ bool init_node_fast(uint8_t *r, int n)
+{
+    FspRec<NV> rec;
+    fsp_load_rec(rec, r);
+    const int d = (int)fsp_rec_byte_dyn(rec, n);
+    bool bad = d > n - 2;
+    unsigned long long seen = 0ull, rem = 0ull;
+#pragma unroll
+    for (int i = 0; i < 16 * NV; ++i) {
+        if (i < n) {
+            const int j = (int)((rec.w[i >> 2] >> ((i & 3) * 8)) & 0xFFu);
+            if (j >= n) { bad = true; continue; }
+            const unsigned long long bit = 1ull << j;
+            if (seen & bit) bad = true;
+            seen |= bit;
+            if (i >= d) rem |= bit;
+        }
+    }
+    if (bad) return false;
+    int o = d;  // rewrite positions d..n-1 with the remaining jobs in increasing order
+#pragma unroll
+    for (int i = 0; i < 16 * NV; ++i) {
+        if (i >= d && i < n) {
+            const int j = __ffsll((long long)rem) - 1;
+            rem &= rem - 1ull;
+            const int sh = (i & 3) * 8;
+            rec.w[i >> 2] = (rec.w[i >> 2] & ~(0xFFu << sh)) | ((uint32_t)j << sh);
+            ++o;
+        }
+    }
+    (void)o;
+    fsp_store_rec(rec, r);
+    return true;
+}
+
 __global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long count, int ub0)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -149,6 +186,13 @@ __global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long coun
     }
     if (t >= count) return;
     uint8_t *r = ws.stack + t * stride;
+    if (n <= 63) {
+        const int nv = stride >> 4;
+        const bool ok = nv == 1 ? init_node_fast<1>(r, n) : nv == 2 ? init_node_fast<2>(r, n)
+                      : nv == 3 ? init_node_fast<3>(r, n) : init_node_fast<4>(r, n);
+        if (!ok) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
+        return;
+    }
     const int d = r[n];
     uint32_t seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t rem[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -254,9 +298,10 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
         }
         if (threadIdx.x == 0) { s_taken = 0; s_sum = 0; }
         __syncthreads();
-        if (taken) {
-            atomicAdd(&s_taken, taken);
-            atomicAdd(&s_sum, tsum_taken);
+        const int wt = __reduce_add_sync(0xffffffffu, taken), ws_ = __reduce_add_sync(0xffffffffu, tsum_taken);
+        if ((threadIdx.x & 31) == 0 && wt) {  // one shared atomic per warp
+            atomicAdd(&s_taken, wt);
+            atomicAdd(&s_sum, ws_);
         }
         __syncthreads();
         const int ct = s_taken, cs = s_sum;
