@@ -135,6 +135,10 @@ typedef struct {
                                here (training data) until log_cap records are stored */
     int64_t log_cap;
     int64_t *log_count;     /* host or NULL: records stored in log_nodes */
+    int32_t *log_lbs;       /* device or NULL: with log_nodes, the bound of each logged
+                               record (log_cap entries; in the learned order a child cut
+                               by its predicted pairs logs that partial bound, which is
+                               >= the UB of its iteration) */
 } fsp_options;
 
 /* Fill *opt with the defaults (pool 1024, no budget, default capacity). */

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfsp.so")
 INCLUDE = os.path.join(ROOT, "include")
-SOURCES = ["fsp_instance.cu", "fsp_bound.cu", "fsp_solve.cu", "fsp_neh.cu", "fsp_mlp.cu", "fsp_batch.cu", "fsp_learned.cu"]
+SOURCES = ["fsp_instance.cu", "fsp_bound.cu", "fsp_solve.cu", "fsp_neh.cu", "fsp_mlp.cu", "fsp_batch.cu", "fsp_learned.cu",
+           "fsp_family.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
          "-I", INCLUDE, "-I", CSRC]

@@ -42,6 +42,8 @@ struct fsp_instance {
     int32_t *d_lag;  // [P][n]
     uint8_t *d_order;  // [P][n] Johnson order (job at each position)
     FspEntry *d_ent;   // [P][n] order-major entries
+    int2 *d_we;        // [n][P] position-major {w, e}: entry at position i of every pair
+    uint8_t *d_rank;   // [P][n] position of job j in pair kl's order
     int *d_status;     // error flag of malformed records
 };
 
@@ -50,6 +52,8 @@ struct DevInst {
     int n, m, P, stride, mp;
     const int32_t *p, *q;
     const FspEntry *ent;
+    const int2 *we;
+    const uint8_t *rank;
     int *status;
 };
 
@@ -58,6 +62,7 @@ static inline DevInst dev_view(const fsp_instance *I)
     DevInst d;
     d.n = I->n; d.m = I->m; d.P = I->P; d.stride = I->stride; d.mp = I->mp;
     d.p = I->d_p; d.q = I->d_q; d.ent = I->d_ent; d.status = I->d_status;
+    d.we = I->d_we; d.rank = I->d_rank;
     return d;
 }
 

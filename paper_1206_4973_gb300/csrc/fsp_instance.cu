@@ -68,8 +68,9 @@ __device__ __forceinline__ bool johnson_precedes(int i, int32_t ai, int32_t bi, 
 }
 
 // One block per machine pair, one thread per job.
-__global__ void k_pair_tables(int n, int m, const int32_t *__restrict__ p, int32_t *__restrict__ lag,
-                              uint8_t *__restrict__ order, FspEntry *__restrict__ ent)
+__global__ void k_pair_tables(int n, int m, int P, const int32_t *__restrict__ p, int32_t *__restrict__ lag,
+                              uint8_t *__restrict__ order, FspEntry *__restrict__ ent, int2 *__restrict__ we,
+                              uint8_t *__restrict__ rank_of)
 {
     __shared__ int32_t a_s[FSP_MAX_JOBS + 1], b_s[FSP_MAX_JOBS + 1], l_s[FSP_MAX_JOBS + 1];
     const int kl = blockIdx.x;
@@ -98,6 +99,8 @@ __global__ void k_pair_tables(int n, int m, const int32_t *__restrict__ p, int32
         e.bit = 1u << (j & 31);
         e.widx = j >> 5;
         ent[(size_t)kl * n + rank] = e;
+        we[(size_t)rank * P + kl] = make_int2(e.w, e.e);
+        rank_of[(size_t)kl * n + j] = (uint8_t)rank;
     }
 }
 
@@ -109,6 +112,8 @@ static void free_instance(fsp_instance *I)
     cudaFree(I->d_lag);
     cudaFree(I->d_order);
     cudaFree(I->d_ent);
+    cudaFree(I->d_we);
+    cudaFree(I->d_rank);
     cudaFree(I->d_status);
     free(I);
 }
@@ -150,12 +155,14 @@ extern "C" int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance 
     TRY(cudaMalloc(&I->d_lag, sizeof(int32_t) * (size_t)I->P * n));
     TRY(cudaMalloc(&I->d_order, (size_t)I->P * n));
     TRY(cudaMalloc(&I->d_ent, sizeof(FspEntry) * (size_t)I->P * n));
+    TRY(cudaMalloc(&I->d_we, sizeof(int2) * (size_t)I->P * n));
+    TRY(cudaMalloc(&I->d_rank, (size_t)I->P * n));
     TRY(cudaMalloc(&I->d_status, sizeof(int)));
     TRY(cudaMemcpy(I->d_p, p, sizeof(int32_t) * n * m, cudaMemcpyHostToDevice));
     TRY(cudaMemset(I->d_status, 0, sizeof(int)));
     k_tails<<<(n * m + 255) / 256, 256>>>(n, m, I->d_p, I->d_q);
     TRY(cudaGetLastError());
-    k_pair_tables<<<I->P, 256>>>(n, m, I->d_p, I->d_lag, I->d_order, I->d_ent);
+    k_pair_tables<<<I->P, 256>>>(n, m, I->P, I->d_p, I->d_lag, I->d_order, I->d_ent, I->d_we, I->d_rank);
     TRY(cudaGetLastError());
     TRY(cudaDeviceSynchronize());
 #undef TRY

@@ -21,7 +21,7 @@
 #include <chrono>
 #include <mutex>
 
-#include "fsp_solve.cuh"
+#include "fsp_family.cuh"
 
 #define SOLVE_B 256        // threads per block of the per-child kernels
 #define SELECT_B 1024      // threads of the selection CTA
@@ -314,6 +314,7 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
         ws.poff[np] = (int)running;
         ctl->n_list = 0;
         ctl->early = 0;
+        ctl->fam_next = 0;
         ctl->best_key = ~0ull;
         ctl->ub_iter = ctl->ub;
         if (S - np + running > ws.cap) {  // could overflow: keep the stack intact
@@ -679,6 +680,8 @@ struct SolvePlan {
     BoundShape shp;
     BranchBoundFn bb;
     BranchBound2Fn bb2;
+    BranchFamilyFn bf;   // families of children bounded together (NULL: per child)
+    FamSmem famL;
     BranchLearnedFn bl;  // learned order (NULL: plain)
     BoundListFn blist;
     int per_cta;
@@ -708,6 +711,18 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
                                       (int)shp.L.bytes));
     }
     P->per_cta = shp.ver == 2 ? shp.B * FSP_NPT : shp.B;
+    // the plain order bounds each parent's children together where the
+    // family kernel's tables fit (FSP_FAMILY=0 keeps the per-child kernel)
+    P->bf = nullptr;
+    if (shp.ver == 2 && !P->L.learned) {
+        const char *ev = getenv("FSP_FAMILY");
+        const int w = (ev && ev[0] == '0') ? 0 : family_warps(I, shp.mt, shp.nv);
+        if (w > 0 && (P->bf = pick_branch_family(shp.mt, shp.nv)) != nullptr) {
+            P->famL = family_smem_layout(I, shp.mt, shp.nv, w);
+            FSP_CUDA(cudaFuncSetAttribute((const void *)P->bf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)P->famL.bytes));
+        }
+    }
     P->bl = nullptr;
     P->blist = nullptr;
     P->list_grid = 0;
@@ -839,6 +854,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 const long long k = h.n_children < o.log_cap - logged ? h.n_children : o.log_cap - logged;
                 TRY(cudaMemcpyAsync(o.log_nodes + logged * I->stride, ws.children, (size_t)k * I->stride,
                                     cudaMemcpyDeviceToDevice, st));
+                if (o.log_lbs)
+                    TRY(cudaMemcpyAsync(o.log_lbs + logged, ws.lbs, (size_t)k * 4, cudaMemcpyDeviceToDevice, st));
                 logged += k;
             }
             if (h.stack_size == 0) break;
@@ -871,6 +888,11 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 const int grid_l = (int)((pool + I->n + 255) / 256);
                 P->bl<<<grid_l, 256, shp.L2.bytes, st>>>(D, ws, shp.L2, L.topk);
                 P->blist<<<P->list_grid, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
+            } else if (P->bf) {
+                // at most pool / 2 + 1 parents: stacked nodes have >= 2 children
+                const long long fam = (pool / 2 + 1 + P->famL.warps - 1) / P->famL.warps;
+                const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
+                P->bf<<<grid_f, P->famL.warps * 32, P->famL.bytes, st>>>(D, ws, P->famL);
             } else if (bb2) {
                 bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             } else {
@@ -993,7 +1015,7 @@ extern "C" int fsp_solve_noalloc(fsp_instance *I, int32_t ub0, int32_t *cmax, in
         fsp_set_error("fsp_solve_noalloc: takes no workspace (it uses its fixed scratch)");
         return FSP_ERR_ARG;
     }
-    if (opt && (opt->order != FSP_ORDER_PLAIN || opt->log_nodes)) {
+    if (opt && (opt->order != FSP_ORDER_PLAIN || opt->log_nodes || opt->log_lbs)) {
         fsp_set_error("fsp_solve_noalloc: the learned order and node logging are not available without allocation");
         return FSP_ERR_ARG;
     }

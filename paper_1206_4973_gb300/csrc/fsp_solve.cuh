@@ -17,6 +17,7 @@ struct SolveCtl {
     long long cnt[7];       // bounded, branched, pruned, leaves, iterations, updates, early cuts
     long long n_list;       // learned order: children left for the full bound
     long long early;        // learned order: children cut by their predicted pairs
+    long long fam_next;     // family kernel: next parent to take
 };
 
 struct SolveWs {

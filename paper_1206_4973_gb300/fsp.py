@@ -62,7 +62,7 @@ class fsp_options(ctypes.Structure):
                 ("schedule_out", ctypes.POINTER(ctypes.c_int64)), ("schedule_out_cap", ctypes.c_int64),
                 ("order", ctypes.c_int), ("topk", ctypes.c_int), ("model", ctypes.c_void_p),
                 ("log_nodes", ctypes.c_void_p), ("log_cap", ctypes.c_int64),
-                ("log_count", ctypes.POINTER(ctypes.c_int64))]
+                ("log_count", ctypes.POINTER(ctypes.c_int64)), ("log_lbs", ctypes.c_void_p)]
 ORDER_PLAIN, ORDER_LEARNED = 0, 1
 
 
@@ -243,7 +243,7 @@ def fsp_tune_simulate(nodes_per_cta: int, sms: int, max_pool: int, score):
 def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
              schedule=None, stream=None, init_nodes=None, init_count=None, max_iterations=0,
              out_nodes=None, profile=False, tune_window=0, schedule_out=None, model=None, topk=0,
-             log_nodes=None):
+             log_nodes=None, log_lbs=None):
     o = fsp_options()
     load().fsp_default_options(ctypes.byref(o))
     o.pool_size = int(pool_size)
@@ -276,6 +276,11 @@ def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, tra
         keep.append(log_nodes)
         o.log_nodes = log_nodes.data_ptr()
         o.log_cap = int(log_nodes.shape[0])
+        if log_lbs is not None:
+            if log_lbs.numel() < o.log_cap:
+                raise ValueError("log_lbs needs an entry per log_nodes record")
+            keep.append(log_lbs)
+            o.log_lbs = log_lbs.data_ptr()
     o.out_count = ctypes.pointer(out_count)
     if out_nodes is not None:
         keep.append(out_nodes)
@@ -313,7 +318,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
               stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
               workspace=None, init_nodes=None, init_count=None, max_iterations: int = 0,
               out_nodes=None, profile: bool = False, tune_window: int = 0, schedule_cap: int = 0,
-              model=None, topk: int = 0, log_nodes=None):
+              model=None, topk: int = 0, log_nodes=None, log_lbs=None):
     """Exact B&B on the device.  The scratch is a torch uint8 tensor (allocated
     here when `workspace` is None).  init_nodes (host array or device tensor of
     records) starts the search from that stack; out_nodes (host array or
@@ -325,7 +330,8 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     sched_out = np.zeros(schedule_cap, np.int64) if schedule_cap > 0 else None
     o, keep, trace, out_count = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap,
                                          schedule, stream, init_nodes, init_count, max_iterations,
-                                         out_nodes, profile, tune_window, sched_out, model, topk, log_nodes)
+                                         out_nodes, profile, tune_window, sched_out, model, topk, log_nodes,
+                                         log_lbs)
     nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")

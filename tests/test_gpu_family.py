@@ -1,0 +1,77 @@
+"""The family kernel (a parent's children bounded together from the parent's
+prefix and suffix maxima per machine pair) gives every child the bound the
+oracle computes for it, bit for bit, and runs the same search as the
+per-child kernel."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1206_4973_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("status", "cmax", "nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iterations",
+        "incumbent_updates", "stack_left")
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    from paper_1206_4973_gb300 import build, fsp
+    build.build()
+    fsp.load()
+    assert torch.cuda.is_available()
+    return fsp
+
+
+def per_child(F, inst, **kw):
+    os.environ["FSP_FAMILY"] = "0"
+    try:
+        return F.fsp_solve(inst, **kw)
+    finally:
+        del os.environ["FSP_FAMILY"]
+
+
+# shapes across the record widths (16, 32, 48, 64 bytes), the 32-job mask
+# boundary, every machine template, one-parent pools and a shape whose
+# tables do not fit the family kernel (63 x 20: per-child kernel)
+CASES = [(12, 5, 0, 1024), (20, 20, 1, 4096), (15, 10, 3, 512), (31, 20, 5, 2048), (32, 20, 9, 1024),
+         (33, 10, 21, 2048), (50, 5, 4, 4096), (63, 10, 8, 2048), (9, 20, 88, 64), (20, 5, 2, 1),
+         (63, 20, 12, 512)]
+
+
+@pytest.mark.parametrize("n,m,seed,pool", CASES)
+def test_children_bounds_match_oracle(F, n, m, seed, pool):
+    import torch
+    p = inputs.instance(n, m, seed)
+    inst = F.fsp_create_instance(p)
+    ub0, perm0 = F.fsp_neh(inst)
+    cap = 60000
+    log = torch.zeros((cap, inst.stride), dtype=torch.uint8, device="cuda")
+    lbs = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    r = F.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=40000, log_nodes=log, log_lbs=lbs)
+    k = r["logged"]
+    assert k == min(cap, r["nodes_bounded"]) and k > 0
+    rec = log[:k].cpu().numpy()
+    got = lbs[:k].cpu().numpy()
+    idx = np.unique(np.linspace(0, k - 1, min(k, 15000)).astype(np.int64))
+    assert np.array_equal(got[idx], oracle.bound_pool(p, rec[idx]))
+
+
+@pytest.mark.parametrize("n,m,seed,pool,budget", [(12, 5, 0, 1024, 0), (20, 20, 6, 8192, 200000),
+                                                  (50, 10, 7, 4096, 100000), (32, 5, 11, 256, 300000)])
+def test_family_and_per_child_kernels_search_alike(F, n, m, seed, pool, budget):
+    p = inputs.instance(n, m, seed)
+    inst = F.fsp_create_instance(p)
+    ub0, perm0 = F.fsp_neh(inst)
+    kw = dict(ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=budget, trace_cap=100000)
+    a = F.fsp_solve(inst, **kw)
+    b = per_child(F, inst, **kw)
+    for key in KEYS:
+        assert a[key] == b[key], key
+    assert np.array_equal(a["trace"], b["trace"])
+    assert (a["perm"] is None) == (b["perm"] is None)
+    if a["perm"] is not None:
+        assert list(a["perm"]) == list(b["perm"])
