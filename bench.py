@@ -40,8 +40,8 @@ UNIT = "subproblems/s"
 L2_FLUSH_BYTES = 512 << 20
 SMS, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) of one branch-and-bound launch of the step, from the ncu capture in
-# profiles/k_bound_pool2_20x20_2e18_full.md; None once that kernel has changed since the capture.
-BB_TRAFFIC_BYTES = 1146624
+# profiles/k_branch_family_20x20_2e18_full.md; None once that kernel has changed since the capture.
+BB_TRAFFIC_BYTES = 982528
 
 
 def work_ops(depth, n=N_JOBS, m=N_MACH):
@@ -234,21 +234,32 @@ def learned_vs_plain(fsp, budget=LEARNED_BUDGET):
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         res, phases = {}, {}
-        for name, extra in (("plain", {}), ("learned", {"model": mlp, "topk": 4})):
-            fsp.fsp_solve(inst, node_budget=budget // 100, **kw, **extra)  # warm-up
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            r = fsp.fsp_solve(inst, node_budget=budget, trace_cap=1, **kw, **extra)
-            res[name] = (r, time.perf_counter() - t1)
-            q = fsp.fsp_solve(inst, node_budget=budget // 20, profile=True, **kw, **extra)  # phase times
+        # plain: the family kernel (certified pair skipping); plain_per_child: every
+        # pair of every child evaluated (FSP_FAMILY=0); learned: the family kernel
+        # with each parent's predicted pairs first
+        for name, extra, env in (("plain", {}, None), ("plain_per_child", {}, "0"),
+                                 ("learned", {"model": mlp, "topk": 4}, None)):
+            if env is not None:
+                os.environ["FSP_FAMILY"] = env
+            try:
+                fsp.fsp_solve(inst, node_budget=budget // 100, **kw, **extra)  # warm-up
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                r = fsp.fsp_solve(inst, node_budget=budget, trace_cap=1, **kw, **extra)
+                res[name] = (r, time.perf_counter() - t1)
+                q = fsp.fsp_solve(inst, node_budget=budget // 20, profile=True, **kw, **extra)  # phase times
+            finally:
+                os.environ.pop("FSP_FAMILY", None)
             phases[name] = {k: round(q[k] / max(1, q["iterations"]) * 1e3, 1)
                             for k in ("select_ms", "infer_ms", "bound_ms", "compact_ms")}
-        (a, ta), (b, tb) = res["plain"], res["learned"]
-        same = all(a[k] == b[k] for k in ("cmax", "nodes_bounded", "nodes_branched", "nodes_pruned", "leaves",
-                                          "iterations", "incumbent_updates", "stack_left"))
+        (a, ta), (b, tb), (c, tc) = res["plain"], res["learned"], res["plain_per_child"]
+        same = all(a[k] == b[k] == c[k] for k in ("cmax", "nodes_bounded", "nodes_branched", "nodes_pruned",
+                                                  "leaves", "iterations", "incumbent_updates", "stack_left"))
         out.append({"instance": f"{n}x{m} seed {seed}", "nodes_bounded": a["nodes_bounded"],
                     "plain_nodes_per_s": a["nodes_bounded"] / ta, "learned_nodes_per_s": b["nodes_bounded"] / tb,
-                    "speedup": ta / tb, "identical_search": same, "cmax": a["cmax"],
+                    "plain_per_child_nodes_per_s": c["nodes_bounded"] / tc,
+                    "speedup": ta / tb, "speedup_vs_per_child": tc / tb, "family_vs_per_child": tc / ta,
+                    "identical_search": same, "cmax": a["cmax"],
                     "optimal": a["status"] == fsp.OK, "early_cut_fraction": b["early_pruned"] / max(1, b["nodes_bounded"]),
                     "train_s": t_train, "train_final_loss": loss,
                     "us_per_iteration": phases})
@@ -449,7 +460,7 @@ def main():
     achieved = ops_per_step / (statistics.mean(bound_ms) / 1e3)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak_ops, "traffic": BB_TRAFFIC_BYTES,
-                "kernel": "k_branch_bound (branching + bounding of the pool's children)",
+                "kernel": "k_branch_family (branching + bounding of the pool's children, one warp per parent)",
                 "ops_per_launch": ops_per_step, "children_per_launch": n_children,
                 "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz (issue ceiling)"}
 

@@ -75,6 +75,7 @@ FamSmem family_smem_layout(const fsp_instance *I, int MT, int NV, int warps)
     L.w_lm = w; w += fsp_align16((size_t)P * 4);
     L.warp_bytes = w;
     L.warps = warps;
+    L.K = 0;
     L.bytes = o + w * warps;
     return L;
 }
@@ -128,7 +129,13 @@ __device__ __forceinline__ int32_t fam_prefix_p(int t, int lane, int d, int k, i
     return on ? pq_s[rec_s[on ? i : 0] * mp + k].x : 0;
 }
 
-template <int MT, int NV>
+// LRN: the learned order.  Children whose LB1 reaches the iteration's UB are
+// cut at once; the parent's K predicted pairs (ws.topk) then give each open
+// child a lower bound from their forward scans and cut more; only if a
+// child is left do the certification and the remaining pairs run, for the
+// children left.  A cut child keeps its partial bound (>= the UB); the
+// others get the exact bound, so the search is the plain one.
+template <int MT, int NV, bool LRN>
 __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst I, SolveWs ws, FamSmem L)
 {
     constexpr int P = MT * (MT - 1) / 2;
@@ -280,13 +287,124 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         }
         __syncwarp();
 
+        // exact terms of the listed pairs, 32 at a time: forward and backward
+        // scans into T (one column per pair), then the lookups of the
+        // children still open
+        auto exact_pairs = [&](int cnt_all) {
+            for (int b0 = 0; b0 < cnt_all; b0 += 32) {
+                const int cnt = min(32, cnt_all - b0);
+                if (lane < cnt) {
+                    const int kl = lkl[b0 + lane];
+                    Mask pm = 0;
+#pragma unroll 4
+                    for (int i = d; i < n; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
+                    int32_t E = 0, M = FSP_NEG;
+                    Mask pf = pm;
+#pragma unroll 2
+                    for (int pos = 0; pos < n; ++pos) {
+                        const int2 v = we_s[pos * P + kl];
+                        const bool b = pf & 1u;
+                        pf >>= 1;
+                        T[pos * FAM_TS + lane] = M;
+                        M = __viaddmax_s32(E, b ? v.x : FSP_NEG, M);
+                        E += b ? v.y : 0;
+                    }
+                    int32_t R = E, Ms = FSP_NEG;
+#pragma unroll 2
+                    for (int pos = n - 1; pos >= 0; --pos) {
+                        const int2 v = we_s[pos * P + kl];
+                        const bool b = (pm >> pos) & 1u;
+                        int32_t *t = T + pos * FAM_TS + lane;
+                        *t = max(*t, Ms - v.y);
+                        R -= b ? v.y : 0;
+                        Ms = __viaddmax_s32(R, b ? v.x : FSP_NEG, Ms);
+                    }
+                }
+                __syncwarp();
+                for (int ci = lane; ci < r; ci += 32) {
+                    int32_t lb = lbv[ci];
+                    if (LRN && lb >= ub_iter) continue;
+                    const int c = rec_s[d + ci];
+                    const int32_t *cr = cc + ci * mtp, *sr = sq + ci * mtp;
+#pragma unroll 4
+                    for (int s = 0; s < cnt; ++s) {
+                        const int kl = lkl[b0 + s];
+                        const int km = klm_s[kl];
+                        const int k = km & 255, l = km >> 8;
+                        const int32_t X = T[rk8[kl * rks8 + c] * FAM_TS + s];
+                        lb = __viaddmax_s32(sr[l], __viaddmax_s32(cr[k], X, cr[l]), lb);
+                    }
+                    lbv[ci] = lb;
+                }
+                __syncwarp();
+            }
+        };
+        // lower bounds from the forward scan alone of the listed pairs (at most
+        // 32): X_c >= the prefix maximum before c, so SQ_l + max(C_l, C_k +
+        // prefix max) is a bound no larger than the pair's value
+        auto forward_pairs = [&](int cnt) {
+            if (lane < cnt) {
+                const int kl = lkl[lane];
+                Mask pm = 0;
+#pragma unroll 4
+                for (int i = d; i < n; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
+                int32_t E = 0, M = FSP_NEG;
+#pragma unroll 2
+                for (int pos = 0; pos < n; ++pos) {
+                    const int2 v = we_s[pos * P + kl];
+                    const bool b = pm & 1u;
+                    pm >>= 1;
+                    T[pos * FAM_TS + lane] = M;
+                    M = __viaddmax_s32(E, b ? v.x : FSP_NEG, M);
+                    E += b ? v.y : 0;
+                }
+            }
+            __syncwarp();
+            for (int ci = lane; ci < r; ci += 32) {
+                int32_t lb = lbv[ci];
+                if (lb >= ub_iter) continue;
+                const int c = rec_s[d + ci];
+                const int32_t *cr = cc + ci * mtp, *sr = sq + ci * mtp;
+                for (int s = 0; s < cnt; ++s) {
+                    const int kl = lkl[s];
+                    const int km = klm_s[kl];
+                    const int k = km & 255, l = km >> 8;
+                    const int32_t X = T[rk8[kl * rks8 + c] * FAM_TS + s];
+                    lb = __viaddmax_s32(sr[l], __viaddmax_s32(cr[k], X, cr[l]), lb);
+                }
+                lbv[ci] = lb;
+            }
+            __syncwarp();
+        };
+        // children still open (all of them in the plain order)
+        auto open_any = [&]() {
+            bool any = false;
+            for (int ci = lane; ci < r; ci += 32) any |= lbv[ci] < ub_iter;
+            return __any_sync(0xffffffffu, any);
+        };
+
         const bool leaves = d + 1 == n - 1;
-        if (!leaves) {
+        bool open = !leaves;
+        if (LRN) {
+            if (open) open = open_any();
+            if (open) {  // the parent's predicted pairs
+                if (lane < L.K) lkl[lane] = (uint16_t)ws.topk[(long long)f * L.K + lane];
+                __syncwarp();
+                forward_pairs(L.K);
+                open = open_any();
+            }
+            int cut = 0;
+            for (int ci = lane; ci < r; ci += 32) cut += lbv[ci] >= ub_iter;
+            cut = __reduce_add_sync(0xffffffffu, cut);
+            if (lane == 0 && cut) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctl->early), (unsigned long long)cut);
+        }
+        if (open) {
             // -- per machine: alpha_k = min_c (LB1 - C_k), beta_l = max_c SQ_l
             if (lane < MT) {
                 int32_t a = 0x7fffffff, b = -0x7fffffff;
 #pragma unroll 4
                 for (int ci = 0; ci < r; ++ci) {
+                    if (LRN && lbv[ci] >= ub_iter) continue;  // cut already
                     a = min(a, lbv[ci] - cc[ci * mtp + lane]);
                     b = max(b, sq[ci * mtp + lane]);
                 }
@@ -358,7 +476,9 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
 #pragma unroll 4
                     for (int ci = 0; ci < r; ++ci) {
                         const int c = rec_s[d + ci];
-                        ok &= Mu + (int)en_s[c * P + kl] + sq[ci * mtp + l] <= lbv[ci] - cc[ci * mtp + k];
+                        const int32_t lbc = lbv[ci];
+                        ok &= (LRN && lbc >= ub_iter) ||
+                              Mu + (int)en_s[c * P + kl] + sq[ci * mtp + l] <= lbc - cc[ci * mtp + k];
                     }
                 }
                 const bool fail = valid && !ok;
@@ -369,54 +489,7 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
             }
             __syncwarp();
 
-            // -- exact terms of the remaining pairs, 32 at a time: forward and
-            // backward scans into T (one column per pair), then the lookups
-            for (int b0 = 0; b0 < n2; b0 += 32) {
-                const int cnt = min(32, n2 - b0);
-                if (lane < cnt) {
-                    const int kl = lkl[b0 + lane];
-                    Mask pm = 0;
-#pragma unroll 4
-                    for (int i = d; i < n; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
-                    int32_t E = 0, M = FSP_NEG;
-                    Mask pf = pm;
-#pragma unroll 2
-                    for (int pos = 0; pos < n; ++pos) {
-                        const int2 v = we_s[pos * P + kl];
-                        const bool b = pf & 1u;
-                        pf >>= 1;
-                        T[pos * FAM_TS + lane] = M;
-                        M = __viaddmax_s32(E, b ? v.x : FSP_NEG, M);
-                        E += b ? v.y : 0;
-                    }
-                    int32_t R = E, Ms = FSP_NEG;
-#pragma unroll 2
-                    for (int pos = n - 1; pos >= 0; --pos) {
-                        const int2 v = we_s[pos * P + kl];
-                        const bool b = (pm >> pos) & 1u;
-                        int32_t *t = T + pos * FAM_TS + lane;
-                        *t = max(*t, Ms - v.y);
-                        R -= b ? v.y : 0;
-                        Ms = __viaddmax_s32(R, b ? v.x : FSP_NEG, Ms);
-                    }
-                }
-                __syncwarp();
-                for (int ci = lane; ci < r; ci += 32) {
-                    const int c = rec_s[d + ci];
-                    const int32_t *cr = cc + ci * mtp, *sr = sq + ci * mtp;
-                    int32_t lb = lbv[ci];
-#pragma unroll 4
-                    for (int s = 0; s < cnt; ++s) {
-                        const int kl = lkl[b0 + s];
-                        const int km = klm_s[kl];
-                        const int k = km & 255, l = km >> 8;
-                        const int32_t X = T[rk8[kl * rks8 + c] * FAM_TS + s];
-                        lb = __viaddmax_s32(sr[l], __viaddmax_s32(cr[k], X, cr[l]), lb);
-                    }
-                    lbv[ci] = lb;
-                }
-                __syncwarp();
-            }
+            exact_pairs(n2);
         }
 
         // -- the bounds; a depth n-1 child is a complete schedule
@@ -433,10 +506,10 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
     }
 }
 
-BranchFamilyFn pick_branch_family(int mt, int nv)
+BranchFamilyFn pick_branch_family(int mt, int nv, bool learned)
 {
 #define FSP_CASEF(MT_, NV_) \
-    if (mt == MT_ && nv == NV_) return &k_branch_family<MT_, NV_>;
+    if (mt == MT_ && nv == NV_) return learned ? &k_branch_family<MT_, NV_, true> : &k_branch_family<MT_, NV_, false>;
     FSP_SHAPES_FAMILY(FSP_CASEF)
 #undef FSP_CASEF
     return nullptr;

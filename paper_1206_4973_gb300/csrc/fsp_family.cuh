@@ -37,10 +37,11 @@ struct FamSmem {
     size_t we_off, rk8_off, en_off, gam_off, klm_off, pq_off, warp_off, warp_bytes, bytes;
     size_t w_ps, w_psa, w_ab, w_rec, w_pofs, w_cc, w_sq, w_lb, w_T, w_lkl, w_lm;
     int rks8, mtp, warps;
+    int K;  // learned order: predicted pairs per parent
 };
 
 FamSmem family_smem_layout(const fsp_instance *I, int MT, int NV, int warps);
 int family_warps(const fsp_instance *I, int MT, int NV);
 
 typedef void (*BranchFamilyFn)(DevInst, SolveWs, FamSmem);
-BranchFamilyFn pick_branch_family(int mt, int nv);
+BranchFamilyFn pick_branch_family(int mt, int nv, bool learned);

@@ -711,14 +711,15 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
                                       (int)shp.L.bytes));
     }
     P->per_cta = shp.ver == 2 ? shp.B * FSP_NPT : shp.B;
-    // the plain order bounds each parent's children together where the
-    // family kernel's tables fit (FSP_FAMILY=0 keeps the per-child kernel)
+    // each parent's children are bounded together where the family kernel's
+    // tables fit (FSP_FAMILY=0 keeps the per-child kernels)
     P->bf = nullptr;
-    if (shp.ver == 2 && !P->L.learned) {
+    if (shp.ver == 2) {
         const char *ev = getenv("FSP_FAMILY");
         const int w = (ev && ev[0] == '0') ? 0 : family_warps(I, shp.mt, shp.nv);
-        if (w > 0 && (P->bf = pick_branch_family(shp.mt, shp.nv)) != nullptr) {
+        if (w > 0 && (P->bf = pick_branch_family(shp.mt, shp.nv, P->L.learned)) != nullptr) {
             P->famL = family_smem_layout(I, shp.mt, shp.nv, w);
+            P->famL.K = P->L.learned ? P->L.topk : 0;
             FSP_CUDA(cudaFuncSetAttribute((const void *)P->bf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)P->famL.bytes));
         }
@@ -726,7 +727,7 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
     P->bl = nullptr;
     P->blist = nullptr;
     P->list_grid = 0;
-    if (P->L.learned && shp.ver == 2) {  // other shapes run the plain order
+    if (P->L.learned && shp.ver == 2 && !P->bf) {  // other shapes run the plain order
         P->bl = pick_branch_learned(shp.mt, shp.nv, shp.nw);
         P->blist = pick_bound_list(shp.mt, shp.nv, shp.nw);
         if (!P->bl || !P->blist) { fsp_set_error("fsp_solve: no learned kernel for this shape"); return FSP_ERR_ARG; }
@@ -836,7 +837,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 t_sel += a;
                 t_bb += b;
                 t_cmp += c;
-                if (P->bl) {
+                if (P->L.learned && (P->bl || P->bf)) {
                     float d = 0;
                     TRY(cudaEventElapsedTime(&d, pe[1], pe[4]));
                     t_inf += d;
@@ -889,6 +890,18 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 P->bl<<<grid_l, 256, shp.L2.bytes, st>>>(D, ws, shp.L2, L.topk);
                 P->blist<<<P->list_grid, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             } else if (P->bf) {
+                if (P->L.learned) {  // each parent's predicted pairs first
+                    const long long npar = pool / 2 + 2;
+                    int frc = fsp_mlp_topk_parents(o.model, I, ws.stack, &ws.ctl->s_pop, &ws.ctl->n_parents, npar,
+                                                   L.topk, ws.topk, st);
+                    if (frc == FSP_ERR_ARG) {  // network shape without the fused kernel
+                        launch_parent_features(D, ws, T, npar, st);
+                        frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
+                        if (frc == FSP_OK) launch_topk(ws, I->P, L.topk, npar, st);
+                    }
+                    if (frc != FSP_OK) { rc = frc; goto out; }
+                    if (prof) TRY(cudaEventRecord(pe[4], st));
+                }
                 // at most pool / 2 + 1 parents: stacked nodes have >= 2 children
                 const long long fam = (pool / 2 + 1 + P->famL.warps - 1) / P->famL.warps;
                 const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
