@@ -30,7 +30,7 @@ struct SolveLayout {
     long long pool_max, max_children, cap, trace_cap, max_parents;
     int max_blocks, topk;
     bool learned;
-    size_t off_ctl, off_stack, off_children, off_lbs, off_poff, off_blk, off_inc, off_trace, bytes;
+    size_t off_ctl, off_stack, off_cum, off_iblk, off_children, off_lbs, off_poff, off_blk, off_inc, off_trace, bytes;
     size_t off_list, off_px, off_pscore, off_topk;
 };
 
@@ -70,10 +70,12 @@ static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout
     size_t off = 0;
     L->off_ctl = off; off = align256(off + sizeof(SolveCtl));
     L->off_stack = off; off = align256(off + (size_t)L->cap * I->stride);
+    L->off_cum = off; off = align256(off + (size_t)L->cap * 8);
+    L->off_iblk = off; off = align256(off + (size_t)((init + 255) / 256 + 1) * 8);
     L->off_children = off; off = align256(off + (size_t)L->max_children * I->stride);
     L->off_lbs = off; off = align256(off + (size_t)L->max_children * 4);
     L->off_poff = off; off = align256(off + (size_t)(L->max_children + 2) * 4);
-    L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 8);
+    L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 12);
     L->off_inc = off; off = align256(off + 256);
     L->off_trace = off; off = align256(off + (size_t)L->trace_cap * 32);
     L->learned = o->order == FSP_ORDER_LEARNED;
@@ -121,6 +123,7 @@ __global__ void k_solve_init(SolveWs ws, int n, int stride, int ub0)
     const int t = threadIdx.x;
     for (int i = t; i < stride; i += blockDim.x) ws.stack[i] = (uint8_t)(i < n ? i : 0);
     if (t == 0) {
+        ws.cum[0] = n;
         SolveCtl c;
         memset(&c, 0, sizeof c);
         c.stack_size = 1;
@@ -236,6 +239,46 @@ __global__ void k_solve_single(SolveWs ws, const int32_t *p, int m, int ub0)
     }
 }
 
+// Sum of one long long per thread over the block (blockDim.x = SOLVE_B).
+__device__ __forceinline__ long long block_sum_ll(long long v, long long *red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// Running children counts of the start records (stack order): the children
+// of each block of 256 records, then each block's records add the blocks
+// before them and their own prefix.
+__global__ void __launch_bounds__(SOLVE_B) k_init_cum_blocks(SolveWs ws, int n, int stride, long long count)
+{
+    __shared__ long long red[SOLVE_B / 32];
+    const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
+    const long long r = t < count ? n - (int)ws.stack[t * stride + n] : 0;
+    const long long s = block_sum_ll(r, red);
+    if (threadIdx.x == 0) ws.iblk[blockIdx.x] = s;
+}
+
+__device__ __forceinline__ int block_incl_scan(int v, int *warp_tot);
+
+__global__ void __launch_bounds__(SOLVE_B) k_init_cum(SolveWs ws, int n, int stride, long long count)
+{
+    __shared__ long long red[SOLVE_B / 32];
+    __shared__ int warp_tot[32];
+    long long before = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += SOLVE_B) before += ws.iblk[i];
+    before = block_sum_ll(before, red);
+    const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
+    const int r = t < count ? n - (int)ws.stack[t * stride + n] : 0;
+    const int incl = block_incl_scan(r, warp_tot);
+    if (t < count) ws.cum[t] = before + incl;
+}
+
 // Inclusive block scan of one int per thread (blockDim.x a multiple of 32).
 __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot)
 {
@@ -263,55 +306,32 @@ __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot)
 }
 
 // Selection (Sec. III): deepest pending nodes first, while their children fit.
-// The candidates are the top min(S, pool) records (every parent has at least
-// one child); each thread takes SEL_PER consecutive candidates per chunk.
-#define SEL_PER 8
+// cum[] holds the running children counts of the stack, so the children of
+// the top i records are cum[S-1] - cum[S-1-i]: the number of parents is the
+// largest i <= min(S, pool) whose children fit the pool (at least one),
+// found by a parallel search that narrows the interval SELECT_B-fold per
+// round, and the parents' first-child offsets follow from cum directly.
 __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stride, long long pool)
 {
-    __shared__ int warp_tot[32];
-    __shared__ int s_taken, s_sum;
     SolveCtl *ctl = ws.ctl;
     const long long S = ctl->stack_size;
     const long long cand = S < pool ? S : pool;
-    long long running = 0, np = 0;
-    for (long long base = 0; base < cand; base += (long long)SELECT_B * SEL_PER) {
-        int r[SEL_PER];
-        int tsum = 0;
-#pragma unroll
-        for (int q = 0; q < SEL_PER; ++q) {
-            const long long i = base + (long long)threadIdx.x * SEL_PER + q;
-            r[q] = i < cand ? n - (int)ws.stack[(S - 1 - i) * stride + n] : 0;
-            tsum += r[q];
-        }
-        const int excl = block_incl_scan(tsum, warp_tot) - tsum;
-        int taken = 0, tsum_taken = 0, run = excl;
-#pragma unroll
-        for (int q = 0; q < SEL_PER; ++q) {
-            const long long i = base + (long long)threadIdx.x * SEL_PER + q;
-            const bool t = i < cand && (i == 0 || running + run + r[q] <= pool);
-            if (t) {
-                ws.poff[i] = (int)(running + run);  // taken candidates are exactly 0..np-1
-                taken++;
-                tsum_taken += r[q];
-            }
-            run += r[q];
-        }
-        if (threadIdx.x == 0) { s_taken = 0; s_sum = 0; }
-        __syncthreads();
-        const int wt = __reduce_add_sync(0xffffffffu, taken), ws_ = __reduce_add_sync(0xffffffffu, tsum_taken);
-        if ((threadIdx.x & 31) == 0 && wt) {  // one shared atomic per warp
-            atomicAdd(&s_taken, wt);
-            atomicAdd(&s_sum, ws_);
-        }
-        __syncthreads();
-        const int ct = s_taken, cs = s_sum;
-        __syncthreads();
-        np += ct;
-        running += cs;
-        if (ct < SELECT_B * SEL_PER) break;
+    const long long top = ws.cum[S - 1];
+    // children of the top i records, 0 <= i <= S
+    auto prefix = [&](long long i) -> long long { return top - (i < S ? ws.cum[S - 1 - i] : 0); };
+    // every i <= lo is taken (lo = 1 always is); no i >= hi fits or exists
+    long long lo = 1, hi = cand + 1;
+    while (hi - lo > 1) {
+        const long long step = (hi - lo + SELECT_B - 1) / SELECT_B;
+        const long long i = lo + (long long)(threadIdx.x + 1) * step;
+        const int c = __syncthreads_count(i < hi && prefix(i) <= pool);
+        lo += (long long)c * step;
+        hi = min(hi, lo + step);
     }
+    const long long np = lo;
+    const long long running = prefix(np);
+    for (long long i = threadIdx.x; i <= np; i += SELECT_B) ws.poff[i] = (int)prefix(i);
     if (threadIdx.x == 0) {
-        ws.poff[np] = (int)running;
         ctl->n_list = 0;
         ctl->early = 0;
         ctl->fam_next = 0;
@@ -423,57 +443,84 @@ __global__ void __launch_bounds__(SOLVE_B) k_count(SolveWs ws, int n, int stride
         leaf = ws.children[c * stride + n] == (uint8_t)(n - 1);
         surv = !leaf && ws.lbs[c] < ubn;
     }
+    __shared__ long long red[SOLVE_B / 32];
     const int cs = __syncthreads_count(surv);
     const int cl = __syncthreads_count(leaf);
+    const long long cr = block_sum_ll(surv ? n - (int)ws.children[c * stride + n] : 0, red);
     if (threadIdx.x == 0) {
-        ws.blk[2 * blockIdx.x] = cs;
-        ws.blk[2 * blockIdx.x + 1] = cl;
+        ws.blk[3 * blockIdx.x] = cs;
+        ws.blk[3 * blockIdx.x + 1] = cl;
+        ws.blk[3 * blockIdx.x + 2] = (int)cr;
     }
 }
 
 // Elimination, step 2: stable compaction onto the stack (reverse pool order).
 __global__ void __launch_bounds__(SOLVE_B) k_push(SolveWs ws, int n, int stride)
 {
-    __shared__ long long red[3][SOLVE_B / 32];
-    __shared__ int wcnt[SOLVE_B / 32];
+    __shared__ long long red[5][SOLVE_B / 32];
+    __shared__ int wcnt[SOLVE_B / 32], wr[SOLVE_B / 32];
     SolveCtl *ctl = ws.ctl;
     const long long nch = ctl->n_children;
     const int ubn = solve_ub_new(ctl);
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    long long before = 0, total = 0, leaves = 0;
+    long long before = 0, total = 0, leaves = 0, before_r = 0, total_r = 0;
     for (int i = tid; i < (int)gridDim.x; i += SOLVE_B) {
-        const long long s = ws.blk[2 * i];
+        const long long s = ws.blk[3 * i], sr = ws.blk[3 * i + 2];
         total += s;
-        leaves += ws.blk[2 * i + 1];
-        if (i < b) before += s;
+        total_r += sr;
+        leaves += ws.blk[3 * i + 1];
+        if (i < b) { before += s; before_r += sr; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         before += __shfl_xor_sync(0xffffffffu, before, o);
         total += __shfl_xor_sync(0xffffffffu, total, o);
         leaves += __shfl_xor_sync(0xffffffffu, leaves, o);
+        before_r += __shfl_xor_sync(0xffffffffu, before_r, o);
+        total_r += __shfl_xor_sync(0xffffffffu, total_r, o);
     }
-    if (lane == 0) { red[0][wid] = before; red[1][wid] = total; red[2][wid] = leaves; }
+    if (lane == 0) {
+        red[0][wid] = before; red[1][wid] = total; red[2][wid] = leaves;
+        red[3][wid] = before_r; red[4][wid] = total_r;
+    }
     const long long c = (long long)b * SOLVE_B + tid;
     bool surv = false;
-    if (c < nch) surv = ws.children[c * stride + n] != (uint8_t)(n - 1) && ws.lbs[c] < ubn;
+    int rc = 0;
+    if (c < nch) {
+        const int dch = ws.children[c * stride + n];
+        surv = dch != n - 1 && ws.lbs[c] < ubn;
+        rc = surv ? n - dch : 0;
+    }
     const unsigned bal = __ballot_sync(0xffffffffu, surv);
+    int rincl = rc;  // survivors' children up to this one, in the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, rincl, o);
+        if (lane >= o) rincl += u;
+    }
     if (lane == 0) wcnt[wid] = __popc(bal);
+    if (lane == 31) wr[wid] = rincl;
     __syncthreads();
-    before = total = leaves = 0;
-    int woff = 0;
+    before = total = leaves = before_r = total_r = 0;
+    int woff = 0, wroff = 0;
     for (int w = 0; w < SOLVE_B / 32; ++w) {
         before += red[0][w];
         total += red[1][w];
         leaves += red[2][w];
-        if (w < wid) woff += wcnt[w];
+        before_r += red[3][w];
+        total_r += red[4][w];
+        if (w < wid) { woff += wcnt[w]; wroff += wr[w]; }
     }
     const long long s_pop = ctl->s_pop;
     if (surv) {
         const long long q = before + woff + __popc(bal & ((1u << lane) - 1u));
+        const long long pos = s_pop + total - 1 - q;
         const uint4 *src = reinterpret_cast<const uint4 *>(ws.children + c * stride);
-        uint4 *dst = reinterpret_cast<uint4 *>(ws.stack + (s_pop + total - 1 - q) * stride);
+        uint4 *dst = reinterpret_cast<uint4 *>(ws.stack + pos * stride);
         for (int v = 0; v < (stride >> 4); ++v) dst[v] = src[v];
+        // the survivors at or below pos are this one and those after it in pool order
+        const long long base = s_pop > 0 ? ws.cum[s_pop - 1] : 0;
+        ws.cum[pos] = base + total_r - (before_r + wroff + rincl - rc);
     }
     if (b == 0) {
         const int ubi = ctl->ub_iter;
@@ -777,6 +824,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     ws.lbs = (int32_t *)(base + L.off_lbs);
     ws.poff = (int *)(base + L.off_poff);
     ws.blk = (int *)(base + L.off_blk);
+    ws.cum = (long long *)(base + L.off_cum);
+    ws.iblk = (long long *)(base + L.off_iblk);
     ws.inc = base + L.off_inc;
     ws.trace = (long long *)(base + L.off_trace);
     ws.trace_cap = L.trace_cap;
@@ -820,8 +869,10 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         if (o.init_nodes && o.init_count > 0) {
             TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(SolveCtl), st));
             TRY(cudaMemcpyAsync(ws.stack, o.init_nodes, (size_t)o.init_count * I->stride, cudaMemcpyDefault, st));
-            k_solve_init_nodes<<<(unsigned)((o.init_count + 255) / 256), 256, 0, st>>>(ws, I->n, I->stride,
-                                                                                         o.init_count, ub0);
+            const unsigned gi = (unsigned)((o.init_count + 255) / 256);
+            k_solve_init_nodes<<<gi, 256, 0, st>>>(ws, I->n, I->stride, o.init_count, ub0);
+            k_init_cum_blocks<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
+            k_init_cum<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
         } else {
             k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
         }

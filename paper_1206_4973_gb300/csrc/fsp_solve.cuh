@@ -23,11 +23,13 @@ struct SolveCtl {
 struct SolveWs {
     SolveCtl *ctl;
     uint8_t *stack;
+    long long *cum;         // cum[s]: children of stack records 0..s (n - depth each), summed
+    long long *iblk;        // start records: children per block of 256
     long long cap;
     uint8_t *children;
     int32_t *lbs;
     int *poff;              // first child of each popped parent; poff[np] = children
-    int *blk;
+    int *blk;               // per block of 256 children: survivors, leaves, survivors' children
     uint8_t *inc;
     long long *trace;
     long long trace_cap;
