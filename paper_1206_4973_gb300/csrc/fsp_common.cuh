@@ -45,7 +45,15 @@ struct fsp_instance {
     int2 *d_we;        // [n][P] position-major {w, e}: entry at position i of every pair
     uint8_t *d_rank;   // [P][n] position of job j in pair kl's order
     int *d_status;     // error flag of malformed records
+    struct FspHostCache *cache;  // events and kernel attributes reused across calls
 };
+
+// Host-side objects an instance keeps between calls (fsp_instance.cu): CUDA
+// events handed out and taken back, and the dynamic shared memory each
+// kernel was last allowed, so repeated searches skip the driver calls.
+int fsp_event_take(fsp_instance *I, cudaEvent_t *ev);
+void fsp_event_give(fsp_instance *I, cudaEvent_t ev);
+int fsp_allow_smem(fsp_instance *I, const void *kernel, size_t bytes);
 
 // By-value view for kernels.
 struct DevInst {

@@ -8,7 +8,48 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
 #include "fsp_common.cuh"
+
+struct FspHostCache {
+    std::mutex mu;
+    std::vector<cudaEvent_t> events;
+    std::unordered_map<const void *, size_t> smem;
+};
+
+int fsp_event_take(fsp_instance *I, cudaEvent_t *ev)
+{
+    {
+        std::lock_guard<std::mutex> g(I->cache->mu);
+        if (!I->cache->events.empty()) {
+            *ev = I->cache->events.back();
+            I->cache->events.pop_back();
+            return FSP_OK;
+        }
+    }
+    FSP_CUDA(cudaEventCreate(ev));
+    return FSP_OK;
+}
+
+void fsp_event_give(fsp_instance *I, cudaEvent_t ev)
+{
+    if (!ev) return;
+    std::lock_guard<std::mutex> g(I->cache->mu);
+    I->cache->events.push_back(ev);
+}
+
+int fsp_allow_smem(fsp_instance *I, const void *kernel, size_t bytes)
+{
+    std::lock_guard<std::mutex> g(I->cache->mu);
+    auto it = I->cache->smem.find(kernel);
+    if (it != I->cache->smem.end() && it->second >= bytes) return FSP_OK;
+    FSP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    I->cache->smem[kernel] = bytes;
+    return FSP_OK;
+}
 
 static thread_local char g_err[512];
 
@@ -115,6 +156,10 @@ static void free_instance(fsp_instance *I)
     cudaFree(I->d_we);
     cudaFree(I->d_rank);
     cudaFree(I->d_status);
+    if (I->cache) {
+        for (cudaEvent_t ev : I->cache->events) cudaEventDestroy(ev);
+        delete I->cache;
+    }
     free(I);
 }
 
@@ -134,6 +179,7 @@ extern "C" int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance 
         }
     fsp_instance *I = (fsp_instance *)calloc(1, sizeof(fsp_instance));
     if (!I) { fsp_set_error("fsp_create_instance: out of host memory"); return FSP_ERR_OOM; }
+    I->cache = new FspHostCache();
     I->n = n;
     I->m = m;
     I->P = m * (m - 1) / 2;

@@ -315,6 +315,20 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
 {
     SolveCtl *ctl = ws.ctl;
     const long long S = ctl->stack_size;
+    if (ctl->status != 0) {  // a malformed start record: the iteration does nothing
+        if (threadIdx.x == 0) {
+            ctl->n_parents = 0;
+            ctl->n_children = 0;
+            ctl->s_pop = S;
+            ctl->n_list = 0;
+            ctl->early = 0;
+            ctl->fam_next = 0;
+            ctl->best_key = ~0ull;
+            ctl->ub_iter = ctl->ub;
+            ws.poff[0] = 0;
+        }
+        return;
+    }
     const long long cand = S < pool ? S : pool;
     const long long top = ws.cum[S - 1];
     // children of the top i records, 0 <= i <= S
@@ -749,13 +763,11 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
     if (shp.ver == 2) {
         P->bb2 = pick_branch_bound2(shp.mt, shp.nv, shp.nw);
         if (!P->bb2) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
-        FSP_CUDA(cudaFuncSetAttribute((const void *)P->bb2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)shp.L2.bytes));
+        if ((rc = fsp_allow_smem(I, (const void *)P->bb2, shp.L2.bytes)) != FSP_OK) return rc;
     } else {
         P->bb = pick_branch_bound(shp.nw, shp.mt, shp.es);
         if (!P->bb) { fsp_set_error("fsp_solve: no kernel for this shape"); return FSP_ERR_ARG; }
-        FSP_CUDA(cudaFuncSetAttribute((const void *)P->bb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)shp.L.bytes));
+        if ((rc = fsp_allow_smem(I, (const void *)P->bb, shp.L.bytes)) != FSP_OK) return rc;
     }
     P->per_cta = shp.ver == 2 ? shp.B * FSP_NPT : shp.B;
     // each parent's children are bounded together where the family kernel's
@@ -767,8 +779,7 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
         if (w > 0 && (P->bf = pick_branch_family(shp.mt, shp.nv, P->L.learned)) != nullptr) {
             P->famL = family_smem_layout(I, shp.mt, shp.nv, w);
             P->famL.K = P->L.learned ? P->L.topk : 0;
-            FSP_CUDA(cudaFuncSetAttribute((const void *)P->bf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)P->famL.bytes));
+            if ((rc = fsp_allow_smem(I, (const void *)P->bf, P->famL.bytes)) != FSP_OK) return rc;
         }
     }
     P->bl = nullptr;
@@ -778,10 +789,8 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
         P->bl = pick_branch_learned(shp.mt, shp.nv, shp.nw);
         P->blist = pick_bound_list(shp.mt, shp.nv, shp.nw);
         if (!P->bl || !P->blist) { fsp_set_error("fsp_solve: no learned kernel for this shape"); return FSP_ERR_ARG; }
-        FSP_CUDA(cudaFuncSetAttribute((const void *)P->bl, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)shp.L2.bytes));
-        FSP_CUDA(cudaFuncSetAttribute((const void *)P->blist, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)shp.L2.bytes));
+        if ((rc = fsp_allow_smem(I, (const void *)P->bl, shp.L2.bytes)) != FSP_OK) return rc;
+        if ((rc = fsp_allow_smem(I, (const void *)P->blist, shp.L2.bytes)) != FSP_OK) return rc;
         int per_sm = 0;
         FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P->blist, shp.B, shp.L2.bytes));
         P->list_grid = I->sm_count * (per_sm > 0 ? per_sm : 1);
@@ -853,11 +862,11 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         if (e != cudaSuccess) { rc = fsp_cuda_fail(e, #call); goto out; } \
     } while (0)
     if (timed) {
-        TRY(cudaEventCreate(&ev0));
-        TRY(cudaEventCreate(&ev1));
+        if ((rc = fsp_event_take(I, &ev0)) != FSP_OK || (rc = fsp_event_take(I, &ev1)) != FSP_OK) goto out;
     }
     if (prof)
-        for (int i = 0; i < 5; ++i) TRY(cudaEventCreate(&pe[i]));
+        for (int i = 0; i < 5; ++i)
+            if ((rc = fsp_event_take(I, &pe[i])) != FSP_OK) goto out;
     if (timed) TRY(cudaEventRecord(ev0, st));
     if (o.pool_size == 0) tuner.start(per_cta, I->sm_count, tuner_max_pool(I), o.tune_window);
     if (I->n == 1) {
@@ -877,9 +886,17 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
         }
         TRY(cudaGetLastError());
+        // the start state is known here, so the first iteration goes out
+        // without a read-back (a malformed start record sets the device
+        // status, that iteration does nothing and the next read-back reports it)
+        memset(&h, 0, sizeof h);
+        h.stack_size = (o.init_nodes && o.init_count > 0) ? o.init_count : 1;
+        h.ub = ub0;
         for (long long it = 0;; ++it) {
-            TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
-            TRY(cudaStreamSynchronize(st));
+            if (it > 0) {
+                TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
+                TRY(cudaStreamSynchronize(st));
+            }
             if (prof && it > 0) {
                 float a = 0, b = 0, c = 0;
                 TRY(cudaEventElapsedTime(&a, pe[0], pe[1]));
@@ -1011,10 +1028,9 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     }
 #undef TRY
 out:
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    for (int i = 0; i < 5; ++i)
-        if (pe[i]) cudaEventDestroy(pe[i]);
+    fsp_event_give(I, ev0);
+    fsp_event_give(I, ev1);
+    for (int i = 0; i < 5; ++i) fsp_event_give(I, pe[i]);
     return rc;
 }
 
