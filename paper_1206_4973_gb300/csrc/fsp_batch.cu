@@ -14,7 +14,7 @@
 #include <chrono>
 #include <vector>
 
-#include "fsp_bound.cuh"
+#include "fsp_family.cuh"
 
 #define BB 256        // threads per CTA
 
@@ -104,6 +104,14 @@ struct BatchShared {  // static shared state of a CTA
     unsigned long long best_key;
 };
 
+// Shared memory of a batch CTA for an n x m instance: the family layout
+// (fsp_family.cuh) for the CTA's warps, then the parents' first-child offsets.
+__host__ __device__ inline size_t batch_smem_nm(int n, int m)
+{
+    const int mp = (m % 2 == 0) ? m + 1 : m, nv = (n + 1 + 15) / 16;
+    return fsp_align16(family_smem_layout_nm(n, m, mp, m, nv, BB / 32).bytes) + (size_t)(POOL_MAX / 2 + 4) * 4;
+}
+
 template <int MT, int NV, int NW>
 __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, BatchOut *out, uint8_t *perm_out,
                         const BatchWs &W, unsigned char *smem, BatchShared &sh)
@@ -111,11 +119,10 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
     const int n = D.n, tid = threadIdx.x;
     const int P = MT * (MT - 1) / 2, mp = (MT % 2 == 0) ? MT + 1 : MT;
     const int stride = (n + 1 + 15) / 16 * 16;
-    FspEntry *ent_s = reinterpret_cast<FspEntry *>(smem);
-    int2 *pq_s = reinterpret_cast<int2 *>(smem + fsp_align16((size_t)P * n * sizeof(FspEntry)));
-    int32_t *cs = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(pq_s) + fsp_align16((size_t)n * mp * 8));
-    int32_t *sq = cs + MT * BB;
-    int *poff = sq + MT * BB;
+    const FamSmem L = family_smem_layout_nm(n, MT, mp, MT, NV, BB / 32);
+    const FamView V = fam_view(smem, L, tid >> 5);
+    int2 *pq_s = V.pq;
+    int *poff = reinterpret_cast<int *>(smem + fsp_align16(L.bytes));
     int *warp_tot = sh.warp_tot;
     uint8_t *inc = sh.inc, *seq = sh.seq, *ord = sh.ord;
     int32_t *tot = sh.tot;
@@ -142,14 +149,11 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
             for (int h = k + 1; h < l; ++h) li += p[i * MT + h];
             rank += b_precedes(i, p[i * MT + k], p[i * MT + l], li, j, aj, bj, lj);
         }
-        FspEntry en;
-        en.w = aj + lj;
-        en.e = aj - bj;
-        en.bit = 1u << (j & 31);
-        en.widx = j >> 5;
-        ent_s[kl * n + rank] = en;
+        V.we[rank * P + kl] = make_int2(aj + lj, aj - bj);  // position-major entries
+        V.rk8[kl * V.rks8 + j] = (uint8_t)rank;             // each job's position
     }
     __syncthreads();
+    fam_tables_finish<MT>(V, n, mp);
 
     // NEH upper bound (unless given): jobs by decreasing total time, each
     // inserted at the position of smallest partial makespan, earliest on ties
@@ -203,7 +207,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
     for (int i = tid; i < stride; i += BB) W.stack[i] = (uint8_t)(i < n ? i : 0);
     __syncthreads();
     const int pool = D.pool;
-    int slot[1] = {tid};
+    const int warp = tid >> 5, lane = tid & 31;
     while (S > 0) {
         if (D.budget > 0 && bounded >= D.budget) { status = FSP_INCOMPLETE; break; }
         // selection: deepest parents while their children fit (at least one)
@@ -238,37 +242,15 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         if (S - np + nch > W.cap) { status = FSP_ERR_CAPACITY; break; }
         if (tid == 0) best_key = ~0ull;
         __syncthreads();
-        // branching + bounding, one child per thread per round
-        for (long long c = tid; c < nch; c += BB) {
-            uint32_t Um[1][NW];
-            int32_t lb[1];
-            int dch = -1;
-            if (c < nch) {
-                int lo = 0, hi = (int)np;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if ((long long)poff[mid] <= c) lo = mid;
-                    else hi = mid;
-                }
-                const int ci = (int)(c - poff[lo]);
-                FspRec<NV> par, ch;
-                fsp_load_rec(par, W.stack + (S - 1 - lo) * stride);
-                fsp_make_child(par, n, ci, ch);
-                fsp_store_rec(ch, W.children + c * stride);
-                dch = (int)fsp_rec_byte_dyn(ch, n);
-                int32_t C[MT], SQ[MT];
-                bool bad;
-                fsp_prologue<MT, NV, NW>(ch, n, pq_s, mp, Um[0], C, SQ, lb[0], bad);
-#pragma unroll
-                for (int k = 0; k < MT; ++k) {
-                    cs[k * BB + tid] = C[k];
-                    sq[k * BB + tid] = SQ[k];
-                }
-                fsp_pair_scan<MT, 1, NW>(n, ent_s, cs, sq, BB, slot, Um, lb);
-                W.lbs[c] = lb[0];
-                if (dch == n - 1 && lb[0] < ub)
-                    atomicMin(&best_key, ((unsigned long long)(uint32_t)lb[0] << 32) | (unsigned long long)c);
-            }
+        // branching + bounding: each warp bounds a parent's children together
+        for (long long f = warp; f < np; f += BB / 32) {
+            if (lane < NV)
+                reinterpret_cast<uint4 *>(V.recb)[lane] =
+                    reinterpret_cast<const uint4 *>(W.stack + (S - 1 - f) * stride)[lane];
+            __syncwarp();
+            fam_bound<MT, NV, false>(V, V.recb, poff[f], n, mp, stride, ub, W.children, W.lbs, &best_key, nullptr,
+                                     0, nullptr);
+            __syncwarp();
         }
         __syncthreads();
         const unsigned long long bk = best_key;
@@ -378,12 +360,6 @@ static bool batch_shape_ok(int n, int m)
     return false;
 }
 
-static size_t batch_smem(int n_max, int m_max)
-{
-    const int P = m_max * (m_max - 1) / 2, mp = (m_max % 2 == 0) ? m_max + 1 : m_max;
-    return fsp_align16((size_t)P * n_max * sizeof(FspEntry)) + fsp_align16((size_t)n_max * mp * 8) +
-           (size_t)2 * m_max * BB * 4 + (size_t)(POOL_MAX / 2 + 4) * 4;
-}
 
 static void batch_free(fsp_batch *B)
 {
@@ -429,6 +405,7 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
     B->count = count;
     long long off = 0;
     int n_max = 2, m_max = 5, s_max = 16;
+    size_t smem_max = 0;
     for (int i = 0; i < count; ++i) {
         const int n = shapes[2 * i], m = shapes[2 * i + 1];
         if (!batch_shape_ok(n, m) || pools[i] < 1 || pools[i] > POOL_MAX) {
@@ -451,6 +428,7 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
         off += (long long)n * m;
         if (n > n_max) n_max = n;
         if (m > m_max) m_max = m;
+        if (batch_smem_nm(n, m) > smem_max) smem_max = batch_smem_nm(n, m);
         const int s = (n + 1 + 15) / 16 * 16;
         if (s > s_max) s_max = s;
     }
@@ -462,7 +440,7 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
     {
         int optin = 0;
         TRYB(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, B->device));
-        B->smem = batch_smem(n_max, m_max);
+        B->smem = smem_max;
         if ((int)B->smem > optin) {
             fsp_set_error("fsp_batch_create: instances too large for one CTA's shared memory");
             rc = FSP_ERR_ARG;
