@@ -54,6 +54,10 @@ struct fsp_instance {
 int fsp_event_take(fsp_instance *I, cudaEvent_t *ev);
 void fsp_event_give(fsp_instance *I, cudaEvent_t ev);
 int fsp_allow_smem(fsp_instance *I, const void *kernel, size_t bytes);
+// Pinned host blocks of FSP_PINNED_BYTES for asynchronous read-backs.
+#define FSP_PINNED_BYTES 1024
+int fsp_pinned_take(fsp_instance *I, void **p);
+void fsp_pinned_give(fsp_instance *I, void *p);
 
 // By-value view for kernels.
 struct DevInst {

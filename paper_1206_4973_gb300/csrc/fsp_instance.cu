@@ -17,6 +17,7 @@
 struct FspHostCache {
     std::mutex mu;
     std::vector<cudaEvent_t> events;
+    std::vector<void *> pinned;
     std::unordered_map<const void *, size_t> smem;
 };
 
@@ -39,6 +40,27 @@ void fsp_event_give(fsp_instance *I, cudaEvent_t ev)
     if (!ev) return;
     std::lock_guard<std::mutex> g(I->cache->mu);
     I->cache->events.push_back(ev);
+}
+
+int fsp_pinned_take(fsp_instance *I, void **p)
+{
+    {
+        std::lock_guard<std::mutex> g(I->cache->mu);
+        if (!I->cache->pinned.empty()) {
+            *p = I->cache->pinned.back();
+            I->cache->pinned.pop_back();
+            return FSP_OK;
+        }
+    }
+    FSP_CUDA(cudaMallocHost(p, FSP_PINNED_BYTES));
+    return FSP_OK;
+}
+
+void fsp_pinned_give(fsp_instance *I, void *p)
+{
+    if (!p) return;
+    std::lock_guard<std::mutex> g(I->cache->mu);
+    I->cache->pinned.push_back(p);
 }
 
 int fsp_allow_smem(fsp_instance *I, const void *kernel, size_t bytes)
@@ -158,6 +180,7 @@ static void free_instance(fsp_instance *I)
     cudaFree(I->d_status);
     if (I->cache) {
         for (cudaEvent_t ev : I->cache->events) cudaEventDestroy(ev);
+        for (void *p : I->cache->pinned) cudaFreeHost(p);
         delete I->cache;
     }
     free(I);

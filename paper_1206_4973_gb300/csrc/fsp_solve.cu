@@ -311,11 +311,15 @@ __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot)
 // largest i <= min(S, pool) whose children fit the pool (at least one),
 // found by a parallel search that narrows the interval SELECT_B-fold per
 // round, and the parents' first-child offsets follow from cum directly.
-__global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stride, long long pool)
+__global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stride, long long pool,
+                                                    long long budget, long long max_it)
 {
     SolveCtl *ctl = ws.ctl;
     const long long S = ctl->stack_size;
-    if (ctl->status != 0) {  // a malformed start record: the iteration does nothing
+    // nothing to do: an error (a malformed start record), an empty stack, or
+    // a stop the host reads one iteration later (node budget, iteration cap)
+    if (ctl->status != 0 || S == 0 || (budget > 0 && ctl->cnt[0] >= budget) ||
+        (max_it > 0 && ctl->cnt[4] >= max_it)) {
         if (threadIdx.x == 0) {
             ctl->n_parents = 0;
             ctl->n_children = 0;
@@ -474,6 +478,7 @@ __global__ void __launch_bounds__(SOLVE_B) k_push(SolveWs ws, int n, int stride)
     __shared__ long long red[5][SOLVE_B / 32];
     __shared__ int wcnt[SOLVE_B / 32], wr[SOLVE_B / 32];
     SolveCtl *ctl = ws.ctl;
+    if (ctl->n_parents == 0) return;  // an iteration that did nothing changes nothing
     const long long nch = ctl->n_children;
     const int ubn = solve_ub_new(ctl);
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -851,6 +856,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t pe[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t rb[2] = {nullptr, nullptr};  // read-backs of the control block
+    void *pin = nullptr;                     // their pinned host buffers
     double t_sel = 0, t_bb = 0, t_cmp = 0, t_inf = 0;
     PoolTuner tuner;
     SolveCtl h;
@@ -892,6 +899,77 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         memset(&h, 0, sizeof h);
         h.stack_size = (o.init_nodes && o.init_count > 0) ? o.init_count : 1;
         h.ub = ub0;
+        // one iteration on the stream with pool size `pool`
+        auto launch_iter = [&](long long pool) -> int {
+            cudaError_t le;
+#define LTRY(call)                                                  \
+    do {                                                            \
+        le = (call);                                                \
+        if (le != cudaSuccess) return fsp_cuda_fail(le, #call);     \
+    } while (0)
+            const int grid = (int)((pool + I->n + SOLVE_B - 1) / SOLVE_B);
+            const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
+            if (prof) LTRY(cudaEventRecord(pe[0], st));
+            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool, o.node_budget, o.max_iterations);
+            if (prof) LTRY(cudaEventRecord(pe[1], st));
+            if (P->bl) {
+                const long long npar = pool / 2 + 2;  // stacked nodes have >= 2 children
+                int frc = fsp_mlp_topk_parents(o.model, I, ws.stack, &ws.ctl->s_pop, &ws.ctl->n_parents, npar,
+                                               L.topk, ws.topk, st);
+                if (frc == FSP_ERR_ARG) {  // network shape without the fused kernel
+                    launch_parent_features(D, ws, T, npar, st);
+                    frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
+                    if (frc == FSP_OK) launch_topk(ws, I->P, L.topk, npar, st);
+                }
+                if (frc != FSP_OK) return frc;
+                if (prof) LTRY(cudaEventRecord(pe[4], st));
+                const int grid_l = (int)((pool + I->n + 255) / 256);
+                P->bl<<<grid_l, 256, shp.L2.bytes, st>>>(D, ws, shp.L2, L.topk);
+                P->blist<<<P->list_grid, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
+            } else if (P->bf) {
+                if (P->L.learned) {  // each parent's predicted pairs first
+                    const long long npar = pool / 2 + 2;
+                    int frc = fsp_mlp_topk_parents(o.model, I, ws.stack, &ws.ctl->s_pop, &ws.ctl->n_parents, npar,
+                                                   L.topk, ws.topk, st);
+                    if (frc == FSP_ERR_ARG) {  // network shape without the fused kernel
+                        launch_parent_features(D, ws, T, npar, st);
+                        frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
+                        if (frc == FSP_OK) launch_topk(ws, I->P, L.topk, npar, st);
+                    }
+                    if (frc != FSP_OK) return frc;
+                    if (prof) LTRY(cudaEventRecord(pe[4], st));
+                }
+                // at most pool / 2 + 1 parents: stacked nodes have >= 2 children
+                const long long fam = (pool / 2 + 1 + P->famL.warps - 1) / P->famL.warps;
+                const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
+                P->bf<<<grid_f, P->famL.warps * 32, P->famL.bytes, st>>>(D, ws, P->famL);
+            } else if (bb2) {
+                bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
+            } else {
+                bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
+            }
+            if (prof) LTRY(cudaEventRecord(pe[2], st));
+            k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
+            k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
+            if (prof) LTRY(cudaEventRecord(pe[3], st));
+            LTRY(cudaGetLastError());
+#undef LTRY
+            return FSP_OK;
+        };
+        auto pool_of = [&](long long it) -> long long {  // fixed, replayed, or the settled tuner's
+            long long pool = tuner.on ? tuner.cur : o.pool_size;
+            if (o.schedule && o.schedule_len > 0) pool = o.schedule[it < o.schedule_len ? it : o.schedule_len - 1];
+            if (o.schedule_out && it < o.schedule_out_cap) o.schedule_out[it] = pool;
+            return pool;
+        };
+        // Without logging or phase times, and once the tuner (if any) has
+        // settled, the next iteration depends on nothing the host reads back,
+        // so it is launched before the read-back of the previous one:
+        // k_select makes an iteration past a stop (empty stack, budget,
+        // iteration cap, error) do nothing, and the host stops one read-back
+        // later.  Until then iterations go out one at a time.
+        const bool may_ahead = !prof && !o.log_nodes;
+        long long it0 = -1;  // first iteration launched ahead
         for (long long it = 0;; ++it) {
             if (it > 0) {
                 TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
@@ -930,6 +1008,10 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if (h.stack_size == 0) break;
             if (o.node_budget > 0 && h.cnt[0] >= o.node_budget) { rc = FSP_INCOMPLETE; break; }
             if (o.max_iterations > 0 && it >= o.max_iterations) { rc = FSP_INCOMPLETE; break; }
+            if (may_ahead && ((o.schedule && o.schedule_len > 0) || !tuner.on || tuner.phase == 2)) {
+                it0 = it;
+                break;
+            }
             long long pool = o.pool_size;
             if (o.schedule && o.schedule_len > 0)
                 pool = o.schedule[it < o.schedule_len ? it : o.schedule_len - 1];
@@ -938,52 +1020,33 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 pool = tuner.cur;
             }
             if (o.schedule_out && it < o.schedule_out_cap) o.schedule_out[it] = pool;
-            const int grid = (int)((pool + I->n + SOLVE_B - 1) / SOLVE_B);
-            const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
-            if (prof) TRY(cudaEventRecord(pe[0], st));
-            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool);
-            if (prof) TRY(cudaEventRecord(pe[1], st));
-            if (P->bl) {
-                const long long npar = pool / 2 + 2;  // stacked nodes have >= 2 children
-                int frc = fsp_mlp_topk_parents(o.model, I, ws.stack, &ws.ctl->s_pop, &ws.ctl->n_parents, npar,
-                                               L.topk, ws.topk, st);
-                if (frc == FSP_ERR_ARG) {  // network shape without the fused kernel
-                    launch_parent_features(D, ws, T, npar, st);
-                    frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
-                    if (frc == FSP_OK) launch_topk(ws, I->P, L.topk, npar, st);
+            if ((rc = launch_iter(pool)) != FSP_OK) goto out;
+        }
+        if (it0 >= 0) {
+            if ((rc = fsp_pinned_take(I, &pin)) != FSP_OK) goto out;
+            if ((rc = fsp_event_take(I, &rb[0])) != FSP_OK || (rc = fsp_event_take(I, &rb[1])) != FSP_OK) goto out;
+            SolveCtl *hb = reinterpret_cast<SolveCtl *>(pin);
+            if ((rc = launch_iter(pool_of(it0))) != FSP_OK) goto out;
+            TRY(cudaMemcpyAsync(&hb[it0 & 1], ws.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
+            TRY(cudaEventRecord(rb[it0 & 1], st));
+            for (long long it = it0 + 1;; ++it) {
+                if ((rc = launch_iter(pool_of(it))) != FSP_OK) goto out;
+                TRY(cudaMemcpyAsync(&hb[it & 1], ws.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
+                TRY(cudaEventRecord(rb[it & 1], st));
+                TRY(cudaEventSynchronize(rb[(it - 1) & 1]));
+                h = hb[(it - 1) & 1];  // the state after `it` iterations
+                if (h.status != 0) {
+                    rc = h.status;
+                    fsp_set_error(rc == FSP_ERR_CAPACITY ? "fsp_solve: stack capacity exceeded"
+                                  : rc == FSP_ERR_ARG ? "fsp_solve: malformed init node (not a permutation "
+                                                        "or depth > n-2)"
+                                                      : "fsp_solve: device error");
+                    break;
                 }
-                if (frc != FSP_OK) { rc = frc; goto out; }
-                if (prof) TRY(cudaEventRecord(pe[4], st));
-                const int grid_l = (int)((pool + I->n + 255) / 256);
-                P->bl<<<grid_l, 256, shp.L2.bytes, st>>>(D, ws, shp.L2, L.topk);
-                P->blist<<<P->list_grid, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
-            } else if (P->bf) {
-                if (P->L.learned) {  // each parent's predicted pairs first
-                    const long long npar = pool / 2 + 2;
-                    int frc = fsp_mlp_topk_parents(o.model, I, ws.stack, &ws.ctl->s_pop, &ws.ctl->n_parents, npar,
-                                                   L.topk, ws.topk, st);
-                    if (frc == FSP_ERR_ARG) {  // network shape without the fused kernel
-                        launch_parent_features(D, ws, T, npar, st);
-                        frc = fsp_mlp_forward_dev(o.model, ws.px, &ws.ctl->n_parents, npar, ws.pscore, st);
-                        if (frc == FSP_OK) launch_topk(ws, I->P, L.topk, npar, st);
-                    }
-                    if (frc != FSP_OK) { rc = frc; goto out; }
-                    if (prof) TRY(cudaEventRecord(pe[4], st));
-                }
-                // at most pool / 2 + 1 parents: stacked nodes have >= 2 children
-                const long long fam = (pool / 2 + 1 + P->famL.warps - 1) / P->famL.warps;
-                const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
-                P->bf<<<grid_f, P->famL.warps * 32, P->famL.bytes, st>>>(D, ws, P->famL);
-            } else if (bb2) {
-                bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
-            } else {
-                bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
+                if (h.stack_size == 0) break;
+                if (o.node_budget > 0 && h.cnt[0] >= o.node_budget) { rc = FSP_INCOMPLETE; break; }
+                if (o.max_iterations > 0 && it >= o.max_iterations) { rc = FSP_INCOMPLETE; break; }
             }
-            if (prof) TRY(cudaEventRecord(pe[2], st));
-            k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
-            k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
-            if (prof) TRY(cudaEventRecord(pe[3], st));
-            TRY(cudaGetLastError());
         }
     }
     if (timed) {
@@ -1030,6 +1093,9 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
 out:
     fsp_event_give(I, ev0);
     fsp_event_give(I, ev1);
+    fsp_event_give(I, rb[0]);
+    fsp_event_give(I, rb[1]);
+    fsp_pinned_give(I, pin);
     for (int i = 0; i < 5; ++i) fsp_event_give(I, pe[i]);
     return rc;
 }
