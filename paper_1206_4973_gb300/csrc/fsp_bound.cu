@@ -175,11 +175,9 @@ extern "C" int fsp_bound_pool(fsp_instance *I, const uint8_t *nodes, int64_t cou
     if (s.ver == 2) {
         BoundPool2Fn fn2 = pick_bound_pool2(s.mt, s.nv, s.nw);
         if (!fn2) { fsp_set_error("fsp_bound_pool: no kernel for this shape"); return FSP_ERR_ARG; }
-        FSP_CUDA(cudaFuncSetAttribute((const void *)fn2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)s.L2.bytes));
-        int per_sm = 0;
-        FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn2, s.B, s.L2.bytes));
-        if (per_sm < 1) per_sm = 1;
+        if ((rc = fsp_allow_smem(I, (const void *)fn2, s.L2.bytes)) != FSP_OK) return rc;
+        int per_sm = 1;
+        if ((rc = fsp_blocks_per_sm(I, (const void *)fn2, s.B, s.L2.bytes, &per_sm)) != FSP_OK) return rc;
         const long long per_block = (long long)s.B * FSP_NPT;
         long long need = (count + per_block - 1) / per_block;
         long long grid = (long long)I->sm_count * per_sm;
@@ -191,11 +189,9 @@ extern "C" int fsp_bound_pool(fsp_instance *I, const uint8_t *nodes, int64_t cou
     }
     BoundPoolFn fn = pick_bound_pool(s.nw, s.mt, s.es);
     if (!fn) { fsp_set_error("fsp_bound_pool: no kernel for this shape"); return FSP_ERR_ARG; }
-    FSP_CUDA(cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)s.L.bytes));
-    int per_sm = 0;
-    FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, s.B, s.L.bytes));
-    if (per_sm < 1) per_sm = 1;
+    if ((rc = fsp_allow_smem(I, (const void *)fn, s.L.bytes)) != FSP_OK) return rc;
+    int per_sm = 1;
+    if ((rc = fsp_blocks_per_sm(I, (const void *)fn, s.B, s.L.bytes, &per_sm)) != FSP_OK) return rc;
     long long need = (count + s.B - 1) / s.B;
     long long grid = (long long)I->sm_count * per_sm;
     if (need < grid) grid = need;

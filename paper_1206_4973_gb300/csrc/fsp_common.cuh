@@ -54,6 +54,9 @@ struct fsp_instance {
 int fsp_event_take(fsp_instance *I, cudaEvent_t *ev);
 void fsp_event_give(fsp_instance *I, cudaEvent_t ev);
 int fsp_allow_smem(fsp_instance *I, const void *kernel, size_t bytes);
+// Resident CTAs per SM of a kernel at a block size and dynamic shared memory
+// (at least 1), remembered per instance.
+int fsp_blocks_per_sm(fsp_instance *I, const void *kernel, int block, size_t smem, int *per_sm);
 // Pinned host blocks of FSP_PINNED_BYTES for asynchronous read-backs.
 #define FSP_PINNED_BYTES 1024
 int fsp_pinned_take(fsp_instance *I, void **p);

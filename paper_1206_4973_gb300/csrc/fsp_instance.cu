@@ -19,6 +19,19 @@ struct FspHostCache {
     std::vector<cudaEvent_t> events;
     std::vector<void *> pinned;
     std::unordered_map<const void *, size_t> smem;
+    struct OccKey {
+        const void *k;
+        int block;
+        size_t smem;
+        bool operator==(const OccKey &o) const { return k == o.k && block == o.block && smem == o.smem; }
+    };
+    struct OccHash {
+        size_t operator()(const OccKey &o) const
+        {
+            return std::hash<const void *>()(o.k) ^ (std::hash<size_t>()(o.smem) * 31u) ^ (size_t)o.block;
+        }
+    };
+    std::unordered_map<OccKey, int, OccHash> occ;
 };
 
 int fsp_event_take(fsp_instance *I, cudaEvent_t *ev)
@@ -61,6 +74,23 @@ void fsp_pinned_give(fsp_instance *I, void *p)
     if (!p) return;
     std::lock_guard<std::mutex> g(I->cache->mu);
     I->cache->pinned.push_back(p);
+}
+
+int fsp_blocks_per_sm(fsp_instance *I, const void *kernel, int block, size_t smem, int *per_sm)
+{
+    const FspHostCache::OccKey key{kernel, block, smem};
+    {
+        std::lock_guard<std::mutex> g(I->cache->mu);
+        auto it = I->cache->occ.find(key);
+        if (it != I->cache->occ.end()) { *per_sm = it->second; return FSP_OK; }
+    }
+    int n = 0;
+    FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem));
+    if (n < 1) n = 1;
+    std::lock_guard<std::mutex> g(I->cache->mu);
+    I->cache->occ[key] = n;
+    *per_sm = n;
+    return FSP_OK;
 }
 
 int fsp_allow_smem(fsp_instance *I, const void *kernel, size_t bytes)

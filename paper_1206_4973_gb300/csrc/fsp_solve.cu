@@ -796,9 +796,9 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
         if (!P->bl || !P->blist) { fsp_set_error("fsp_solve: no learned kernel for this shape"); return FSP_ERR_ARG; }
         if ((rc = fsp_allow_smem(I, (const void *)P->bl, shp.L2.bytes)) != FSP_OK) return rc;
         if ((rc = fsp_allow_smem(I, (const void *)P->blist, shp.L2.bytes)) != FSP_OK) return rc;
-        int per_sm = 0;
-        FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P->blist, shp.B, shp.L2.bytes));
-        P->list_grid = I->sm_count * (per_sm > 0 ? per_sm : 1);
+        int per_sm = 1;
+        if ((rc = fsp_blocks_per_sm(I, (const void *)P->blist, shp.B, shp.L2.bytes, &per_sm)) != FSP_OK) return rc;
+        P->list_grid = I->sm_count * per_sm;
     }
     if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
         fsp_set_error("fsp_solve: workspace must be 256-byte aligned");

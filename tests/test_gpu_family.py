@@ -75,3 +75,29 @@ def test_family_and_per_child_kernels_search_alike(F, n, m, seed, pool, budget):
     assert (a["perm"] is None) == (b["perm"] is None)
     if a["perm"] is not None:
         assert list(a["perm"]) == list(b["perm"])
+
+
+@pytest.mark.parametrize("n,m,seed,pool,budget,max_it", [(12, 5, 0, 64, 0, 0), (20, 20, 6, 4096, 150000, 0),
+                                                         (20, 10, 5, 0, 300000, 0), (15, 5, 3, 128, 0, 37),
+                                                         (50, 5, 3, 2048, 80000, 0)])
+def test_launching_ahead_gives_the_same_search(F, n, m, seed, pool, budget, max_it):
+    """Iterations launched one ahead of their read-back (the default) and one
+    at a time (forced by phase timing) stop at the same budget or iteration
+    cap with the same state; pool 0 runs the tuner first."""
+    p = inputs.instance(n, m, seed)
+    inst = F.fsp_create_instance(p)
+    ub0, perm0 = F.fsp_neh(inst)
+    out_a = np.zeros((60000, inst.stride), np.uint8)
+    out_b = np.zeros_like(out_a)
+    kw = dict(ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=budget, max_iterations=max_it,
+              trace_cap=100000, schedule_cap=100000)
+    a = F.fsp_solve(inst, out_nodes=out_a, **kw)
+    if pool == 0:  # the tuner's choices depend on measured times: replay them
+        kw = dict(kw, pool_size=1024, schedule=a["schedule"])
+    b = F.fsp_solve(inst, out_nodes=out_b, profile=True, **kw)
+    for key in KEYS:
+        assert a[key] == b[key], key
+    assert np.array_equal(a["trace"], b["trace"])
+    assert np.array_equal(a["schedule"], b["schedule"])
+    k = min(a["stack_left"], len(out_a))
+    assert np.array_equal(out_a[:k], out_b[:k])
