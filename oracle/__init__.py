@@ -61,14 +61,14 @@ def _load():
                 "orc_release_times": (None, [c_int, c_int, i32p, u8p, c_int, i32p]),
                 "orc_makespan": (c_i32, [c_int, c_int, i32p, u8p, c_int]),
                 "orc_check_node": (c_int, [c_int, u8p, c_int]),
-                "orc_bound_pool": (c_int, [c_int, c_int, i32p, u8p, c_i64, c_int, i32p]),
-                "orc_lb_parts": (c_int, [c_int, c_int, i32p, u8p, c_int, i32p, i32p, i32p]),
+                "orc_bound_pool": (c_int, [c_int, c_int, i32p, u8p, c_i64, c_int, c_int, i32p]),
+                "orc_lb_parts": (c_int, [c_int, c_int, i32p, u8p, c_int, c_int, i32p, i32p, i32p]),
                 "orc_tables_dump": (c_int, [c_int, c_int, i32p, i32p, i32p, u8p]),
                 "orc_bruteforce": (c_i32, [c_int, c_int, i32p, u8p]),
                 "orc_neh": (c_i32, [c_int, c_int, i32p, u8p]),
                 "orc_solve": (c_int, [c_int, c_int, i32p, c_i32, c_i64, c_i64, i64p, c_i64,
                                       u8p, c_i64, c_int, c_i64,
-                                      i32p, u8p, i64p, i64p, c_i64, u8p, c_i64, i64p]),
+                                      i32p, u8p, i64p, i64p, c_i64, u8p, c_i64, i64p, c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -129,32 +129,33 @@ def tables(p):
     return q, lag, order
 
 
-def lb_parts(p, perm, d: int):
-    """The node bound and its parts: (LB, LB1, [LB_kl per pair])."""
+def lb_parts(p, perm, d: int, bound: int = 0):
+    """The node bound and its parts: (LB, LB1, [LB_kl per pair]).  bound 1: the
+    release times strengthened by the smallest head (fsp_oracle.c, orc_lb)."""
     p, n, m = _inst(p)
     perm = np.ascontiguousarray(perm, dtype=np.uint8)
     lb = ctypes.c_int32(0)
     lb1 = ctypes.c_int32(0)
     pv = np.zeros(max(num_pairs(m), 1), np.int32)
-    rc = _load().orc_lb_parts(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8), int(d),
+    rc = _load().orc_lb_parts(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8), int(d), int(bound),
                               ctypes.byref(lb), ctypes.byref(lb1), _p(pv, ctypes.c_int32))
     if rc != OK:
         raise ValueError("invalid node")
     return int(lb.value), int(lb1.value), pv[: num_pairs(m)].copy()
 
 
-def lb(p, perm, d: int) -> int:
-    return lb_parts(p, perm, d)[0]
+def lb(p, perm, d: int, bound: int = 0) -> int:
+    return lb_parts(p, perm, d, bound)[0]
 
 
-def bound_pool(p, nodes) -> np.ndarray:
+def bound_pool(p, nodes, bound: int = 0) -> np.ndarray:
     """Bound every record of nodes (uint8 [count, stride]: perm[n], depth at byte n)."""
     p, n, m = _inst(p)
     nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
     count, stride = nodes.shape
     out = np.zeros(count, np.int32)
     rc = _load().orc_bound_pool(n, m, _p(p, ctypes.c_int32), _p(nodes, ctypes.c_uint8), count,
-                                stride, _p(out, ctypes.c_int32))
+                                stride, int(bound), _p(out, ctypes.c_int32))
     if rc != OK:
         raise ValueError(f"orc_bound_pool failed ({rc})")
     return out
@@ -178,7 +179,7 @@ def neh(p):
 
 def solve(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, schedule=None,
           trace_cap: int = 0, ub0_perm=None, init_nodes=None, max_iterations: int = 0,
-          export_stack: bool = False):
+          export_stack: bool = False, bound: int = 0):
     """Serial pool-synchronous depth-first B&B (Sec. II-A operators, Sec. III pool).
 
     Returns a dict with status, cmax, perm (None if no schedule beat ub0 and no
@@ -204,7 +205,7 @@ def solve(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, schedule=No
             None if init is None else _p(init, ctypes.c_uint8), 0 if init is None else len(init),
             stride, int(max_iterations), ctypes.byref(cmax), _p(perm, ctypes.c_uint8),
             _p(stats, ctypes.c_int64), _p(trace, ctypes.c_int64) if trace_cap > 0 else None,
-            int(trace_cap), None, 0, ctypes.byref(out_count)]
+            int(trace_cap), None, 0, ctypes.byref(out_count), int(bound)]
     rc = _load().orc_solve(*args)
     if rc == ERR_ARG:
         raise ValueError("orc_solve: invalid arguments or init node")

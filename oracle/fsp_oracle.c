@@ -184,10 +184,16 @@ int orc_check_node(int n, const uint8_t *perm, int d)
  *              t_k += a_j; t_l = max(t_l, t_k + lag_j) + b_j;
  *            LB_kl = t_l + qmin_l                            (two machines)
  *   LB       max(LB1, max over pairs LB_kl)
+ * variant 1 (release times strengthened by the smallest head, one of the
+ * refinements of the Lageweg-Lenstra-Rinnooy Kan family of bounds): a
+ * remaining job starts on machine k only after the prefix frees k and after
+ * it has been processed on machine k-1, so with U non-empty
+ *     R_0 = C_0,   R_k = max(C_k, R_{k-1} + min over U of p[j][k-1]),
+ * and every C_k above is replaced by R_k (variant 0: R = C).
  * lb1_out (may be NULL) receives LB1; pair_out (may be NULL) receives the
  * m(m-1)/2 values LB_kl in pair order. */
 int32_t orc_lb(int n, int m, const int32_t *p, const int32_t *q, const int32_t *lag,
-               const uint8_t *order, const uint8_t *perm, int d,
+               const uint8_t *order, const uint8_t *perm, int d, int variant,
                int32_t *lb1_out, int32_t *pair_out)
 {
     int32_t C[ORC_MAXM], S[ORC_MAXM], qmin[ORC_MAXM];
@@ -208,6 +214,20 @@ int32_t orc_lb(int n, int m, const int32_t *p, const int32_t *q, const int32_t *
         }
         S[k] = s;
         qmin[k] = mn;
+    }
+
+    if (variant == 1 && d < n) {
+        /* the smallest time any remaining job spends on machine k-1 */
+        for (int k = 1; k < m; k++) {
+            int32_t mn = 0;
+            int first = 1;
+            for (int j = 0; j < n; j++) {
+                if (!inU[j]) continue;
+                if (first || pt(p, m, j, k - 1) < mn) mn = pt(p, m, j, k - 1);
+                first = 0;
+            }
+            C[k] = imax(C[k], C[k - 1] + mn);  /* C[k-1] already holds R_{k-1} */
+        }
     }
 
     int32_t lb1 = 0;
@@ -275,7 +295,7 @@ static int shape_ok(int n, int m, const int32_t *p)
 /* Bound a pool of node records: record t is nodes[t*stride ..], perm bytes
  * 0..n-1, depth at byte n.  Returns ORC_ERR_ARG if any record is invalid. */
 int orc_bound_pool(int n, int m, const int32_t *p, const uint8_t *nodes, int64_t count,
-                   int stride, int32_t *lb_out)
+                   int stride, int variant, int32_t *lb_out)
 {
     orc_tables t;
     if (!shape_ok(n, m, p) || count < 0 || stride < n + 1) return ORC_ERR_ARG;
@@ -284,20 +304,20 @@ int orc_bound_pool(int n, int m, const int32_t *p, const uint8_t *nodes, int64_t
     for (int64_t i = 0; i < count; i++) {
         const uint8_t *rec = nodes + (size_t)i * stride;
         if (!orc_check_node(n, rec, rec[n])) { rc = ORC_ERR_ARG; break; }
-        lb_out[i] = orc_lb(n, m, p, t.q, t.lag, t.order, rec, rec[n], NULL, NULL);
+        lb_out[i] = orc_lb(n, m, p, t.q, t.lag, t.order, rec, rec[n], variant, NULL, NULL);
     }
     tables_free(&t);
     return rc;
 }
 
 /* Per-node parts: LB1 and every LB_kl of one node (for pins). */
-int orc_lb_parts(int n, int m, const int32_t *p, const uint8_t *perm, int d,
+int orc_lb_parts(int n, int m, const int32_t *p, const uint8_t *perm, int d, int variant,
                  int32_t *lb_out, int32_t *lb1_out, int32_t *pair_out)
 {
     orc_tables t;
     if (!shape_ok(n, m, p) || !orc_check_node(n, perm, d)) return ORC_ERR_ARG;
     if (tables_make(&t, n, m, p) != ORC_OK) { tables_free(&t); return ORC_ERR_OOM; }
-    *lb_out = orc_lb(n, m, p, t.q, t.lag, t.order, perm, d, lb1_out, pair_out);
+    *lb_out = orc_lb(n, m, p, t.q, t.lag, t.order, perm, d, variant, lb1_out, pair_out);
     tables_free(&t);
     return ORC_OK;
 }
@@ -436,9 +456,9 @@ int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t
               const uint8_t *init, int64_t init_count, int rec_stride, int64_t max_iterations,
               int32_t *cmax, uint8_t *perm_out, int64_t *stats,
               int64_t *trace, int64_t trace_cap,
-              uint8_t *out, int64_t out_cap, int64_t *out_count)
+              uint8_t *out, int64_t out_cap, int64_t *out_count, int variant)
 {
-    if (!shape_ok(n, m, p) || pool < 1) return ORC_ERR_ARG;
+    if (!shape_ok(n, m, p) || pool < 1 || variant < 0 || variant > 1) return ORC_ERR_ARG;
     if ((init || out) && rec_stride < n + 1) return ORC_ERR_ARG;
     if (init)
         for (int64_t i = 0; i < init_count; i++) {
@@ -539,7 +559,7 @@ int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t
         /* bounding */
         for (int64_t i = 0; i < nch; i++) {
             const uint8_t *ch = children + (size_t)i * w;
-            lbs[i] = orc_lb(n, m, p, t.q, t.lag, t.order, ch, ch[n], NULL, NULL);
+            lbs[i] = orc_lb(n, m, p, t.q, t.lag, t.order, ch, ch[n], variant, NULL, NULL);
         }
         stats[ST_BOUNDED] += nch;
         stats[ST_BRANCHED] += np;

@@ -193,6 +193,66 @@ def test_bound_pool_matches_single_node_and_rejects_bad_records():
         oracle.bound_pool(p, bad)
 
 
+# ----------------------------------------- bound variant: smallest heads ---
+def test_head_variant_hand_worked():
+    """Job 0 scheduled (times 5, 1, 1); jobs 1 (3, 4, 9) and 2 (4, 3, 8) remain.
+    Prefix release times C = (5, 6, 7).  A remaining job reaches machine 1 no
+    earlier than 5 + min(3, 4) = 8 and machine 2 no earlier than 8 + min(4, 3)
+    = 11, so the machine-2 one-machine term rises from 7 + 17 = 24 to 11 + 17
+    = 28 (tails: job 1 (13, 9, 0), job 2 (11, 8, 0)); the best completion is
+    29 either way round."""
+    p = np.array([[5, 1, 1], [3, 4, 9], [4, 3, 8]], np.int32)
+    perm = np.array([0, 1, 2], np.uint8)
+    _, lb1_base, _ = oracle.lb_parts(p, perm, 1)
+    lb_head, lb1_head, _ = oracle.lb_parts(p, perm, 1, bound=1)
+    assert lb1_base == 24 and lb1_head == 28
+    assert lb_head <= 29 == min(longest_path_makespan(p, [0, 1, 2]), longest_path_makespan(p, [0, 2, 1]))
+
+
+@pytest.mark.parametrize("n,m,seed", [(6, 3, 141), (7, 4, 142), (5, 6, 143), (7, 5, 144)])
+def test_head_variant_is_valid_dominant_and_exact_at_the_leaves(n, m, seed):
+    p = inputs.instance(n, m, seed)
+    for perm, d in rand_nodes(n, 14, seed + 7):
+        base = oracle.lb(p, perm, d)
+        head = oracle.lb(p, perm, d, bound=1)
+        best = min(oracle.makespan(p, list(perm[:d]) + list(o))
+                   for o in itertools.permutations(perm[d:]))
+        assert base <= head <= best
+        if d >= n - 1:
+            assert head == best == longest_path_makespan(p, list(perm))
+    # the one-machine part is where the heads act (the pair bounds already
+    # carry most of them): it rises on some nodes and never falls
+    rises = 0
+    for perm, d in rand_nodes(n, 200, seed + 8):
+        lb1_base = oracle.lb_parts(p, perm, d)[1]
+        lb1_head = oracle.lb_parts(p, perm, d, bound=1)[1]
+        assert lb1_head >= lb1_base
+        rises += lb1_head > lb1_base
+    assert rises > 0
+
+
+@pytest.mark.parametrize("seed", [151, 152])
+def test_head_variant_exact_at_m2(seed):
+    """At m = 2 the base bound is already the best completion (Johnson), so the
+    stronger variant must equal it."""
+    n = 7
+    p = inputs.instance(n, 2, seed)
+    for perm, d in rand_nodes(n, 12, seed + 3):
+        assert oracle.lb(p, perm, d, bound=1) == oracle.lb(p, perm, d)
+
+
+@pytest.mark.parametrize("n,m,seed", [(6, 3, 161), (7, 5, 162), (8, 4, 163), (9, 3, 164)])
+@pytest.mark.parametrize("pool", [1, 7, 1024])
+def test_head_variant_solver_reaches_brute_force_optimum(n, m, seed, pool):
+    p = inputs.instance(n, m, seed)
+    opt, _ = oracle.bruteforce(p)
+    head = oracle.solve(p, pool=pool, bound=1)
+    base = oracle.solve(p, pool=pool)
+    assert head["status"] == oracle.OK and head["cmax"] == opt
+    assert oracle.makespan(p, head["perm"]) == opt
+    if pool == 1:  # depth-first one node at a time: a stronger bound never bounds more nodes
+        assert head["bounded"] <= base["bounded"]
+
 # ----------------------------------------------------------- the search ---
 @pytest.mark.parametrize("n,m,seed", [(2, 3, 80), (5, 2, 81), (6, 3, 82), (7, 5, 83), (8, 4, 84),
                                       (8, 2, 85), (9, 3, 86)])
