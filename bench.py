@@ -267,6 +267,33 @@ def learned_vs_plain(fsp, budget=LEARNED_BUDGET):
     return out
 
 
+VARIANT_RUNS = ((20, 10, 5, 0, 0), (20, 5, 2, 0, 0), (20, 20, 6, 2**17, 200_000_000), (50, 20, 7, 2**17, 50_000_000))
+
+
+def bound_variants(fsp):
+    """The base bound against the heads variant (release times raised by the
+    smallest heads) on the same searches: device NEH UB, the tuned pool (0) or
+    a fixed one, a node budget (0 = to optimality)."""
+    from paper_1206_4973_gb300 import inputs
+    out = []
+    for n, m, seed, pool, budget in VARIANT_RUNS:
+        p = inputs.instance(n, m, seed)
+        inst = fsp.fsp_create_instance(p)
+        ub0, perm0 = fsp.fsp_neh(inst)
+        row = {"instance": f"{n}x{m} seed {seed}", "pool": pool or "tuned", "node_budget": budget}
+        for name, var in (("base", fsp.BOUND_BASE), ("heads", fsp.BOUND_HEADS)):
+            inst.set_bound(var)
+            fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=pool or 1024, node_budget=200_000)  # warm-up
+            t0 = time.perf_counter()
+            r = fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=budget)
+            dt = time.perf_counter() - t0
+            row[name] = {"time_s": dt, "nodes_bounded": r["nodes_bounded"], "cmax": r["cmax"],
+                         "optimal": r["status"] == fsp.OK, "nodes_per_s": r["nodes_bounded"] / dt}
+        inst.close()
+        out.append(row)
+    return out
+
+
 BATCH_COUNT, BATCH_BUDGET, LEFTOVER_BUDGET = 256, 5_000_000, 200_000_000
 
 
@@ -479,6 +506,7 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "bound_pool": bp,
+            "bound_variants": bound_variants(fsp),
             "phase_ms": {"select": r["select_ms"], "branch_bound": r["bound_ms"], "compact": r["compact_ms"]},
             "wall_s": t_wall,
             "solves": solve_times(fsp),

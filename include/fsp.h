@@ -157,6 +157,22 @@ int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance **out);
 /* Release the instance and its device tables (synchronises its device). */
 void fsp_destroy_instance(fsp_instance *inst);
 
+/* Bound variants (an instance setting, used by every later fsp_bound_pool and
+ * fsp_solve on it; fsp_batch_* always use the base bound).
+ * FSP_BOUND_BASE: the bound of Sec. V-D as read here (one-machine bounds and
+ *   two-machine Johnson bounds with lags over every machine pair).
+ * FSP_BOUND_HEADS: the same bound with each machine's release time raised to
+ *   the earliest start of any remaining job, R_0 = C_0 and
+ *   R_k = max(C_k, R_{k-1} + min over the remaining jobs of p[j][k-1]) (a
+ *   refinement of the Lageweg-Lenstra-Rinnooy Kan family of bounds; never
+ *   below the base bound, equal to it at depth n-1).  No counterpart in the
+ *   paper, which plans other bounds as future work (Sec. VI). */
+#define FSP_BOUND_BASE 0
+#define FSP_BOUND_HEADS 1
+/* Set the bound variant of inst.  Errors: FSP_ERR_ARG (NULL inst or unknown
+ * variant). */
+int fsp_set_bound(fsp_instance *inst, int variant);
+
 /* Copy the device tables back for inspection (synchronous).  Any pointer may
  * be NULL.  q: host n*m int32 (q[j*m+k] = time of job j after machine k);
  * lag: host P*n int32; order: host P*n uint8 (Johnson order of pair kl);

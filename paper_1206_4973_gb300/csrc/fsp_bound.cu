@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(FSP_B2) k_bound_pool2(DevInst I, const uint8_t
                 for (int q = 0; q < 4 * NV; ++q) r.w[q] = 0u;
             }
             int32_t C[MT], SQ[MT];
-            fsp_prologue<MT, NV, NW>(r, I.n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad[j]);
+            fsp_prologue<MT, NV, NW>(r, I.n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad[j], I.var);
 #pragma unroll
             for (int k = 0; k < MT; ++k) {
                 cs[k * SB + slot[j]] = C[k];

@@ -83,11 +83,13 @@ __device__ __forceinline__ void fsp_make_child(const FspRec<NV> &par, int n, int
 }
 
 // a1-a3 for one node: release times C, S + qmin per machine, the remaining
-// set Um, the one-machine bound, and the validity of the record.
+// set Um, the one-machine bound, and the validity of the record.  var =
+// FSP_BOUND_HEADS raises C_k to the earliest start of any remaining job,
+// max(C_k, C_{k-1} + min over the remaining set of p[j][k-1]).
 template <int MT, int NV, int NW>
 __device__ __forceinline__ void fsp_prologue(const FspRec<NV> &r, int n, const int2 *__restrict__ pq, int mp,
                                              uint32_t (&Um)[NW], int32_t (&C)[MT], int32_t (&SQ)[MT],
-                                             int32_t &lb1, bool &bad)
+                                             int32_t &lb1, bool &bad, int var)
 {
     const int d = (int)fsp_rec_byte_dyn(r, n);
     bad = d > n;
@@ -134,6 +136,22 @@ __device__ __forceinline__ void fsp_prologue(const FspRec<NV> &r, int n, const i
                 }
             }
         }
+    }
+    if (var == FSP_BOUND_HEADS && d < n && !bad) {
+        int32_t Pm[MT];
+#pragma unroll
+        for (int k = 0; k < MT; ++k) Pm[k] = 0x7fffffff;
+#pragma unroll
+        for (int i = 0; i < 16 * NV; ++i) {
+            if (i >= d && i < n) {
+                const uint32_t j = (r.w[i >> 2] >> ((i & 3) * 8)) & 0xFFu;
+                const int2 *row = pq + j * mp;
+#pragma unroll
+                for (int k = 0; k < MT; ++k) Pm[k] = min(Pm[k], row[k].x);
+            }
+        }
+#pragma unroll
+        for (int k = 1; k < MT; ++k) C[k] = max(C[k], C[k - 1] + Pm[k - 1]);
     }
     lb1 = 0;
 #pragma unroll

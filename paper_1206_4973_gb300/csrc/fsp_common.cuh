@@ -45,6 +45,7 @@ struct fsp_instance {
     int2 *d_we;        // [n][P] position-major {w, e}: entry at position i of every pair
     uint8_t *d_rank;   // [P][n] position of job j in pair kl's order
     int *d_status;     // error flag of malformed records
+    int var;           // bound variant (FSP_BOUND_*)
     struct FspHostCache *cache;  // events and kernel attributes reused across calls
 };
 
@@ -70,6 +71,7 @@ struct DevInst {
     const int2 *we;
     const uint8_t *rank;
     int *status;
+    int var;  // bound variant (FSP_BOUND_*)
 };
 
 static inline DevInst dev_view(const fsp_instance *I)
@@ -78,6 +80,7 @@ static inline DevInst dev_view(const fsp_instance *I)
     d.n = I->n; d.m = I->m; d.P = I->P; d.stride = I->stride; d.mp = I->mp;
     d.p = I->d_p; d.q = I->d_q; d.ent = I->d_ent; d.status = I->d_status;
     d.we = I->d_we; d.rank = I->d_rank;
+    d.var = I->var;
     return d;
 }
 
@@ -229,6 +232,31 @@ __device__ __forceinline__ int32_t fsp_node_bound(const DevInst &I, const FspEnt
                         }
                     }
                 }
+            }
+        }
+    }
+
+    // FSP_BOUND_HEADS: release times raised to the earliest start of any
+    // remaining job, R_k = max(C_k, R_{k-1} + min over U of p[j][k-1]).
+    if (I.var == FSP_BOUND_HEADS && d < n && !bad) {
+        if (MT > 0) {
+            int32_t Pm[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) Pm[k] = 0x7fffffff;
+            for (int i = d; i < n; ++i) {
+                const int32_t *row = p_s + fsp_rec_byte(rec, B, i) * mp;
+#pragma unroll
+                for (int k = 0; k < R; ++k) Pm[k] = min(Pm[k], row[k]);
+            }
+#pragma unroll
+            for (int k = 1; k < R; ++k) C[k] = max(C[k], C[k - 1] + Pm[k - 1]);
+        } else {
+            int32_t prev = cs[0];
+            for (int k = 1; k < m; ++k) {
+                int32_t pm = 0x7fffffff;
+                for (int i = d; i < n; ++i) pm = min(pm, p_s[fsp_rec_byte(rec, B, i) * mp + k - 1]);
+                prev = max(cs[k * B], prev + pm);
+                cs[k * B] = prev;
             }
         }
     }

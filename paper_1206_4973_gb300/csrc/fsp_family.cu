@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         if (fn < np) fam_fetch<NV>(ws, S, stride, fn, lane, V.recb + (buf ^ 1) * 16 * NV, V.pofs + (buf ^ 1));
         fam_bound<MT, NV, LRN>(V, rec_s, c0, n, mp, stride, ub_iter, ws.children, ws.lbs, &ws.ctl->best_key,
                                LRN ? ws.topk + (long long)f * L.K : nullptr, L.K,
-                               reinterpret_cast<unsigned long long *>(&ws.ctl->early));
+                               reinterpret_cast<unsigned long long *>(&ws.ctl->early), I.var);
         __syncwarp();
         f = fn;
         buf ^= 1;

@@ -39,7 +39,7 @@ struct FamMask<2> {
 // the list of pairs still to evaluate.
 struct FamSmem {
     size_t we_off, rk8_off, en_off, gam_off, klm_off, pq_off, warp_off, warp_bytes, bytes;
-    size_t w_ps, w_psa, w_ab, w_rec, w_pofs, w_cc, w_sq, w_lb, w_T, w_lkl, w_lm;
+    size_t w_ps, w_psa, w_pp, w_ab, w_rec, w_pofs, w_cc, w_sq, w_lb, w_T, w_lkl, w_lm;
     int rks8, mtp, warps;
     int K;  // learned order: predicted pairs per parent
 };
@@ -71,6 +71,7 @@ __host__ __device__ inline FamSmem family_smem_layout_nm(int n, int m, int mp, i
     size_t w = 0;
     L.w_ps = w; w += (size_t)MT * 16;
     L.w_psa = w; w += fsp_align16((size_t)MT * 4);
+    L.w_pp = w; w += (size_t)MT * 16;
     L.w_ab = w; w += fsp_align16((size_t)MT * 8);
     L.w_rec = w; w += 32 * (size_t)NV;
     L.w_pofs = w; w += 16;
@@ -105,7 +106,7 @@ struct FamView {
     int32_t *gam;
     uint16_t *klm;
     int2 *pq;
-    int4 *ps;
+    int4 *ps, *pp;
     int32_t *psa, *ab, *cc, *sq, *lbv, *T, *lm;
     uint16_t *lkl;
     uint8_t *recb;
@@ -125,6 +126,7 @@ __device__ __forceinline__ FamView fam_view(unsigned char *smem, const FamSmem &
     unsigned char *wb = smem + L.warp_off + warp * L.warp_bytes;
     V.ps = reinterpret_cast<int4 *>(wb + L.w_ps);
     V.psa = reinterpret_cast<int32_t *>(wb + L.w_psa);
+    V.pp = reinterpret_cast<int4 *>(wb + L.w_pp);  // heads variant: smallest p per machine
     V.ab = reinterpret_cast<int32_t *>(wb + L.w_ab);  // alpha[MT], beta[MT]
     V.recb = wb + L.w_rec;                            // two record buffers
     V.pofs = reinterpret_cast<int *>(wb + L.w_pofs);  // and their first children
@@ -211,7 +213,7 @@ template <int MT, int NV, bool LRN>
 __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s, long long c0, int n, int mp,
                                           int stride, int ub_iter, uint8_t *children, int32_t *lbs,
                                           unsigned long long *best_key, const int16_t *topk_row, int K,
-                                          unsigned long long *early)
+                                          unsigned long long *early, int var)
 {
     constexpr int P = MT * (MT - 1) / 2;
     constexpr int NS = (P + 31) / 32;
@@ -225,7 +227,8 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
     const int32_t *gam_s = V.gam;
     const uint16_t *klm_s = V.klm;
     const int2 *pq_s = V.pq;
-    int4 *ps = V.ps;
+    int4 *ps = V.ps, *pp = V.pp;
+    const bool heads = var == FSP_BOUND_HEADS;
     int32_t *psa = V.psa, *ab = V.ab, *cc = V.cc, *sq = V.sq, *lbv = V.lbv, *T = V.T, *lm = V.lm;
     uint16_t *lkl = V.lkl;
     FspRec<NV> par;
@@ -273,6 +276,16 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 ps[lane] = make_int4(Ck, Sk, Q1, Q2);
                 psa[lane] = A;
             }
+            if (heads) {  // smallest and second smallest p on machine k, and a job attaining it
+                int32_t P1 = 0x7fffffff, P2 = 0x7fffffff, AP = 0;
+                for (int i = d; i < n; ++i) {
+                    const int j = rec_s[i];
+                    const int32_t v = pq_s[j * mp + k].x;
+                    if (v < P1) { P2 = P1; P1 = v; AP = j; }
+                    else P2 = min(P2, v);
+                }
+                if (lane < MT) pp[lane] = make_int4(P1, P2, AP, 0);
+            }
         }
         __syncwarp();
 
@@ -280,7 +293,7 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
         for (int ci = lane; ci < r; ci += 32) {
             const int c = rec_s[d + ci];
             const int2 *prow = pq_s + c * mp;
-            int32_t lb = 0, prev = 0;
+            int32_t lb = 0, prev = 0, rprev = 0;
 #pragma unroll
             for (int k = 0; k < MT; ++k) {
                 const int4 st = ps[k];
@@ -288,9 +301,16 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 const int32_t ck = max(st.x, prev) + v.x;
                 const int32_t sqk = st.y - v.x + (psa[k] == c ? st.w : st.z);
                 prev = ck;
-                cc[ci * mtp + k] = ck;
+                // heads variant: the earliest start of a job of U \ {c} on machine k
+                int32_t rk = ck;
+                if (heads && k > 0) {
+                    const int4 pk = pp[k - 1];
+                    rk = max(ck, rprev + (pk.z == c ? pk.y : pk.x));
+                }
+                rprev = rk;
+                cc[ci * mtp + k] = rk;
                 sq[ci * mtp + k] = sqk;
-                lb = max(lb, ck + sqk);
+                lb = max(lb, rk + sqk);
             }
             lbv[ci] = lb;
             FspRec<NV> ch;

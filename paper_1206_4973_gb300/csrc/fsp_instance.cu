@@ -272,6 +272,16 @@ fail:
     return rc;
 }
 
+extern "C" int fsp_set_bound(fsp_instance *inst, int variant)
+{
+    if (!inst || (variant != FSP_BOUND_BASE && variant != FSP_BOUND_HEADS)) {
+        fsp_set_error("fsp_set_bound: NULL instance or unknown variant %d", variant);
+        return FSP_ERR_ARG;
+    }
+    inst->var = variant;
+    return FSP_OK;
+}
+
 extern "C" void fsp_destroy_instance(fsp_instance *inst)
 {
     if (!inst) return;

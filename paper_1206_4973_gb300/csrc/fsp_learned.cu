@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(256) k_branch_learned(DevInst I, SolveWs ws, B
         uint32_t Um[NW];
         int32_t C[MT], SQ[MT], lb;
         bool bad;
-        fsp_prologue<MT, NV, NW>(ch, n, pq_s, I.mp, Um, C, SQ, lb, bad);
+        fsp_prologue<MT, NV, NW>(ch, n, pq_s, I.mp, Um, C, SQ, lb, bad, I.var);
 #pragma unroll
         for (int k = 0; k < MT; ++k) {
             cs[k * B + tid] = C[k];
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(FSP_B2) k_bound_list(DevInst I, SolveWs ws, Bo
             dch[j] = (int)fsp_rec_byte_dyn(r, n);
             int32_t C[MT], SQ[MT];
             bool bad;
-            fsp_prologue<MT, NV, NW>(r, n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad);
+            fsp_prologue<MT, NV, NW>(r, n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad, I.var);
 #pragma unroll
             for (int k = 0; k < MT; ++k) {
                 cs[k * SB + slot[j]] = C[k];

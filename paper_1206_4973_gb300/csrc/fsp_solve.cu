@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(FSP_B2) k_branch_bound2(DevInst I, SolveWs ws,
         dch[j] = (int)fsp_rec_byte_dyn(ch, n);
         int32_t C[MT], SQ[MT];
         bool bad;
-        fsp_prologue<MT, NV, NW>(ch, n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad);
+        fsp_prologue<MT, NV, NW>(ch, n, pq_s, I.mp, Um[j], C, SQ, lb[j], bad, I.var);
 #pragma unroll
         for (int k = 0; k < MT; ++k) {
             cs[k * SB + slot[j]] = C[k];

@@ -29,7 +29,8 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp
            "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
            "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
-           "fsp_batch_tune_pools", "fsp_last_error")
+           "fsp_batch_tune_pools", "fsp_set_bound", "fsp_last_error")
+BOUND_BASE, BOUND_HEADS = 0, 1
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -117,6 +118,7 @@ def load(path: str | None = None):
         "fsp_batch_run": (ctypes.c_int, [vp, vp]),
         "fsp_batch_results": (ctypes.c_int, [vp, vp, vp, vp]),
         "fsp_batch_tune_pools": (ctypes.c_int, [ctypes.c_int, vp, vp, i64, vp]),
+        "fsp_set_bound": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -146,6 +148,11 @@ class Instance:
     def __init__(self, handle, n: int, m: int):
         self.handle, self.n, self.m = handle, n, m
         self.stride = fsp_node_stride(n)
+
+    def set_bound(self, variant: int) -> None:
+        """BOUND_BASE or BOUND_HEADS (release times raised by the smallest heads)."""
+        _check(load().fsp_set_bound(self.handle, int(variant)))
+        self.bound = int(variant)
 
     def close(self):
         if self.handle:
