@@ -195,7 +195,7 @@ def solve_times(fsp, budget=SOLVE_BUDGET):
         out.append({"instance": f"{n}x{m} seed {seed}", "ub0": None if pool else ub0, "cmax": r["cmax"],
                     "optimal": r["status"] == fsp.OK, "time_s": dt, "nodes_bounded": r["nodes_bounded"],
                     "iterations": r["iterations"], "pool": r["tuned_pool"] if pool == 0 else pool,
-                    "nodes_per_s": r["nodes_bounded"] / dt})
+                    "warps_per_cta": r["tuned_warps"], "nodes_per_s": r["nodes_bounded"] / dt})
         inst.close()
     return out
 

@@ -79,6 +79,9 @@ typedef struct {
     int64_t tuned_pool;        /* pool size the tuner settled on (pool_size = 0), else the pool */
     int64_t early_pruned;      /* children cut by their predicted pairs alone (order = learned) */
     double infer_ms;           /* device time in the network + top-K (learned, opt->profile) */
+    int64_t tuned_warps;       /* warps per CTA of the family kernel (chosen on measured
+                                  throughput with pool_size = 0); 0 if the per-child
+                                  kernels ran */
 } fsp_stats;
 
 #define FSP_ORDER_PLAIN 0   /* every child gets its full bound */

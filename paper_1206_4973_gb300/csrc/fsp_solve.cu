@@ -734,6 +734,39 @@ struct PoolTuner {
     }
 };
 
+// Block shape of the family kernel (warps per CTA), chosen after the pool
+// settled: each candidate runs `window` iterations and the best nodes bounded
+// per second of wall time is kept (the bounds do not depend on it).
+struct BlockTuner {
+    bool on = false, settled = true;
+    int n = 0, cur = 0, best = 0, tried = 0;
+    double best_eff = -1e300;
+    long long window = 8, it_in = 0, b0 = 0;
+    double t0 = 0.0;
+    void start(int ncand, long long win)
+    {
+        n = ncand;
+        on = n > 1;
+        settled = !on;
+        cur = best = n - 1;  // start from the most warps
+        window = win > 0 ? win : 8;
+    }
+    void observe(long long bounded, double now)
+    {
+        if (settled) return;
+        if (it_in == window) {
+            const double dt = now - t0;
+            const double eff = dt > 0 ? (double)(bounded - b0) / dt : 0.0;
+            if (eff > best_eff) { best_eff = eff; best = cur; }
+            it_in = 0;
+            if (++tried == n) { settled = true; cur = best; return; }
+            cur = (cur + 1) % n;
+        }
+        if (it_in == 0) { t0 = now; b0 = bounded; }
+        it_in++;
+    }
+};
+
 static double wall_seconds()
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -747,7 +780,9 @@ struct SolvePlan {
     BranchBoundFn bb;
     BranchBound2Fn bb2;
     BranchFamilyFn bf;   // families of children bounded together (NULL: per child)
-    FamSmem famL;
+    FamSmem famL;        // its layout at the most warps that fit
+    FamSmem famC[4];     // the block shapes the tuner tries (ascending warps; famL last)
+    int nfam;
     BranchLearnedFn bl;  // learned order (NULL: plain)
     BoundListFn blist;
     int per_cta;
@@ -778,12 +813,21 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
     // each parent's children are bounded together where the family kernel's
     // tables fit (FSP_FAMILY=0 keeps the per-child kernels)
     P->bf = nullptr;
+    P->nfam = 0;
     if (shp.ver == 2) {
         const char *ev = getenv("FSP_FAMILY");
         const int w = (ev && ev[0] == '0') ? 0 : family_warps(I, shp.mt, shp.nv);
         if (w > 0 && (P->bf = pick_branch_family(shp.mt, shp.nv, P->L.learned)) != nullptr) {
             P->famL = family_smem_layout(I, shp.mt, shp.nv, w);
             P->famL.K = P->L.learned ? P->L.topk : 0;
+            P->nfam = 0;
+            const int cand[3] = {4, 8, 12};
+            for (int c = 0; c < 3; ++c)
+                if (cand[c] < w) {
+                    P->famC[P->nfam] = family_smem_layout(I, shp.mt, shp.nv, cand[c]);
+                    P->famC[P->nfam++].K = P->famL.K;
+                }
+            P->famC[P->nfam++] = P->famL;
             if ((rc = fsp_allow_smem(I, (const void *)P->bf, P->famL.bytes)) != FSP_OK) return rc;
         }
     }
@@ -860,6 +904,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     void *pin = nullptr;                     // their pinned host buffers
     double t_sel = 0, t_bb = 0, t_cmp = 0, t_inf = 0;
     PoolTuner tuner;
+    BlockTuner btuner;
+    int fam_i = P->bf ? P->nfam - 1 : 0;
     SolveCtl h;
     memset(&h, 0, sizeof h);
     cudaError_t e = cudaSuccess;
@@ -876,6 +922,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if ((rc = fsp_event_take(I, &pe[i])) != FSP_OK) goto out;
     if (timed) TRY(cudaEventRecord(ev0, st));
     if (o.pool_size == 0) tuner.start(per_cta, I->sm_count, tuner_max_pool(I), o.tune_window);
+    if (o.pool_size == 0 && P->bf) btuner.start(P->nfam, o.tune_window);
     if (I->n == 1) {
         k_solve_single<<<1, 32, 0, st>>>(ws, I->d_p, I->m, ub0);
         TRY(cudaGetLastError());
@@ -940,9 +987,10 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                     if (prof) LTRY(cudaEventRecord(pe[4], st));
                 }
                 // at most pool / 2 + 1 parents: stacked nodes have >= 2 children
-                const long long fam = (pool / 2 + 1 + P->famL.warps - 1) / P->famL.warps;
+                const FamSmem &FL = P->famC[fam_i];
+                const long long fam = (pool / 2 + 1 + FL.warps - 1) / FL.warps;
                 const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
-                P->bf<<<grid_f, P->famL.warps * 32, P->famL.bytes, st>>>(D, ws, P->famL);
+                P->bf<<<grid_f, FL.warps * 32, FL.bytes, st>>>(D, ws, FL);
             } else if (bb2) {
                 bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             } else {
@@ -1008,7 +1056,11 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if (h.stack_size == 0) break;
             if (o.node_budget > 0 && h.cnt[0] >= o.node_budget) { rc = FSP_INCOMPLETE; break; }
             if (o.max_iterations > 0 && it >= o.max_iterations) { rc = FSP_INCOMPLETE; break; }
-            if (may_ahead && ((o.schedule && o.schedule_len > 0) || !tuner.on || tuner.phase == 2)) {
+            if (tuner.on && tuner.phase == 2 && !btuner.settled) {  // then the block shape
+                btuner.observe(h.cnt[0], wall_seconds());
+                fam_i = btuner.cur;
+            }
+            if (may_ahead && ((o.schedule && o.schedule_len > 0) || !tuner.on || (tuner.phase == 2 && btuner.settled))) {
                 it0 = it;
                 break;
             }
@@ -1083,6 +1135,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         stats->iterations = h.cnt[4];
         stats->incumbent_updates = h.cnt[5];
         stats->tuned_pool = tuner.on ? tuner.best : o.pool_size;
+        stats->tuned_warps = P->bf ? P->famC[fam_i].warps : 0;
         stats->early_pruned = h.cnt[6];
         stats->infer_ms = t_inf;
         float ms = 0.f;

@@ -47,7 +47,8 @@ class fsp_stats(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64),
                 ("time_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
                 ("bound_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
-                ("tuned_pool", ctypes.c_int64), ("early_pruned", ctypes.c_int64), ("infer_ms", ctypes.c_double)]
+                ("tuned_pool", ctypes.c_int64), ("early_pruned", ctypes.c_int64), ("infer_ms", ctypes.c_double),
+                ("tuned_warps", ctypes.c_int64)]
 
 
 class fsp_options(ctypes.Structure):
@@ -359,6 +360,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     res["cmax"] = int(cmax.value)
     res["perm"] = perm if perm[0] >= 0 else None
     res["tuned_pool"] = int(st.tuned_pool)
+    res["tuned_warps"] = int(st.tuned_warps)
     res["early_pruned"] = int(st.early_pruned)
     res["logged"] = int(o._log_count.value)
     if trace is not None:

@@ -101,3 +101,19 @@ def test_launching_ahead_gives_the_same_search(F, n, m, seed, pool, budget, max_
     assert np.array_equal(a["schedule"], b["schedule"])
     k = min(a["stack_left"], len(out_a))
     assert np.array_equal(out_a[:k], out_b[:k])
+
+
+def test_block_shape_tuning_reports_a_shape_and_keeps_the_search(F):
+    """pool_size = 0 tunes the pool, then the family kernel's warps per CTA;
+    the search equals a replay of the tuned pools with the default shape."""
+    p = inputs.instance(20, 10, 5)
+    inst = F.fsp_create_instance(p)
+    ub0, perm0 = F.fsp_neh(inst)
+    a = F.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=0, tune_window=4, schedule_cap=100000,
+                    trace_cap=100000)
+    assert a["status"] == F.OK and a["tuned_warps"] in (4, 8, 12, 16)
+    b = F.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=1024, schedule=a["schedule"], trace_cap=100000)
+    for key in KEYS:
+        assert a[key] == b[key], key
+    assert np.array_equal(a["trace"], b["trace"])
+    assert b["tuned_warps"] == 16  # a fixed pool keeps the most warps that fit
