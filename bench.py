@@ -127,6 +127,16 @@ def dist_init(args):
     return rank, world, local
 
 
+def step_config(frontier, ub, n_children, world):
+    """The workload both arms report: one B&B iteration with a pool of 2^18
+    children from the 20x20 seed-1 frontier."""
+    return {"workload": "20x20 B&B iteration, pool 2^18 children, from the seed-1 frontier",
+            "n": N_JOBS, "m": N_MACH, "seed": SEED, "pool": POOL,
+            "frontier_nodes": int(len(frontier)), "ub": int(ub), "children_per_step": int(n_children),
+            "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, outside the step events)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle timed as the reference arm (host cores, one thread)."""
     if rank != 0:
@@ -143,15 +153,14 @@ def run_reference(args, rank, world):
         bounded += r["bounded"]
     dt = time.perf_counter() - t0
     value = bounded / dt
-    sample = (f"one B&B iteration with a pool of {sample_pool} children from the 20x20 seed-1 frontier, "
-              f"x{args.steps} steps")
+    sample = (f"each step one B&B iteration of the same workload with a pool of {sample_pool} children "
+              f"(of the 2^18) from the 20x20 seed-1 frontier, x{args.steps} steps, serial C oracle")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "20x20 B&B iteration from the seed-1 frontier (CPU oracle sample)",
-                   "n": N_JOBS, "m": N_MACH, "seed": SEED, "pool": sample_pool},
+        "config": step_config(frontier, ub, children_depths(frontier, POOL)[1], world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -496,11 +505,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "20x20 B&B iteration, pool 2^18 children, from the seed-1 frontier",
-                       "n": N_JOBS, "m": N_MACH, "seed": SEED, "pool": POOL,
-                       "frontier_nodes": int(len(frontier)), "ub": ub, "children_per_step": n_children,
-                       "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write, outside the step events)",
-                       "parallelism": f"replicas x{world}"},
+            "config": step_config(frontier, ub, n_children, world),
             "roofline": roofline,
             "gpu_launches": launches,
             "clocks": clk.summary(),
