@@ -248,8 +248,8 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
                 reinterpret_cast<uint4 *>(V.recb)[lane] =
                     reinterpret_cast<const uint4 *>(W.stack + (S - 1 - f) * stride)[lane];
             __syncwarp();
-            fam_bound<MT, NV, false>(V, V.recb, poff[f], n, mp, stride, ub, W.children, W.lbs, &best_key, nullptr,
-                                     0, nullptr, FSP_BOUND_BASE);
+            fam_bound<MT, NV, false, false>(V, V.recb, poff[f], n, mp, stride, ub, W.children, W.lbs, &best_key,
+                                            nullptr, 0, nullptr);
             __syncwarp();
         }
         __syncthreads();

@@ -96,7 +96,7 @@ static inline FamSmem family_smem_layout(const fsp_instance *I, int MT, int NV, 
 int family_warps(const fsp_instance *I, int MT, int NV);
 
 typedef void (*BranchFamilyFn)(DevInst, SolveWs, FamSmem);
-BranchFamilyFn pick_branch_family(int mt, int nv, bool learned);
+BranchFamilyFn pick_branch_family(int mt, int nv, bool learned, bool heads);
 
 // One warp's view of the family shared memory.
 struct FamView {
@@ -209,11 +209,11 @@ __device__ __forceinline__ int32_t fam_prefix_p(int t, int lane, int d, int k, i
 // child is left do the certification and the remaining pairs run, for the
 // children left.  A cut child keeps its partial bound (>= the UB); the
 // others get the exact bound, so the search is the plain one.
-template <int MT, int NV, bool LRN>
+template <int MT, int NV, bool LRN, bool HEADS>
 __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s, long long c0, int n, int mp,
                                           int stride, int ub_iter, uint8_t *children, int32_t *lbs,
                                           unsigned long long *best_key, const int16_t *topk_row, int K,
-                                          unsigned long long *early, int var)
+                                          unsigned long long *early)
 {
     constexpr int P = MT * (MT - 1) / 2;
     constexpr int NS = (P + 31) / 32;
@@ -228,7 +228,7 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
     const uint16_t *klm_s = V.klm;
     const int2 *pq_s = V.pq;
     int4 *ps = V.ps, *pp = V.pp;
-    const bool heads = var == FSP_BOUND_HEADS;
+    constexpr bool heads = HEADS;  // FSP_BOUND_HEADS
     int32_t *psa = V.psa, *ab = V.ab, *cc = V.cc, *sq = V.sq, *lbv = V.lbv, *T = V.T, *lm = V.lm;
     uint16_t *lkl = V.lkl;
     FspRec<NV> par;

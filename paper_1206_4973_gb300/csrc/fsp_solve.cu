@@ -817,7 +817,8 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
     if (shp.ver == 2) {
         const char *ev = getenv("FSP_FAMILY");
         const int w = (ev && ev[0] == '0') ? 0 : family_warps(I, shp.mt, shp.nv);
-        if (w > 0 && (P->bf = pick_branch_family(shp.mt, shp.nv, P->L.learned)) != nullptr) {
+        if (w > 0 && (P->bf = pick_branch_family(shp.mt, shp.nv, P->L.learned, I->var == FSP_BOUND_HEADS)) !=
+                         nullptr) {
             P->famL = family_smem_layout(I, shp.mt, shp.nv, w);
             P->famL.K = P->L.learned ? P->L.topk : 0;
             P->nfam = 0;
