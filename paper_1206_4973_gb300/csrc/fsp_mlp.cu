@@ -536,6 +536,8 @@ extern "C" int fsp_node_features(fsp_instance *I, const uint8_t *nodes, int64_t 
 #define FM_KP 48   // padded input width
 #define FM_NP 192  // padded output width
 #define FM_S 8     // row padding (bf16) against bank conflicts
+#define FM_TKR 4   // rows whose top-K reductions run together
+#define FM_SCS (FM_NP + 2)  // score row stride (bf16): an odd word count, rows in distinct banks
 
 struct FusedSmem {
     size_t w1, w2, w3, act, sc, pq, bytes;
@@ -549,7 +551,7 @@ static inline FusedSmem fused_layout(const fsp_instance *I)
     L.w2 = o; o += (size_t)FM_H * (FM_H + FM_S) * 2;
     L.w3 = o; o += (size_t)FM_NP * (FM_H + FM_S) * 2;
     L.act = o; o += (size_t)FM_RM * (FM_H + FM_S) * 2;  // X, then H1, then H2 (per warp strip)
-    L.sc = o; o += (size_t)FM_RM * FM_NP * 2;            // scores (bf16) for the top-K
+    L.sc = o; o += (size_t)FM_RM * FM_SCS * 2;           // scores (bf16) for the top-K
     L.pq = o; o += (size_t)I->n * I->mp * 8;
     L.bytes = o;
     return L;
@@ -618,6 +620,41 @@ __device__ __forceinline__ void fm_features(const uint8_t *r, int n, const int2 
     x[2 * MT] = __fdiv_rn((float)d, (float)n);
 }
 
+// Half of fm_features' columns as bf16 into xr: part 0 the release times
+// (columns 0..MT-1), the depth (2 MT) and the zero padding; part 1 the
+// remaining work (MT..2 MT-1).  Same values as fsp_features.
+template <int MT>
+__device__ __forceinline__ void fm_features_part(const uint8_t *r, int n, const int2 *pq, int mp, float T, int part,
+                                                 bf16_t *xr)
+{
+    const int d = r[n] <= n ? r[n] : n;
+    int32_t A[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) A[k] = 0;
+    if (part == 0) {
+        for (int i = 0; i < d; ++i) {
+            const int j = r[i] < n ? r[i] : 0;
+            const int2 *row = pq + j * mp;
+            A[0] += row[0].x;
+#pragma unroll
+            for (int k = 1; k < MT; ++k) A[k] = max(A[k], A[k - 1]) + row[k].x;
+        }
+#pragma unroll
+        for (int k = 0; k < MT; ++k) xr[k] = __float2bfloat16_rn(__fdiv_rn((float)A[k], T));
+        xr[2 * MT] = __float2bfloat16_rn(__fdiv_rn((float)d, (float)n));
+        for (int k = 2 * MT + 1; k < FM_KP; ++k) xr[k] = __float2bfloat16_rn(0.f);
+    } else {
+        for (int i = d; i < n; ++i) {
+            const int j = r[i] < n ? r[i] : 0;
+            const int2 *row = pq + j * mp;
+#pragma unroll
+            for (int k = 0; k < MT; ++k) A[k] += row[k].x;
+        }
+#pragma unroll
+        for (int k = 0; k < MT; ++k) xr[MT + k] = __float2bfloat16_rn(__fdiv_rn((float)A[k], T));
+    }
+}
+
 template <int MT>
 __global__ void __launch_bounds__(FM_T) k_mlp_topk_parents(DevInst I, const uint8_t *__restrict__ stack,
                                                            const long long *__restrict__ s_pop,
@@ -662,19 +699,18 @@ __global__ void __launch_bounds__(FM_T) k_mlp_topk_parents(DevInst I, const uint
     bf16_t *strip = act + rw * (FM_H + FM_S);        // X (stride FM_KP + FM_S), then H1, H2 (stride FM_H + FM_S)
     for (long long r0 = (long long)blockIdx.x * FM_RM; r0 < np; r0 += (long long)gridDim.x * FM_RM) {
         __syncthreads();  // weights staged / previous rows done
-        if (tid < FM_RM) {  // features: thread tid -> row tid (warp tid/16's strip, row tid%16)
-            const long long r = r0 + tid;
-            float x[2 * MT + 1];
+        {   // features: row tid % FM_RM (warp row/16's strip, row row%16); the first
+            // half of the threads writes the release-time columns and the depth,
+            // the second half the remaining-work columns
+            const int row = tid % FM_RM, part = tid / FM_RM;
+            const long long r = r0 + row;
+            bf16_t *xr = act + (row >> 4) * 16 * (FM_H + FM_S) + (row & 15) * (FM_KP + FM_S);
             if (r < np) {
                 const long long at = reversed ? S - 1 - r : r;  // the search's parents sit top down
-                fm_features<MT>(stack + at * I.stride, I.n, pq, I.mp, T, x);
+                fm_features_part<MT>(stack + at * I.stride, I.n, pq, I.mp, T, part, xr);
             } else {
-#pragma unroll
-                for (int k = 0; k < 2 * MT + 1; ++k) x[k] = 0.f;
+                for (int k = part; k < FM_KP; k += 2) xr[k] = __float2bfloat16_rn(0.f);
             }
-            bf16_t *xr = act + (tid >> 4) * 16 * (FM_H + FM_S) + (tid & 15) * (FM_KP + FM_S);
-#pragma unroll
-            for (int k = 0; k < FM_KP; ++k) xr[k] = __float2bfloat16_rn(k < 2 * MT + 1 ? x[k] : 0.f);
         }
         __syncthreads();
         {   // layer 1: X (16 x 48) -> H1 (16 x 128), written over the strip once X is consumed
@@ -709,7 +745,7 @@ __global__ void __launch_bounds__(FM_T) k_mlp_topk_parents(DevInst I, const uint
         __syncwarp();
         // layer 3 in two halves of 96 columns, scores to shared memory (bf16: the
         // order is a heuristic, the search stays exact whatever it is)
-        bf16_t *sc = reinterpret_cast<bf16_t *>(smem + L.sc) + rw * FM_NP;
+        bf16_t *sc = reinterpret_cast<bf16_t *>(smem + L.sc) + rw * FM_SCS;
         for (int half = 0; half < 2; ++half) {
             float acc[12][4];
 #pragma unroll
@@ -720,41 +756,57 @@ __global__ void __launch_bounds__(FM_T) k_mlp_topk_parents(DevInst I, const uint
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const int row = g + (c >= 2 ? 8 : 0), col = half * 96 + nt * 8 + 2 * t + (c & 1);
-                    sc[row * FM_NP + col] = __float2bfloat16_rn(col < P ? acc[nt][c] + w[ob3 + col] : -INFINITY);
+                    sc[row * FM_SCS + col] = __float2bfloat16_rn(col < P ? acc[nt][c] + w[ob3 + col] : -INFINITY);
                 }
         }
         __syncwarp();
-        // top-K of each of the warp's 16 rows across the warp: best first, ties to the lower pair
+        // top-K of each of the warp's 16 rows across the warp: best first, ties to
+        // the lower pair; FM_TKR rows at a time so their reduction chains overlap
 #pragma unroll 1
-        for (int rr = 0; rr < 16; ++rr) {
-            const long long r = r0 + rw + rr;
-            if (r >= np) break;
-            const bf16_t *sr = sc + rr * FM_NP;
-            float v6[FM_NP / 32];
+        for (int rr = 0; rr < 16; rr += FM_TKR) {
+            float v6[FM_TKR][FM_NP / 32];
+            uint32_t taken[FM_TKR];
 #pragma unroll
-            for (int q = 0; q < FM_NP / 32; ++q) v6[q] = lane + 32 * q < P ? __bfloat162float(sr[lane + 32 * q]) : -INFINITY;
-            uint32_t taken = 0u;
+            for (int u = 0; u < FM_TKR; ++u) {
+                const bf16_t *sr = sc + (rr + u) * FM_SCS;
+                taken[u] = 0u;
+#pragma unroll
+                for (int q = 0; q < FM_NP / 32; ++q)
+                    v6[u][q] = lane + 32 * q < P ? __bfloat162float(sr[lane + 32 * q]) : -INFINITY;
+            }
 #pragma unroll 1
             for (int j = 0; j < K; ++j) {
-                float bv = -INFINITY;
-                int bq = 0x7fffffff;
+                float bv[FM_TKR];
+                int bq[FM_TKR];
 #pragma unroll
-                for (int q = 0; q < FM_NP / 32; ++q) {
-                    const int pq2 = lane + 32 * q;
-                    if (pq2 < P && !(taken & (1u << q)) && (v6[q] > bv || (v6[q] == bv && pq2 < bq))) {
-                        bv = v6[q];
-                        bq = pq2;
+                for (int u = 0; u < FM_TKR; ++u) {
+                    bv[u] = -INFINITY;
+                    bq[u] = 0x7fffffff;
+#pragma unroll
+                    for (int q = 0; q < FM_NP / 32; ++q) {
+                        const int pq2 = lane + 32 * q;
+                        if (pq2 < P && !(taken[u] & (1u << q)) && (v6[u][q] > bv[u] || (v6[u][q] == bv[u] && pq2 < bq[u]))) {
+                            bv[u] = v6[u][q];
+                            bq[u] = pq2;
+                        }
                     }
                 }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
-                    const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                    const int oq = __shfl_xor_sync(0xffffffffu, bq, o);
-                    if (ov > bv || (ov == bv && oq < bq)) { bv = ov; bq = oq; }
+#pragma unroll
+                    for (int u = 0; u < FM_TKR; ++u) {
+                        const float ov = __shfl_xor_sync(0xffffffffu, bv[u], o);
+                        const int oq = __shfl_xor_sync(0xffffffffu, bq[u], o);
+                        if (ov > bv[u] || (ov == bv[u] && oq < bq[u])) { bv[u] = ov; bq[u] = oq; }
+                    }
                 }
-                if (bq == 0x7fffffff) bq = 0;
-                if ((bq & 31) == lane) taken |= 1u << (bq >> 5);
-                if (lane == 0) topk[r * K + j] = (int16_t)bq;
+#pragma unroll
+                for (int u = 0; u < FM_TKR; ++u) {
+                    const long long r = r0 + rw + rr + u;
+                    int q = bq[u] == 0x7fffffff ? 0 : bq[u];
+                    if ((q & 31) == lane) taken[u] |= 1u << (q >> 5);
+                    if (lane == 0 && r < np) topk[r * K + j] = (int16_t)q;
+                }
             }
         }
     }
