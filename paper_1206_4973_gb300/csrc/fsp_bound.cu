@@ -8,7 +8,7 @@
 // is persistent (SMs x resident CTAs) and strides over the pool.
 #include <stdlib.h>
 
-#include "fsp_bound.cuh"
+#include "fsp_family.cuh"
 
 template <int NW, int MT, bool ES>
 __global__ void __launch_bounds__(256) k_bound_pool(DevInst I, const uint8_t *__restrict__ nodes,
@@ -172,6 +172,12 @@ extern "C" int fsp_bound_pool(fsp_instance *I, const uint8_t *nodes, int64_t cou
     BoundShape s;
     int rc = fsp_bound_shape(I, &s);
     if (rc != FSP_OK) return rc;
+    if (s.ver == 2 && count <= FAM_POOL_SMALL && !getenv("FSP_FAMILY_POOL0")) {
+        // a pool too small to fill the GPU one node per thread: one warp per node
+        rc = fam_bound_pool(I, s.mt, s.nv, nodes, count, lb_out, (cudaStream_t)stream);
+        if (rc != FSP_ERR_ARG) return rc;
+        rc = FSP_OK;
+    }
     if (s.ver == 2) {
         BoundPool2Fn fn2 = pick_bound_pool2(s.mt, s.nv, s.nw);
         if (!fn2) { fsp_set_error("fsp_bound_pool: no kernel for this shape"); return FSP_ERR_ARG; }

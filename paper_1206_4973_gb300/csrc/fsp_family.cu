@@ -117,6 +117,166 @@ BranchFamilyFn pick_branch_family(int mt, int nv, bool learned, bool heads)
     return nullptr;
 }
 
+// Small pools of arbitrary nodes (fsp_bound_pool): one warp per node, so a
+// pool too small to fill the GPU with one node per thread is not paced by
+// one thread's serial work.  Lanes own machines for the node's release
+// times (the diagonal recurrence), remaining sums and smallest tails, and
+// machine pairs for the forward scans; the node bound is the warp's maximum.
+// The same integers as the per-node kernels; a malformed record gives
+// FSP_LB_INVALID and sets the instance's status bit 1.
+template <int MT, int NV>
+__global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_bound_pool_warp(DevInst I, const uint8_t *__restrict__ nodes,
+                                                                            long long count, int32_t *__restrict__ lb_out,
+                                                                            FamSmem L)
+{
+    constexpr int P = MT * (MT - 1) / 2;
+    constexpr int NS = (P + 31) / 32;
+    typedef typename FamMask<NV>::type Mask;
+    const int W = blockDim.x >> 5;
+    if ((long long)blockIdx.x * W >= count) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = I.n, stride = I.stride, mp = I.mp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const FamView V = fam_view(smem, L, warp);
+    for (int i = threadIdx.x; i < n * P; i += blockDim.x) V.we[i] = __ldg(I.we + i);
+    for (int i = threadIdx.x; i < P * V.rks8; i += blockDim.x) {
+        const int kl = i / V.rks8, j = i - kl * V.rks8;
+        V.rk8[i] = j < n ? __ldg(I.rank + kl * n + j) : (uint8_t)0;
+    }
+    for (int i = threadIdx.x; i < n * MT; i += blockDim.x) {
+        const int j = i / MT, k = i - j * MT;
+        V.pq[j * mp + k] = make_int2(__ldg(I.p + i), __ldg(I.q + i));
+    }
+    fam_tables_finish<MT>(V, n, mp);
+    uint8_t *rec_s = V.recb;
+    int32_t *Cs = V.cc, *SQs = V.sq;  // the node's release times and S + qmin per machine
+    for (long long t = (long long)blockIdx.x * W + warp; t < count; t += (long long)gridDim.x * W) {
+        if (lane < NV)
+            reinterpret_cast<uint4 *>(rec_s)[lane] = __ldg(reinterpret_cast<const uint4 *>(nodes + t * stride) + lane);
+        __syncwarp();
+        int bad = 0;
+        if (lane == 0) {  // a permutation of 0..n-1 and a depth <= n
+            unsigned long long seen = 0ull;
+            bad = rec_s[n] > n;
+            for (int i = 0; i < n; ++i) {
+                const int j = rec_s[i];
+                if (j >= n || ((seen >> j) & 1ull)) bad = 1;
+                else seen |= 1ull << j;
+            }
+        }
+        bad = __shfl_sync(0xffffffffu, bad, 0);
+        if (bad) {
+            if (lane == 0) {
+                lb_out[t] = FSP_LB_INVALID;
+                atomicOr(I.status, 1);
+            }
+            __syncwarp();
+            continue;
+        }
+        const int d = rec_s[n];
+        const int k = lane < MT ? lane : MT - 1;
+        int32_t Sk = 0, Qk = 0x7fffffff, Pk = 0x7fffffff;
+        for (int i = d; i < n; ++i) {
+            const int2 v = V.pq[rec_s[i] * mp + k];
+            Sk += v.x;
+            Qk = min(Qk, v.y);
+            Pk = min(Pk, v.x);
+        }
+        int32_t Ck = 0;
+        if (d > 0) {
+            int32_t p0 = fam_prefix_p(0, lane, d, k, mp, rec_s, V.pq);
+            int32_t p1 = fam_prefix_p(1, lane, d, k, mp, rec_s, V.pq);
+            for (int s = 0; s < d + MT - 1; ++s) {
+                const int32_t p2 = fam_prefix_p(s + 2, lane, d, k, mp, rec_s, V.pq);
+                int32_t up = __shfl_up_sync(0xffffffffu, Ck, 1);
+                if (lane == 0) up = 0;
+                const int i = s - lane;
+                if (lane < MT && i >= 0 && i < d) Ck = max(Ck, up) + p0;
+                p0 = p1;
+                p1 = p2;
+            }
+        }
+        if (I.var == FSP_BOUND_HEADS && d < n) {
+            // R_k = max(C_k, R_{k-1} + min over the remaining set of p[j][k-1])
+            for (int kk = 1; kk < MT; ++kk) {
+                const int32_t r_prev = __shfl_sync(0xffffffffu, Ck, kk - 1);
+                const int32_t p_prev = __shfl_sync(0xffffffffu, Pk, kk - 1);
+                if (lane == kk) Ck = max(Ck, r_prev + p_prev);
+            }
+        }
+        const int32_t SQk = Sk + (Qk == 0x7fffffff ? 0 : Qk);
+        if (lane < MT) {
+            Cs[lane] = Ck;
+            SQs[lane] = SQk;
+        }
+        __syncwarp();
+        int32_t best = lane < MT ? Ck + SQk : 0;
+        // the pairs: forward scans over the remaining set
+        int klc[NS];
+        Mask pm[NS];
+        int32_t E[NS], M[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            klc[s] = min(lane + 32 * s, P - 1);
+            pm[s] = 0;
+            E[s] = 0;
+            M[s] = FSP_NEG;
+        }
+        for (int i = d; i < n; ++i) {
+            const int j = rec_s[i];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) pm[s] |= (Mask)1 << V.rk8[klc[s] * V.rks8 + j];
+        }
+        const int2 *wrow = V.we;
+#pragma unroll 2
+        for (int pos = 0; pos < n; ++pos, wrow += P) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const int2 v = wrow[klc[s]];
+                const bool b = pm[s] & 1u;
+                pm[s] >>= 1;
+                M[s] = __viaddmax_s32(E[s], b ? v.x : FSP_NEG, M[s]);
+                E[s] += b ? v.y : 0;
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int km = V.klm[klc[s]];
+            const int kk = km & 255, l = km >> 8;
+            const int32_t v = __viaddmax_s32(SQs[l], __viaddmax_s32(Cs[kk], M[s], Cs[l]), best);
+            if (lane + 32 * s < P) best = v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) lb_out[t] = best;
+        __syncwarp();
+    }
+}
+
+// Launch the warp-per-node bound on a pool of count nodes, if this shape has
+// the kernel and its tables fit; returns FSP_ERR_ARG otherwise (the caller
+// then uses the per-node kernels).
+int fam_bound_pool(fsp_instance *I, int mt, int nv, const uint8_t *nodes, long long count, int32_t *lb_out,
+                   cudaStream_t st)
+{
+    typedef void (*Fn)(DevInst, const uint8_t *, long long, int32_t *, FamSmem);
+    Fn fn = nullptr;
+#define FSP_CASEP(MT_, NV_) \
+    if (mt == MT_ && nv == NV_) fn = &k_bound_pool_warp<MT_, NV_>;
+    FSP_SHAPES_FAMILY(FSP_CASEP)
+#undef FSP_CASEP
+    const int w = fn ? family_warps(I, mt, nv) : 0;
+    if (!fn || w == 0) return FSP_ERR_ARG;
+    const FamSmem L = family_smem_layout(I, mt, nv, w);
+    int rc = fsp_allow_smem(I, (const void *)fn, L.bytes);
+    if (rc != FSP_OK) return rc;
+    long long grid = (count + w - 1) / w;
+    if (grid > I->sm_count) grid = I->sm_count;
+    fn<<<(unsigned)grid, w * 32, L.bytes, st>>>(dev_view(I), nodes, count, lb_out, L);
+    FSP_CUDA(cudaGetLastError());
+    return FSP_OK;
+}
+
 // Warps per CTA that fit (the most up to FAM_MAX_WARPS); 0 if fewer than
 // FAM_MIN_WARPS fit, and the per-child kernel is used instead.
 int family_warps(const fsp_instance *I, int MT, int NV)

@@ -94,6 +94,9 @@ static inline FamSmem family_smem_layout(const fsp_instance *I, int MT, int NV, 
 }
 
 int family_warps(const fsp_instance *I, int MT, int NV);
+int fam_bound_pool(fsp_instance *I, int mt, int nv, const uint8_t *nodes, long long count, int32_t *lb_out,
+                   cudaStream_t st);
+#define FAM_POOL_SMALL 16384  // fsp_bound_pool uses one warp per node up to this many nodes
 
 typedef void (*BranchFamilyFn)(DevInst, SolveWs, FamSmem);
 BranchFamilyFn pick_branch_family(int mt, int nv, bool learned, bool heads);

@@ -590,39 +590,11 @@ __device__ __forceinline__ void fm_cp16(void *dst_smem, const void *src_gmem)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src_gmem));
 }
 
-// Features of one node with the machine count known at compile time: the
-// arrays stay in registers and p / tails come from shared memory ({p, q}
-// rows of odd stride mp).  Same values as fsp_features.
-template <int MT>
-__device__ __forceinline__ void fm_features(const uint8_t *r, int n, const int2 *pq, int mp, float T, float *x)
-{
-    const int d = r[n] <= n ? r[n] : n;
-    int32_t C[MT], S[MT];
-#pragma unroll
-    for (int k = 0; k < MT; ++k) { C[k] = 0; S[k] = 0; }
-    for (int i = 0; i < n; ++i) {
-        const int j = r[i] < n ? r[i] : 0;
-        const int2 *row = pq + j * mp;
-        if (i < d) {
-            C[0] += row[0].x;
-#pragma unroll
-            for (int k = 1; k < MT; ++k) C[k] = max(C[k], C[k - 1]) + row[k].x;
-        } else {
-#pragma unroll
-            for (int k = 0; k < MT; ++k) S[k] += row[k].x;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < MT; ++k) {
-        x[k] = __fdiv_rn((float)C[k], T);
-        x[MT + k] = __fdiv_rn((float)S[k], T);
-    }
-    x[2 * MT] = __fdiv_rn((float)d, (float)n);
-}
-
-// Half of fm_features' columns as bf16 into xr: part 0 the release times
-// (columns 0..MT-1), the depth (2 MT) and the zero padding; part 1 the
-// remaining work (MT..2 MT-1).  Same values as fsp_features.
+// Half of a node's features as bf16 into xr (the machine count known at
+// compile time, p from the shared {p, q} rows of odd stride mp): part 0 the
+// release times over T (columns 0..MT-1), the depth over n (2 MT) and the
+// zero padding; part 1 the remaining work over T (MT..2 MT-1).  Same values
+// as fsp_features.
 template <int MT>
 __device__ __forceinline__ void fm_features_part(const uint8_t *r, int n, const int2 *pq, int mp, float T, int part,
                                                  bf16_t *xr)

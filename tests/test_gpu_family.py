@@ -117,3 +117,40 @@ def test_block_shape_tuning_reports_a_shape_and_keeps_the_search(F):
         assert a[key] == b[key], key
     assert np.array_equal(a["trace"], b["trace"])
     assert b["tuned_warps"] == 16  # a fixed pool keeps the most warps that fit
+
+
+@pytest.mark.parametrize("n,m,seed,count", [(20, 20, 1, 4096), (12, 5, 2, 777), (33, 10, 3, 3000), (50, 20, 4, 1500),
+                                            (63, 5, 5, 1)])
+def test_small_pools_one_warp_per_node(F, n, m, seed, count):
+    """fsp_bound_pool on a small pool (one warp per node) gives the oracle's
+    bounds and the per-thread kernel's, also for the heads variant, and flags
+    malformed records the same way."""
+    import torch
+    p = inputs.instance(n, m, seed)
+    inst = F.fsp_create_instance(p)
+    rec = inputs.random_prefix_pool(n, count, inputs.SplitMix64(seed + 9))
+    rec[::5, n] = n
+    rec[1::7, n] = n - 1
+    dev = torch.from_numpy(rec).cuda()
+    for variant in (F.BOUND_BASE, F.BOUND_HEADS):
+        inst.set_bound(variant)
+        got = F.fsp_bound_pool(inst, dev).cpu().numpy()
+        F.fsp_check_status(inst)
+        assert np.array_equal(got, oracle.bound_pool(p, rec, bound=variant))
+        os.environ["FSP_FAMILY_POOL0"] = "1"
+        try:
+            per_thread = F.fsp_bound_pool(inst, dev).cpu().numpy()
+        finally:
+            del os.environ["FSP_FAMILY_POOL0"]
+        assert np.array_equal(got, per_thread)
+    if count > 3:
+        bad = rec.copy()
+        bad[2, 0] = bad[2, 1]          # a repeated job
+        bad[3, n] = n + 1              # depth > n
+        got = F.fsp_bound_pool(inst, torch.from_numpy(bad).cuda()).cpu().numpy()
+        assert got[2] == F.LB_INVALID and got[3] == F.LB_INVALID
+        with pytest.raises(F.FspError):
+            F.fsp_check_status(inst)
+        keep = np.ones(count, bool)
+        keep[[2, 3]] = False
+        assert np.array_equal(got[keep], oracle.bound_pool(p, rec[keep], bound=F.BOUND_HEADS))
