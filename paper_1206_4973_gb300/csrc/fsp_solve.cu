@@ -142,7 +142,7 @@ __device__ __forceinline__ bool init_node_fast(uint8_t *r, int n)
 {
     FspRec<NV> rec;
     fsp_load_rec(rec, r);
-    const int d = (int)fsp_rec_byte_dyn(rec, n);
+    const int d = r[n];  // a byte load: no run-time index into the record's registers
     bool bad = d > n - 2;
     unsigned long long seen = 0ull, rem = 0ull;
 #pragma unroll
@@ -173,7 +173,7 @@ __device__ __forceinline__ bool init_node_fast(uint8_t *r, int n)
     return true;
 }
 
-__global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long count, int ub0)
+__global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long count, int ub0, int wide)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
@@ -187,15 +187,20 @@ __global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long coun
         c->ub_iter = ub0;
         for (int i = 0; i < 7; ++i) c->cnt[i] = 0;
     }
+    if (t >= count || wide) return;  // records of n >= 64 jobs: k_solve_init_nodes_wide
+    uint8_t *r = ws.stack + t * stride;
+    const int nv = stride >> 4;
+    const bool ok = nv == 1 ? init_node_fast<1>(r, n) : nv == 2 ? init_node_fast<2>(r, n)
+                  : nv == 3 ? init_node_fast<3>(r, n) : init_node_fast<4>(r, n);
+    if (!ok) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
+}
+
+// The same for n >= 64 (records of 80 bytes or more): masks of 8 words.
+__global__ void k_solve_init_nodes_wide(SolveWs ws, int n, int stride, long long count)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
     uint8_t *r = ws.stack + t * stride;
-    if (n <= 63) {
-        const int nv = stride >> 4;
-        const bool ok = nv == 1 ? init_node_fast<1>(r, n) : nv == 2 ? init_node_fast<2>(r, n)
-                      : nv == 3 ? init_node_fast<3>(r, n) : init_node_fast<4>(r, n);
-        if (!ok) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
-        return;
-    }
     const int d = r[n];
     uint32_t seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t rem[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -934,7 +939,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(SolveCtl), st));
             TRY(cudaMemcpyAsync(ws.stack, o.init_nodes, (size_t)o.init_count * I->stride, cudaMemcpyDefault, st));
             const unsigned gi = (unsigned)((o.init_count + 255) / 256);
-            k_solve_init_nodes<<<gi, 256, 0, st>>>(ws, I->n, I->stride, o.init_count, ub0);
+            k_solve_init_nodes<<<gi, 256, 0, st>>>(ws, I->n, I->stride, o.init_count, ub0, I->n > 63);
+            if (I->n > 63) k_solve_init_nodes_wide<<<gi, 256, 0, st>>>(ws, I->n, I->stride, o.init_count);
             k_init_cum_blocks<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
             k_init_cum<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
         } else {

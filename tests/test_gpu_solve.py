@@ -211,3 +211,23 @@ def test_v1_search_kernels_match_oracle(F, n, m, seed, pool, monkeypatch):
     ref = oracle.solve(p, pool=pool, trace_cap=100000)
     got = F.fsp_solve(F.fsp_create_instance(p), pool_size=pool, trace_cap=100000)
     same(got, ref)
+
+
+def test_wide_start_records_match_oracle(F):
+    """Start records of n >= 64 jobs (their own validation kernel): a few
+    iterations from random prefixes equal the oracle's; a malformed one is
+    rejected."""
+    n, m = 70, 5
+    p = inputs.instance(n, m, 171)
+    rec = inputs.random_prefix_pool(n, 300, inputs.SplitMix64(172))
+    rec[:, n] = np.minimum(rec[:, n], n - 2)
+    ub = oracle.makespan(p, list(range(n)))
+    inst = F.fsp_create_instance(p)
+    ref = oracle.solve(p, ub0=ub, pool=512, init_nodes=rec, max_iterations=3, trace_cap=8)
+    got = F.fsp_solve(inst, ub0=ub, pool_size=512, init_nodes=rec, max_iterations=3, trace_cap=8)
+    same(got, ref)
+    bad = rec.copy()
+    bad[5, 0] = bad[5, 1]
+    with pytest.raises(F.FspError) as e:
+        F.fsp_solve(inst, ub0=ub, pool_size=512, init_nodes=bad, max_iterations=3)
+    assert e.value.code == F.ERR_ARG
