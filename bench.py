@@ -444,7 +444,7 @@ def main():
             ev[i][1].record(st)
             bound_ms.append(r["bound_ms"])
             bounded += r["nodes_bounded"]
-            launches += 1 + 4 * r["iterations"]
+            launches += 2 + 4 * r["iterations"]  # k_solve_init_nodes, k_init_cum; per iteration select, branch-bound, count, push
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
     if world > 1:

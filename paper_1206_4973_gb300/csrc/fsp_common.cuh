@@ -62,6 +62,9 @@ int fsp_blocks_per_sm(fsp_instance *I, const void *kernel, int block, size_t sme
 #define FSP_PINNED_BYTES 1024
 int fsp_pinned_take(fsp_instance *I, void **p);
 void fsp_pinned_give(fsp_instance *I, void *p);
+// True when p is memory of the current device (not host, not managed) aligned
+// to `align` bytes, so that kernels may read it in place.
+bool fsp_on_device(const void *p, int align);
 
 // By-value view for kernels.
 struct DevInst {

@@ -69,6 +69,19 @@ int fsp_pinned_take(fsp_instance *I, void **p)
     return FSP_OK;
 }
 
+bool fsp_on_device(const void *p, int align)
+{
+    if (!p || ((uintptr_t)p % (uintptr_t)align) != 0) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 void fsp_pinned_give(fsp_instance *I, void *p)
 {
     if (!p) return;

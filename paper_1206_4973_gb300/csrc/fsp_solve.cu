@@ -25,6 +25,9 @@
 
 #define SOLVE_B 256        // threads per block of the per-child kernels
 #define SELECT_B 1024      // threads of the selection CTA
+#define SOLVE_RB 512       // one read-back: the control block (256 bytes), then the incumbent
+static_assert(sizeof(SolveCtl) <= 256, "the incumbent follows the control block at byte 256");
+static_assert(2 * SOLVE_RB <= FSP_PINNED_BYTES, "two read-back slots per pinned buffer");
 
 struct SolveLayout {
     long long pool_max, max_children, cap, trace_cap, max_parents;
@@ -69,6 +72,7 @@ static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout
     L->trace_cap = (o->trace && o->trace_cap > 0) ? o->trace_cap : 0;
     size_t off = 0;
     L->off_ctl = off; off = align256(off + sizeof(SolveCtl));
+    L->off_inc = off; off = align256(off + 256);  // right after the control block: one read-back
     L->off_stack = off; off = align256(off + (size_t)L->cap * I->stride);
     L->off_cum = off; off = align256(off + (size_t)L->cap * 8);
     L->off_iblk = off; off = align256(off + (size_t)((init + 255) / 256 + 1) * 8);
@@ -76,7 +80,6 @@ static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout
     L->off_lbs = off; off = align256(off + (size_t)L->max_children * 4);
     L->off_poff = off; off = align256(off + (size_t)(L->max_children + 2) * 4);
     L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 12);
-    L->off_inc = off; off = align256(off + 256);
     L->off_trace = off; off = align256(off + (size_t)L->trace_cap * 32);
     L->learned = o->order == FSP_ORDER_LEARNED;
     L->topk = o->topk > 0 ? o->topk : 4;
@@ -136,13 +139,14 @@ __global__ void k_solve_init(SolveWs ws, int n, int stride, int ub0)
 
 // Start from caller records: validate each (a permutation, depth <= n-2) and
 // re-sort its remaining part by job index, the order branching relies on.
-// n <= 63: the record and the job masks stay in registers.
+// n <= 63: the record and the job masks stay in registers; the record is read
+// from `src` (the caller's device copy, or the stack itself) and written to
+// `dst` on the stack.
 template <int NV>
-__device__ __forceinline__ bool init_node_fast(uint8_t *r, int n)
+__device__ __forceinline__ bool init_node_fast(const uint8_t *src, uint8_t *dst, int n, int d)
 {
     FspRec<NV> rec;
-    fsp_load_rec(rec, r);
-    const int d = r[n];  // a byte load: no run-time index into the record's registers
+    fsp_load_rec(rec, src);
     bool bad = d > n - 2;
     unsigned long long seen = 0ull, rem = 0ull;
 #pragma unroll
@@ -169,13 +173,21 @@ __device__ __forceinline__ bool init_node_fast(uint8_t *r, int n)
         }
     }
     (void)o;
-    fsp_store_rec(rec, r);
+    fsp_store_rec(rec, dst);
     return true;
 }
 
-__global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long count, int ub0, int wide)
+__device__ __forceinline__ long long block_sum_ll(long long v, long long *red);
+
+// One thread per start record: the control block, the record validated and
+// copied (or re-sorted in place when src is the stack), and the children of
+// each block of 256 records for the running counts (k_init_cum).  A malformed
+// record sets the status; the first selection then does nothing.
+__global__ void __launch_bounds__(SOLVE_B) k_solve_init_nodes(SolveWs ws, const uint8_t *src, int n, int stride,
+                                                              long long count, int ub0, int wide)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ long long red[SOLVE_B / 32];
+    const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
     if (t == 0) {
         SolveCtl *c = ws.ctl;
         c->stack_size = count;
@@ -187,12 +199,20 @@ __global__ void k_solve_init_nodes(SolveWs ws, int n, int stride, long long coun
         c->ub_iter = ub0;
         for (int i = 0; i < 7; ++i) c->cnt[i] = 0;
     }
-    if (t >= count || wide) return;  // records of n >= 64 jobs: k_solve_init_nodes_wide
-    uint8_t *r = ws.stack + t * stride;
-    const int nv = stride >> 4;
-    const bool ok = nv == 1 ? init_node_fast<1>(r, n) : nv == 2 ? init_node_fast<2>(r, n)
-                  : nv == 3 ? init_node_fast<3>(r, n) : init_node_fast<4>(r, n);
-    if (!ok) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
+    int d = 0;
+    if (t < count) {
+        d = src[t * stride + n];  // a byte load: no run-time index into the record's registers
+        if (!wide) {  // records of n >= 64 jobs: k_solve_init_nodes_wide, on the stack
+            const uint8_t *r = src + t * stride;
+            uint8_t *w = ws.stack + t * stride;
+            const int nv = stride >> 4;
+            const bool ok = nv == 1 ? init_node_fast<1>(r, w, n, d) : nv == 2 ? init_node_fast<2>(r, w, n, d)
+                          : nv == 3 ? init_node_fast<3>(r, w, n, d) : init_node_fast<4>(r, w, n, d);
+            if (!ok) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
+        }
+    }
+    const long long s = block_sum_ll(t < count ? n - d : 0, red);
+    if (threadIdx.x == 0) ws.iblk[blockIdx.x] = s;
 }
 
 // The same for n >= 64 (records of 80 bytes or more): masks of 8 words.
@@ -257,18 +277,9 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long *red)
     return s;
 }
 
-// Running children counts of the start records (stack order): the children
-// of each block of 256 records, then each block's records add the blocks
-// before them and their own prefix.
-__global__ void __launch_bounds__(SOLVE_B) k_init_cum_blocks(SolveWs ws, int n, int stride, long long count)
-{
-    __shared__ long long red[SOLVE_B / 32];
-    const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
-    const long long r = t < count ? n - (int)ws.stack[t * stride + n] : 0;
-    const long long s = block_sum_ll(r, red);
-    if (threadIdx.x == 0) ws.iblk[blockIdx.x] = s;
-}
-
+// Running children counts of the start records (stack order): each block of
+// 256 records adds the children of the blocks before it (summed by
+// k_solve_init_nodes) and its own prefix.
 __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot);
 
 __global__ void __launch_bounds__(SOLVE_B) k_init_cum(SolveWs ws, int n, int stride, long long count)
@@ -906,8 +917,10 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
 
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t pe[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    cudaEvent_t rb[2] = {nullptr, nullptr};  // read-backs of the control block
-    void *pin = nullptr;                     // their pinned host buffers
+    cudaEvent_t rb[2] = {nullptr, nullptr};  // read-backs launched ahead
+    void *pin = nullptr;                     // two pinned read-back slots of SOLVE_RB bytes
+    const uint8_t *last = nullptr;           // the slot h was taken from (its incumbent at byte 256)
+    bool idle = false;                       // nothing enqueued since the last read-back's sync
     double t_sel = 0, t_bb = 0, t_cmp = 0, t_inf = 0;
     PoolTuner tuner;
     BlockTuner btuner;
@@ -926,22 +939,33 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     if (prof)
         for (int i = 0; i < 5; ++i)
             if ((rc = fsp_event_take(I, &pe[i])) != FSP_OK) goto out;
+    if ((rc = fsp_pinned_take(I, &pin)) != FSP_OK) goto out;
     if (timed) TRY(cudaEventRecord(ev0, st));
     if (o.pool_size == 0) tuner.start(per_cta, I->sm_count, tuner_max_pool(I), o.tune_window);
     if (o.pool_size == 0 && P->bf) btuner.start(P->nfam, o.tune_window);
     if (I->n == 1) {
         k_solve_single<<<1, 32, 0, st>>>(ws, I->d_p, I->m, ub0);
         TRY(cudaGetLastError());
-        TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
+        if (timed) TRY(cudaEventRecord(ev1, st));
+        TRY(cudaMemcpyAsync(pin, ws.ctl, 256 + I->n, cudaMemcpyDeviceToHost, st));
         TRY(cudaStreamSynchronize(st));
+        last = (const uint8_t *)pin;
+        memcpy(&h, last, sizeof h);
+        idle = true;
     } else {
         if (o.init_nodes && o.init_count > 0) {
             TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(SolveCtl), st));
-            TRY(cudaMemcpyAsync(ws.stack, o.init_nodes, (size_t)o.init_count * I->stride, cudaMemcpyDefault, st));
-            const unsigned gi = (unsigned)((o.init_count + 255) / 256);
-            k_solve_init_nodes<<<gi, 256, 0, st>>>(ws, I->n, I->stride, o.init_count, ub0, I->n > 63);
-            if (I->n > 63) k_solve_init_nodes_wide<<<gi, 256, 0, st>>>(ws, I->n, I->stride, o.init_count);
-            k_init_cum_blocks<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
+            const bool wide = I->n > 63;
+            // records already on this device are read in place by the start
+            // kernel; host records (and records of n >= 64 jobs) are copied first
+            const uint8_t *src = o.init_nodes;
+            if (wide || !fsp_on_device(src, 16)) {
+                TRY(cudaMemcpyAsync(ws.stack, o.init_nodes, (size_t)o.init_count * I->stride, cudaMemcpyDefault, st));
+                src = ws.stack;
+            }
+            const unsigned gi = (unsigned)((o.init_count + SOLVE_B - 1) / SOLVE_B);
+            k_solve_init_nodes<<<gi, SOLVE_B, 0, st>>>(ws, src, I->n, I->stride, o.init_count, ub0, wide);
+            if (wide) k_solve_init_nodes_wide<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
             k_init_cum<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
         } else {
             k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
@@ -963,6 +987,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     } while (0)
             const int grid = (int)((pool + I->n + SOLVE_B - 1) / SOLVE_B);
             const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
+            idle = false;
             if (prof) LTRY(cudaEventRecord(pe[0], st));
             k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool, o.node_budget, o.max_iterations);
             if (prof) LTRY(cudaEventRecord(pe[1], st));
@@ -1027,8 +1052,12 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         long long it0 = -1;  // first iteration launched ahead
         for (long long it = 0;; ++it) {
             if (it > 0) {
-                TRY(cudaMemcpyAsync(&h, ws.ctl, sizeof h, cudaMemcpyDeviceToHost, st));
+                if (timed) TRY(cudaEventRecord(ev1, st));  // the end of the search if it stops here
+                TRY(cudaMemcpyAsync(pin, ws.ctl, 256 + I->n, cudaMemcpyDeviceToHost, st));
                 TRY(cudaStreamSynchronize(st));
+                last = (const uint8_t *)pin;
+                memcpy(&h, last, sizeof h);
+                idle = true;
             }
             if (prof && it > 0) {
                 float a = 0, b = 0, c = 0;
@@ -1054,6 +1083,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             }
             if (o.log_nodes && it > 0 && logged < o.log_cap && h.n_children > 0) {
                 const long long k = h.n_children < o.log_cap - logged ? h.n_children : o.log_cap - logged;
+                idle = false;
                 TRY(cudaMemcpyAsync(o.log_nodes + logged * I->stride, ws.children, (size_t)k * I->stride,
                                     cudaMemcpyDeviceToDevice, st));
                 if (o.log_lbs)
@@ -1082,18 +1112,21 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if ((rc = launch_iter(pool)) != FSP_OK) goto out;
         }
         if (it0 >= 0) {
-            if ((rc = fsp_pinned_take(I, &pin)) != FSP_OK) goto out;
             if ((rc = fsp_event_take(I, &rb[0])) != FSP_OK || (rc = fsp_event_take(I, &rb[1])) != FSP_OK) goto out;
-            SolveCtl *hb = reinterpret_cast<SolveCtl *>(pin);
+            uint8_t *hb = reinterpret_cast<uint8_t *>(pin);
             if ((rc = launch_iter(pool_of(it0))) != FSP_OK) goto out;
-            TRY(cudaMemcpyAsync(&hb[it0 & 1], ws.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
+            TRY(cudaMemcpyAsync(hb + (it0 & 1) * SOLVE_RB, ws.ctl, 256 + I->n, cudaMemcpyDeviceToHost, st));
             TRY(cudaEventRecord(rb[it0 & 1], st));
             for (long long it = it0 + 1;; ++it) {
                 if ((rc = launch_iter(pool_of(it))) != FSP_OK) goto out;
-                TRY(cudaMemcpyAsync(&hb[it & 1], ws.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, st));
+                TRY(cudaMemcpyAsync(hb + (it & 1) * SOLVE_RB, ws.ctl, 256 + I->n, cudaMemcpyDeviceToHost, st));
                 TRY(cudaEventRecord(rb[it & 1], st));
                 TRY(cudaEventSynchronize(rb[(it - 1) & 1]));
-                h = hb[(it - 1) & 1];  // the state after `it` iterations
+                // the state after `it` iterations; iteration it + 1, launched
+                // ahead, does nothing if the search stops here, so this slot
+                // (its incumbent included) is the final state
+                last = hb + ((it - 1) & 1) * SOLVE_RB;
+                memcpy(&h, last, sizeof h);
                 if (h.status != 0) {
                     rc = h.status;
                     fsp_set_error(rc == FSP_ERR_CAPACITY ? "fsp_solve: stack capacity exceeded"
@@ -1108,17 +1141,17 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             }
         }
     }
-    if (timed) {
-        TRY(cudaEventRecord(ev1, st));
-        TRY(cudaEventSynchronize(ev1));
-    } else {
-        TRY(cudaStreamSynchronize(st));
+    if (!idle) {  // after a read-back the stream is already idle and ev1 recorded before it
+        if (timed) {
+            TRY(cudaEventRecord(ev1, st));
+            TRY(cudaEventSynchronize(ev1));
+        } else {
+            TRY(cudaStreamSynchronize(st));
+        }
     }
     *cmax = h.ub;
-    if (h.cnt[5] > 0) {
-        uint8_t pb[FSP_MAX_JOBS + 1];
-        TRY(cudaMemcpy(pb, ws.inc, I->n, cudaMemcpyDeviceToHost));
-        for (int i = 0; i < I->n; ++i) perm[i] = pb[i];
+    if (h.cnt[5] > 0 && last) {  // the incumbent came with the control block
+        for (int i = 0; i < I->n; ++i) perm[i] = last[256 + i];
     } else if (o.ub0_perm) {
         for (int i = 0; i < I->n; ++i) perm[i] = o.ub0_perm[i];
     }

@@ -217,6 +217,7 @@ def test_wide_start_records_match_oracle(F):
     """Start records of n >= 64 jobs (their own validation kernel): a few
     iterations from random prefixes equal the oracle's; a malformed one is
     rejected."""
+    import torch
     n, m = 70, 5
     p = inputs.instance(n, m, 171)
     rec = inputs.random_prefix_pool(n, 300, inputs.SplitMix64(172))
@@ -224,10 +225,35 @@ def test_wide_start_records_match_oracle(F):
     ub = oracle.makespan(p, list(range(n)))
     inst = F.fsp_create_instance(p)
     ref = oracle.solve(p, ub0=ub, pool=512, init_nodes=rec, max_iterations=3, trace_cap=8)
-    got = F.fsp_solve(inst, ub0=ub, pool_size=512, init_nodes=rec, max_iterations=3, trace_cap=8)
-    same(got, ref)
+    for init in (rec, torch.from_numpy(rec).cuda()):
+        got = F.fsp_solve(inst, ub0=ub, pool_size=512, init_nodes=init, max_iterations=3, trace_cap=8)
+        same(got, ref)
     bad = rec.copy()
     bad[5, 0] = bad[5, 1]
     with pytest.raises(F.FspError) as e:
         F.fsp_solve(inst, ub0=ub, pool_size=512, init_nodes=bad, max_iterations=3)
     assert e.value.code == F.ERR_ARG
+
+
+def test_device_start_records_in_place_or_copied(F):
+    """Start records on the device are read in place when 16-byte aligned and
+    copied first otherwise: both give the host records' search, and a
+    malformed record is rejected on either path."""
+    import torch
+    p, ub_perm, rec = frontier_20x20(3000)
+    ub = oracle.makespan(p, ub_perm)
+    ref = oracle.solve(p, ub0=ub, pool=2048, init_nodes=rec, max_iterations=2, trace_cap=4)
+    inst = F.fsp_create_instance(p)
+    flat = torch.zeros(rec.size + 8, dtype=torch.uint8, device="cuda")
+    flat[8:] = torch.from_numpy(rec.reshape(-1)).cuda()
+    odd = flat[8:].view(rec.shape)  # 8 bytes past an aligned base: copied first
+    assert odd.data_ptr() % 16 == 8
+    bad = rec.copy()
+    bad[77, 3] = bad[77, 4]
+    for init, wrong in ((torch.from_numpy(rec).cuda(), torch.from_numpy(bad).cuda()), (odd, None)):
+        got = F.fsp_solve(inst, ub0=ub, pool_size=2048, init_nodes=init, max_iterations=2, trace_cap=4)
+        same(got, ref)
+        if wrong is not None:
+            with pytest.raises(F.FspError) as e:
+                F.fsp_solve(inst, ub0=ub, pool_size=2048, init_nodes=wrong, max_iterations=2)
+            assert e.value.code == F.ERR_ARG
