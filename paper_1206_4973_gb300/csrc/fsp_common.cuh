@@ -62,9 +62,11 @@ int fsp_blocks_per_sm(fsp_instance *I, const void *kernel, int block, size_t sme
 #define FSP_PINNED_BYTES 1024
 int fsp_pinned_take(fsp_instance *I, void **p);
 void fsp_pinned_give(fsp_instance *I, void *p);
-// True when p is memory of the current device (not host, not managed) aligned
-// to `align` bytes, so that kernels may read it in place.
-bool fsp_on_device(const void *p, int align);
+// The address at which kernels on the current device read p in place: p for
+// memory of this device, the mapped address of pinned host memory (read over
+// the host link), nullptr for anything else (pageable or managed memory,
+// another device) or when not `align`-byte aligned: such data is copied first.
+const void *fsp_device_view(const void *p, int align);
 
 // By-value view for kernels.
 struct DevInst {

@@ -69,17 +69,21 @@ int fsp_pinned_take(fsp_instance *I, void **p)
     return FSP_OK;
 }
 
-bool fsp_on_device(const void *p, int align)
+const void *fsp_device_view(const void *p, int align)
 {
-    if (!p || ((uintptr_t)p % (uintptr_t)align) != 0) return false;
+    if (!p || ((uintptr_t)p % (uintptr_t)align) != 0) return nullptr;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         (void)cudaGetLastError();
-        return false;
+        return nullptr;
     }
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    return a.type == cudaMemoryTypeDevice && a.device == dev;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (a.type == cudaMemoryTypeDevice) return a.device == dev ? p : nullptr;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer &&
+        ((uintptr_t)a.devicePointer % (uintptr_t)align) == 0)
+        return a.devicePointer;
+    return nullptr;
 }
 
 void fsp_pinned_give(fsp_instance *I, void *p)

@@ -181,25 +181,26 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long *red);
 
 // One thread per start record: the control block, the record validated and
 // copied (or re-sorted in place when src is the stack), and the children of
-// each block of 256 records for the running counts (k_init_cum).  A malformed
-// record sets the status; the first selection then does nothing.
+// each block of 256 records for the running counts (k_init_cum).  A block
+// with a malformed record writes -1 there instead and k_init_cum, launched
+// after this kernel has set up the control block, raises the status; the
+// first selection then does nothing.
 __global__ void __launch_bounds__(SOLVE_B) k_solve_init_nodes(SolveWs ws, const uint8_t *src, int n, int stride,
                                                               long long count, int ub0, int wide)
 {
     __shared__ long long red[SOLVE_B / 32];
     const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
     if (t == 0) {
-        SolveCtl *c = ws.ctl;
-        c->stack_size = count;
-        c->s_pop = 0;
-        c->n_parents = 0;
-        c->n_children = 0;
-        c->best_key = ~0ull;
-        c->ub = ub0;
-        c->ub_iter = ub0;
-        for (int i = 0; i < 7; ++i) c->cnt[i] = 0;
+        SolveCtl c;
+        memset(&c, 0, sizeof c);
+        c.stack_size = count;
+        c.best_key = ~0ull;
+        c.ub = ub0;
+        c.ub_iter = ub0;
+        *ws.ctl = c;
     }
     int d = 0;
+    bool bad = false;
     if (t < count) {
         d = src[t * stride + n];  // a byte load: no run-time index into the record's registers
         if (!wide) {  // records of n >= 64 jobs: k_solve_init_nodes_wide, on the stack
@@ -208,11 +209,12 @@ __global__ void __launch_bounds__(SOLVE_B) k_solve_init_nodes(SolveWs ws, const 
             const int nv = stride >> 4;
             const bool ok = nv == 1 ? init_node_fast<1>(r, w, n, d) : nv == 2 ? init_node_fast<2>(r, w, n, d)
                           : nv == 3 ? init_node_fast<3>(r, w, n, d) : init_node_fast<4>(r, w, n, d);
-            if (!ok) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
+            bad = !ok;
         }
     }
     const long long s = block_sum_ll(t < count ? n - d : 0, red);
-    if (threadIdx.x == 0) ws.iblk[blockIdx.x] = s;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) ws.iblk[blockIdx.x] = bad ? -1 : s;
 }
 
 // The same for n >= 64 (records of 80 bytes or more): masks of 8 words.
@@ -279,20 +281,66 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long *red)
 
 // Running children counts of the start records (stack order): each block of
 // 256 records adds the children of the blocks before it (summed by
-// k_solve_init_nodes) and its own prefix.
+// k_solve_init_nodes) and its own prefix.  Up to INIT_SCAN_BLOCKS blocks each
+// block sums the blocks before it itself; above, k_init_scan first turns the
+// block sums into exclusive prefixes (scanned = 1).
+#define INIT_SCAN_BLOCKS 2048
 __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot);
 
-__global__ void __launch_bounds__(SOLVE_B) k_init_cum(SolveWs ws, int n, int stride, long long count)
+__global__ void __launch_bounds__(SOLVE_B) k_init_cum(SolveWs ws, int n, int stride, long long count, int scanned)
 {
     __shared__ long long red[SOLVE_B / 32];
     __shared__ int warp_tot[32];
     long long before = 0;
-    for (int i = threadIdx.x; i < (int)blockIdx.x; i += SOLVE_B) before += ws.iblk[i];
-    before = block_sum_ll(before, red);
+    if (scanned) {
+        before = ws.iblk[blockIdx.x];
+    } else {
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += SOLVE_B) before += ws.iblk[i];
+        before = block_sum_ll(before, red);
+        if (threadIdx.x == 0 && ws.iblk[blockIdx.x] < 0) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
+    }
     const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
     const int r = t < count ? n - (int)ws.stack[t * stride + n] : 0;
     const int incl = block_incl_scan(r, warp_tot);
     if (t < count) ws.cum[t] = before + incl;
+}
+
+// One CTA: exclusive prefix sums of the nb block sums, in place; a block
+// marked malformed (-1) raises the status.
+__global__ void __launch_bounds__(1024) k_init_scan(SolveWs ws, long long nb)
+{
+    __shared__ long long part[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long carry = 0;
+    bool bad = false;
+    for (long long base = 0; base < nb; base += 1024) {
+        const long long i = base + threadIdx.x;
+        long long v = i < nb ? ws.iblk[i] : 0;
+        if (v < 0) { bad = true; v = 0; }
+        long long x = v;  // inclusive warp scan
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane == 31) part[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            long long w = part[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const long long u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
+            }
+            part[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const long long incl = x + (wid > 0 ? part[wid - 1] : 0);
+        if (i < nb) ws.iblk[i] = carry + incl - v;
+        carry += part[31];
+        __syncthreads();
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&ws.ctl->status, FSP_ERR_ARG);
 }
 
 // Inclusive block scan of one int per thread (blockDim.x a multiple of 32).
@@ -954,19 +1002,20 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         idle = true;
     } else {
         if (o.init_nodes && o.init_count > 0) {
-            TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(SolveCtl), st));
             const bool wide = I->n > 63;
-            // records already on this device are read in place by the start
-            // kernel; host records (and records of n >= 64 jobs) are copied first
-            const uint8_t *src = o.init_nodes;
-            if (wide || !fsp_on_device(src, 16)) {
+            // records on this device or in pinned host memory are read in place
+            // by the start kernel; others (and records of n >= 64 jobs) are copied first
+            const uint8_t *src = wide ? nullptr : (const uint8_t *)fsp_device_view(o.init_nodes, 16);
+            if (!src) {
                 TRY(cudaMemcpyAsync(ws.stack, o.init_nodes, (size_t)o.init_count * I->stride, cudaMemcpyDefault, st));
                 src = ws.stack;
             }
             const unsigned gi = (unsigned)((o.init_count + SOLVE_B - 1) / SOLVE_B);
             k_solve_init_nodes<<<gi, SOLVE_B, 0, st>>>(ws, src, I->n, I->stride, o.init_count, ub0, wide);
             if (wide) k_solve_init_nodes_wide<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
-            k_init_cum<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
+            const int scanned = gi > INIT_SCAN_BLOCKS;
+            if (scanned) k_init_scan<<<1, 1024, 0, st>>>(ws, gi);
+            k_init_cum<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count, scanned);
         } else {
             k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
         }

@@ -95,9 +95,9 @@ def load(path: str | None = None):
         "fsp_bound_pool": (ctypes.c_int, [vp, vp, i64, ctypes.c_int32, vp, vp]),
         "fsp_check_status": (ctypes.c_int, [vp, vp]),
         "fsp_solve_workspace_bytes": (i64, [vp, ctypes.POINTER(fsp_options)]),
-        "fsp_solve": (ctypes.c_int, [vp, ctypes.c_int32, i32p, i32p, ctypes.POINTER(fsp_stats),
+        "fsp_solve": (ctypes.c_int, [vp, ctypes.c_int32, i32p, vp, ctypes.POINTER(fsp_stats),
                                      ctypes.POINTER(fsp_options)]),
-        "fsp_solve_noalloc": (ctypes.c_int, [vp, ctypes.c_int32, i32p, i32p, ctypes.POINTER(fsp_stats),
+        "fsp_solve_noalloc": (ctypes.c_int, [vp, ctypes.c_int32, i32p, vp, ctypes.POINTER(fsp_stats),
                                              ctypes.POINTER(fsp_options)]),
         "fsp_neh": (ctypes.c_int, [vp, i32p, i32p]),
         "fsp_tune_simulate": (i64, [i64, ctypes.c_int, i64, SCORE_FN, vp, ctypes.POINTER(ctypes.c_int64), i64,
@@ -248,12 +248,19 @@ def fsp_tune_simulate(nodes_per_cta: int, sms: int, max_pool: int, score):
     return out[:k].tolist(), int(best.value)
 
 
+_default_options = None  # fsp_default_options' struct, as bytes
+
+
 def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
              schedule=None, stream=None, init_nodes=None, init_count=None, max_iterations=0,
              out_nodes=None, profile=False, tune_window=0, schedule_out=None, model=None, topk=0,
              log_nodes=None, log_lbs=None):
-    o = fsp_options()
-    load().fsp_default_options(ctypes.byref(o))
+    global _default_options
+    if _default_options is None:
+        d = fsp_options()
+        load().fsp_default_options(ctypes.byref(d))
+        _default_options = bytes(d)
+    o = fsp_options.from_buffer_copy(_default_options)
     o.pool_size = int(pool_size)
     o.tune_window = int(tune_window)
     if model is not None:
@@ -349,8 +356,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     perm = np.full(inst.n, -1, np.int32)
     cmax = ctypes.c_int32(0)
     st = fsp_stats()
-    rc = _check(load().fsp_solve(inst.handle, int(ub0), ctypes.byref(cmax),
-                                 perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(st),
+    rc = _check(load().fsp_solve(inst.handle, int(ub0), ctypes.byref(cmax), perm.ctypes.data, ctypes.byref(st),
                                  ctypes.byref(o)))
     res = {k: int(getattr(st, k)) for k in STATS}
     for k in ("time_ms", "select_ms", "bound_ms", "compact_ms", "infer_ms"):
@@ -384,9 +390,8 @@ def fsp_solve_noalloc(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, 
     perm = np.full(inst.n, -1, np.int32)
     cmax = ctypes.c_int32(0)
     st = fsp_stats()
-    rc = _check(load().fsp_solve_noalloc(inst.handle, int(ub0), ctypes.byref(cmax),
-                                         perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(st),
-                                         ctypes.byref(o)))
+    rc = _check(load().fsp_solve_noalloc(inst.handle, int(ub0), ctypes.byref(cmax), perm.ctypes.data,
+                                         ctypes.byref(st), ctypes.byref(o)))
     res = {k: int(getattr(st, k)) for k in STATS}
     res["status"] = rc
     res["cmax"] = int(cmax.value)

@@ -236,9 +236,9 @@ def test_wide_start_records_match_oracle(F):
 
 
 def test_device_start_records_in_place_or_copied(F):
-    """Start records on the device are read in place when 16-byte aligned and
-    copied first otherwise: both give the host records' search, and a
-    malformed record is rejected on either path."""
+    """Start records on the device or in pinned host memory are read in place
+    when 16-byte aligned and copied first otherwise: every path gives the
+    pageable host records' search, and a malformed record is rejected."""
     import torch
     p, ub_perm, rec = frontier_20x20(3000)
     ub = oracle.makespan(p, ub_perm)
@@ -250,10 +250,32 @@ def test_device_start_records_in_place_or_copied(F):
     assert odd.data_ptr() % 16 == 8
     bad = rec.copy()
     bad[77, 3] = bad[77, 4]
-    for init, wrong in ((torch.from_numpy(rec).cuda(), torch.from_numpy(bad).cuda()), (odd, None)):
+    cases = ((torch.from_numpy(rec).cuda(), torch.from_numpy(bad).cuda()),
+             (torch.from_numpy(rec).pin_memory(), torch.from_numpy(bad).pin_memory()), (odd, None))
+    for init, wrong in cases:
         got = F.fsp_solve(inst, ub0=ub, pool_size=2048, init_nodes=init, max_iterations=2, trace_cap=4)
         same(got, ref)
         if wrong is not None:
             with pytest.raises(F.FspError) as e:
                 F.fsp_solve(inst, ub0=ub, pool_size=2048, init_nodes=wrong, max_iterations=2)
             assert e.value.code == F.ERR_ARG
+
+
+def test_large_start_stack_matches_oracle(F):
+    """More than 2048 blocks of 256 start records: the running children counts
+    come from the single-CTA scan of the block sums.  Two iterations equal the
+    oracle's, and a malformed record far down the stack is rejected."""
+    import torch
+    p, ub_perm, rec = frontier_20x20(700000)
+    assert len(rec) > 2048 * 256
+    ub = oracle.makespan(p, ub_perm)
+    ref = oracle.solve(p, ub0=ub, pool=8192, init_nodes=rec, max_iterations=2, trace_cap=4)
+    inst = F.fsp_create_instance(p)
+    got = F.fsp_solve(inst, ub0=ub, pool_size=8192, init_nodes=torch.from_numpy(rec).cuda(), max_iterations=2,
+                      trace_cap=4)
+    same(got, ref)
+    bad = rec.copy()
+    bad[600001, 0] = 20
+    with pytest.raises(F.FspError) as e:
+        F.fsp_solve(inst, ub0=ub, pool_size=8192, init_nodes=bad, max_iterations=2)
+    assert e.value.code == F.ERR_ARG
