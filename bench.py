@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 512 << 20
 SMS, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # DRAM bytes (read + write) of one branch-and-bound launch of the step, from the ncu capture in
 # profiles/k_branch_family_20x20_2e18_full.md; None once that kernel has changed since the capture.
-BB_TRAFFIC_BYTES = 982784
+BB_TRAFFIC_BYTES = 1083136
 
 
 def work_ops(depth, n=N_JOBS, m=N_MACH):

@@ -38,18 +38,19 @@
 #include "fsp_family.cuh"
 
 // Asynchronous copy of family f's record (lanes 0..NV-1, 16 bytes each) and
-// of its first child's index (lane NV) into this warp's buffers.
+// of the running children count below it (lane NV; its first child is the
+// count at the stack top minus this) into this warp's buffers.
 template <int NV>
 __device__ __forceinline__ void fam_fetch(const SolveWs &ws, long long S, int stride, int f, int lane,
-                                          uint8_t *rec_dst, int *poff_dst)
+                                          uint8_t *rec_dst, long long *cum_dst)
 {
     if (lane < NV) {
         const unsigned d = (unsigned)__cvta_generic_to_shared(rec_dst + lane * 16);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d),
                      "l"(ws.stack + (S - 1 - f) * stride + lane * 16));
     } else if (lane == NV) {
-        const unsigned d = (unsigned)__cvta_generic_to_shared(poff_dst);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(ws.poff + f));
+        const unsigned d = (unsigned)__cvta_generic_to_shared(cum_dst);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(ws.cum + (S - 1 - f)));
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -79,7 +80,8 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
     }
     fam_tables_finish<MT>(V, n, mp);
 
-    const long long S = ctl->s_pop + np;
+    const long long S = ctl->s_pop + np;  // the stack before the pops (np >= 1 here)
+    const long long top = ws.cum[S - 1];  // children of the whole stack
     const int ub_iter = ctl->ub_iter;
     // parents are taken from a shared counter one ahead: the next one's
     // record is copied into the other buffer while this one is processed
@@ -92,7 +94,7 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncwarp();
         const uint8_t *rec_s = V.recb + buf * 16 * NV;
-        const long long c0 = V.pofs[buf];
+        const long long c0 = top - V.pofs[buf];  // children of the parents above this one
         int fn = 0;
         if (lane == 0) fn = (int)atomicAdd(next_f, 1ull);
         fn = __shfl_sync(0xffffffffu, fn, 0);

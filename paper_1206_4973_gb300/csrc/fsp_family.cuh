@@ -113,7 +113,7 @@ struct FamView {
     int32_t *psa, *ab, *cc, *sq, *lbv, *T, *lm;
     uint16_t *lkl;
     uint8_t *recb;
-    int *pofs;
+    long long *pofs;
     int rks8, mtp;
 };
 
@@ -132,7 +132,7 @@ __device__ __forceinline__ FamView fam_view(unsigned char *smem, const FamSmem &
     V.pp = reinterpret_cast<int4 *>(wb + L.w_pp);  // heads variant: smallest p per machine
     V.ab = reinterpret_cast<int32_t *>(wb + L.w_ab);  // alpha[MT], beta[MT]
     V.recb = wb + L.w_rec;                            // two record buffers
-    V.pofs = reinterpret_cast<int *>(wb + L.w_pofs);  // and their first children
+    V.pofs = reinterpret_cast<long long *>(wb + L.w_pofs);  // and the running counts below them
     V.cc = reinterpret_cast<int32_t *>(wb + L.w_cc);
     V.sq = reinterpret_cast<int32_t *>(wb + L.w_sq);
     V.lbv = reinterpret_cast<int32_t *>(wb + L.w_lb);

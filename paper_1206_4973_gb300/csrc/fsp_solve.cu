@@ -374,9 +374,11 @@ __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot)
 // the top i records are cum[S-1] - cum[S-1-i]: the number of parents is the
 // largest i <= min(S, pool) whose children fit the pool (at least one),
 // found by a parallel search that narrows the interval SELECT_B-fold per
-// round, and the parents' first-child offsets follow from cum directly.
+// round.  The parents' first-child offsets follow from cum directly: written
+// to poff for the per-child kernels (write_poff), read from cum by the family
+// kernel itself.
 __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stride, long long pool,
-                                                    long long budget, long long max_it)
+                                                    long long budget, long long max_it, int write_poff)
 {
     SolveCtl *ctl = ws.ctl;
     const long long S = ctl->stack_size;
@@ -412,7 +414,8 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
     }
     const long long np = lo;
     const long long running = prefix(np);
-    for (long long i = threadIdx.x; i <= np; i += SELECT_B) ws.poff[i] = (int)prefix(i);
+    if (write_poff)
+        for (long long i = threadIdx.x; i <= np; i += SELECT_B) ws.poff[i] = (int)prefix(i);
     if (threadIdx.x == 0) {
         ctl->n_list = 0;
         ctl->early = 0;
@@ -1038,7 +1041,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
             idle = false;
             if (prof) LTRY(cudaEventRecord(pe[0], st));
-            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool, o.node_budget, o.max_iterations);
+            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool, o.node_budget, o.max_iterations,
+                                             P->bf == nullptr);
             if (prof) LTRY(cudaEventRecord(pe[1], st));
             if (P->bl) {
                 const long long npar = pool / 2 + 2;  // stacked nodes have >= 2 children
