@@ -20,6 +20,7 @@
 
 #include <chrono>
 #include <mutex>
+#include <type_traits>
 
 #include "fsp_family.cuh"
 
@@ -139,40 +140,53 @@ __global__ void k_solve_init(SolveWs ws, int n, int stride, int ub0)
 
 // Start from caller records: validate each (a permutation, depth <= n-2) and
 // re-sort its remaining part by job index, the order branching relies on.
-// n <= 63: the record and the job masks stay in registers; the record is read
-// from `src` (the caller's device copy, or the stack itself) and written to
-// `dst` on the stack.
+// n <= 63: the record and the job masks stay in registers (32-bit masks up to
+// two 16-byte words, n <= 31); the record is read from `src` (the caller's
+// buffer, or the stack itself) and written to `dst` on the stack.  The n jobs
+// form a permutation iff all are below n and their bits number n; a remaining
+// part already in increasing order is kept as it is.
+__device__ __forceinline__ int init_popc(uint32_t x) { return __popc(x); }
+__device__ __forceinline__ int init_popc(unsigned long long x) { return __popcll(x); }
+__device__ __forceinline__ int init_low(uint32_t x) { return __ffs((int)x) - 1; }
+__device__ __forceinline__ int init_low(unsigned long long x) { return __ffsll((long long)x) - 1; }
+
 template <int NV>
 __device__ __forceinline__ bool init_node_fast(const uint8_t *src, uint8_t *dst, int n, int d)
 {
+    typedef typename std::conditional<(NV <= 2), uint32_t, unsigned long long>::type M;
     FspRec<NV> rec;
     fsp_load_rec(rec, src);
-    bool bad = d > n - 2;
-    unsigned long long seen = 0ull, rem = 0ull;
+    bool ok = d <= n - 2, sorted = true;
+    M seen = 0, rem = 0;
+    int prev = -1;
 #pragma unroll
     for (int i = 0; i < 16 * NV; ++i) {
         if (i < n) {
             const int j = (int)((rec.w[i >> 2] >> ((i & 3) * 8)) & 0xFFu);
-            if (j >= n) { bad = true; continue; }
-            const unsigned long long bit = 1ull << j;
-            if (seen & bit) bad = true;
+            ok &= j < n;
+            const M bit = j < n ? (M)1 << j : (M)0;
             seen |= bit;
-            if (i >= d) rem |= bit;
+            if (i >= d) {
+                rem |= bit;
+                sorted &= j > prev;
+                prev = j;
+            }
         }
     }
-    if (bad) return false;
-    int o = d;  // rewrite positions d..n-1 with the remaining jobs in increasing order
+    if (!ok || init_popc(seen) != n) return false;
+    if (sorted) {
+        if (src != dst) fsp_store_rec(rec, dst);
+        return true;
+    }
 #pragma unroll
-    for (int i = 0; i < 16 * NV; ++i) {
+    for (int i = 0; i < 16 * NV; ++i) {  // positions d..n-1: the remaining jobs in increasing order
         if (i >= d && i < n) {
-            const int j = __ffsll((long long)rem) - 1;
-            rem &= rem - 1ull;
+            const int j = init_low(rem);
+            rem &= rem - (M)1;
             const int sh = (i & 3) * 8;
             rec.w[i >> 2] = (rec.w[i >> 2] & ~(0xFFu << sh)) | ((uint32_t)j << sh);
-            ++o;
         }
     }
-    (void)o;
     fsp_store_rec(rec, dst);
     return true;
 }
@@ -185,6 +199,7 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long *red);
 // with a malformed record writes -1 there instead and k_init_cum, launched
 // after this kernel has set up the control block, raises the status; the
 // first selection then does nothing.
+template <int NV>
 __global__ void __launch_bounds__(SOLVE_B) k_solve_init_nodes(SolveWs ws, const uint8_t *src, int n, int stride,
                                                               long long count, int ub0, int wide)
 {
@@ -204,12 +219,7 @@ __global__ void __launch_bounds__(SOLVE_B) k_solve_init_nodes(SolveWs ws, const 
     if (t < count) {
         d = src[t * stride + n];  // a byte load: no run-time index into the record's registers
         if (!wide) {  // records of n >= 64 jobs: k_solve_init_nodes_wide, on the stack
-            const uint8_t *r = src + t * stride;
-            uint8_t *w = ws.stack + t * stride;
-            const int nv = stride >> 4;
-            const bool ok = nv == 1 ? init_node_fast<1>(r, w, n, d) : nv == 2 ? init_node_fast<2>(r, w, n, d)
-                          : nv == 3 ? init_node_fast<3>(r, w, n, d) : init_node_fast<4>(r, w, n, d);
-            bad = !ok;
+            bad = !init_node_fast<NV>(src + t * stride, ws.stack + t * stride, n, d);
         }
     }
     const long long s = block_sum_ll(t < count ? n - d : 0, red);
@@ -1014,7 +1024,10 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 src = ws.stack;
             }
             const unsigned gi = (unsigned)((o.init_count + SOLVE_B - 1) / SOLVE_B);
-            k_solve_init_nodes<<<gi, SOLVE_B, 0, st>>>(ws, src, I->n, I->stride, o.init_count, ub0, wide);
+            const int nv = wide ? 1 : I->stride >> 4;  // wide: block sums only, the records follow
+            auto init_fn = nv == 1 ? &k_solve_init_nodes<1> : nv == 2 ? &k_solve_init_nodes<2>
+                         : nv == 3 ? &k_solve_init_nodes<3> : &k_solve_init_nodes<4>;
+            init_fn<<<gi, SOLVE_B, 0, st>>>(ws, src, I->n, I->stride, o.init_count, ub0, wide);
             if (wide) k_solve_init_nodes_wide<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
             const int scanned = gi > INIT_SCAN_BLOCKS;
             if (scanned) k_init_scan<<<1, 1024, 0, st>>>(ws, gi);
