@@ -127,6 +127,21 @@ def dist_init(args):
     return rank, world, local
 
 
+def whole_job_rate(units_local, seconds_local, world, device=None):
+    """Whole-job throughput of a timed region: the units all ranks processed
+    over the slowest rank's time (an all-reduce sum of the units and max of
+    the seconds; one rank needs no collective).  Returns (rate, seconds)."""
+    if world == 1:
+        return units_local / seconds_local, seconds_local
+    import torch
+    import torch.distributed as dist
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(seconds_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def step_config(frontier, ub, n_children, world):
     """The workload both arms report: one B&B iteration with a pool of 2^18
     children from the 20x20 seed-1 frontier."""
@@ -450,12 +465,7 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = bounded * world / t_total
+    value, t_total = whole_job_rate(bounded, sum(step_ms) / 1e3, world, dev)
 
     # ---- end to end through the C ABI with host buffers (frontier H2D inside the call)
     e2e_ms = []
