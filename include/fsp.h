@@ -113,7 +113,11 @@ typedef struct {
     const uint8_t *init_nodes; /* host or device or NULL: start from these node records
                                (bottom of the stack first) instead of the root; each
                                must have depth <= n-2; the remaining part of each
-                               record is re-sorted by job index on the device */
+                               record is re-sorted by job index on the device.  Memory
+                               of the current device or pinned host memory, 16-byte
+                               aligned and n <= 63, is read in place by the start
+                               kernel (never written); anything else is copied to the
+                               stack first */
     int64_t init_count;
     int64_t max_iterations; /* stop (FSP_INCOMPLETE) after this many iterations; 0 = no limit */
     uint8_t *out_nodes;     /* host or device or NULL: receives the stack left when the
