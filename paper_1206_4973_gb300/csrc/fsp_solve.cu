@@ -1181,15 +1181,22 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if ((rc = fsp_event_take(I, &rb[0])) != FSP_OK || (rc = fsp_event_take(I, &rb[1])) != FSP_OK) goto out;
             uint8_t *hb = reinterpret_cast<uint8_t *>(pin);
             if ((rc = launch_iter(pool_of(it0))) != FSP_OK) goto out;
+            if (timed) TRY(cudaEventRecord(ev1, st));  // moved to each later read-back
             TRY(cudaMemcpyAsync(hb + (it0 & 1) * SOLVE_RB, ws.ctl, 256 + I->n, cudaMemcpyDeviceToHost, st));
             TRY(cudaEventRecord(rb[it0 & 1], st));
+            long long pending = it0;  // the last iteration launched, with its read-back
             for (long long it = it0 + 1;; ++it) {
-                if ((rc = launch_iter(pool_of(it))) != FSP_OK) goto out;
-                TRY(cudaMemcpyAsync(hb + (it & 1) * SOLVE_RB, ws.ctl, 256 + I->n, cudaMemcpyDeviceToHost, st));
-                TRY(cudaEventRecord(rb[it & 1], st));
+                // an iteration at or past the iteration cap would do nothing: not launched
+                if (!(o.max_iterations > 0 && it >= o.max_iterations)) {
+                    if ((rc = launch_iter(pool_of(it))) != FSP_OK) goto out;
+                    if (timed) TRY(cudaEventRecord(ev1, st));
+                    TRY(cudaMemcpyAsync(hb + (it & 1) * SOLVE_RB, ws.ctl, 256 + I->n, cudaMemcpyDeviceToHost, st));
+                    TRY(cudaEventRecord(rb[it & 1], st));
+                    pending = it;
+                }
                 TRY(cudaEventSynchronize(rb[(it - 1) & 1]));
-                // the state after `it` iterations; iteration it + 1, launched
-                // ahead, does nothing if the search stops here, so this slot
+                // the state after `it` iterations; iteration it + 1, if launched
+                // ahead, does nothing when the search stops here, so this slot
                 // (its incumbent included) is the final state
                 last = hb + ((it - 1) & 1) * SOLVE_RB;
                 memcpy(&h, last, sizeof h);
@@ -1205,6 +1212,9 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 if (o.node_budget > 0 && h.cnt[0] >= o.node_budget) { rc = FSP_INCOMPLETE; break; }
                 if (o.max_iterations > 0 && it >= o.max_iterations) { rc = FSP_INCOMPLETE; break; }
             }
+            // the last read-back follows everything launched and the last ev1
+            TRY(cudaEventSynchronize(rb[pending & 1]));
+            idle = true;
         }
     }
     if (!idle) {  // after a read-back the stream is already idle and ev1 recorded before it

@@ -274,6 +274,7 @@ def test_large_start_stack_matches_oracle(F):
     got = F.fsp_solve(inst, ub0=ub, pool_size=8192, init_nodes=torch.from_numpy(rec).cuda(), max_iterations=2,
                       trace_cap=4)
     same(got, ref)
+    assert got["iterations"] == 2 and got["time_ms"] > 0  # launched ahead, none past the cap
     bad = rec.copy()
     bad[600001, 0] = 20
     with pytest.raises(F.FspError) as e:
