@@ -327,6 +327,8 @@ def fsp_solve_workspace_bytes(inst: Instance, **kw) -> int:
 
 
 STATS = ("nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iterations", "incumbent_updates")
+_RESULT_FIELDS = STATS + ("time_ms", "select_ms", "bound_ms", "compact_ms", "infer_ms", "tuned_pool", "tuned_warps",
+                          "early_pruned")
 
 
 def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,
@@ -353,22 +355,19 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     elif workspace.numel() < nbytes:
         raise ValueError(f"workspace needs {nbytes} bytes")
     o.workspace = workspace.data_ptr()
-    perm = np.full(inst.n, -1, np.int32)
+    perm = np.empty(inst.n, np.int32)
+    perm.fill(-1)
     cmax = ctypes.c_int32(0)
     st = fsp_stats()
     rc = _check(load().fsp_solve(inst.handle, int(ub0), ctypes.byref(cmax), perm.ctypes.data, ctypes.byref(st),
                                  ctypes.byref(o)))
-    res = {k: int(getattr(st, k)) for k in STATS}
-    for k in ("time_ms", "select_ms", "bound_ms", "compact_ms", "infer_ms"):
-        res[k] = float(getattr(st, k))
-    res["stack_left"] = int(out_count.value)
+    # ctypes returns the struct's integer and floating fields as Python ints and floats
+    res = {k: getattr(st, k) for k in _RESULT_FIELDS}
+    res["stack_left"] = out_count.value
     res["status"] = rc
-    res["cmax"] = int(cmax.value)
+    res["cmax"] = cmax.value
     res["perm"] = perm if perm[0] >= 0 else None
-    res["tuned_pool"] = int(st.tuned_pool)
-    res["tuned_warps"] = int(st.tuned_warps)
-    res["early_pruned"] = int(st.early_pruned)
-    res["logged"] = int(o._log_count.value)
+    res["logged"] = o._log_count.value
     if trace is not None:
         res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
     if sched_out is not None:
