@@ -280,3 +280,24 @@ def test_large_start_stack_matches_oracle(F):
     with pytest.raises(F.FspError) as e:
         F.fsp_solve(inst, ub0=ub, pool_size=8192, init_nodes=bad, max_iterations=2)
     assert e.value.code == F.ERR_ARG
+
+
+def test_bench_step_matches_oracle(F):
+    """The benchmark step at its full size, in the configuration bench.py
+    times: one iteration with a pool of 2^18 children from the 248,115-record
+    20 x 20 seed-1 frontier held on the device (read in place), UB = makespan
+    of the seed's random permutation, phase timing on.  Counters, UB,
+    incumbent and the whole stack left equal the oracle's."""
+    import torch
+    n, pool = 20, 2**18
+    p, ub_perm, rec = frontier_20x20(2**18)
+    ub = oracle.makespan(p, ub_perm)
+    ref = oracle.solve(p, ub0=ub, pool=pool, init_nodes=rec, max_iterations=1, trace_cap=1, export_stack=True)
+    inst = F.fsp_create_instance(p)
+    out = torch.zeros((len(rec) + pool, inst.stride), dtype=torch.uint8, device="cuda")
+    got = F.fsp_solve(inst, ub0=ub, pool_size=pool, init_nodes=torch.from_numpy(rec).cuda(), max_iterations=1,
+                      trace_cap=1, out_nodes=out, profile=True)
+    same(got, ref)
+    k = got["stack_left"]
+    assert k == ref["stack_left"]
+    assert canon(out[:k].cpu().numpy(), n) == canon(ref["stack"], n)
