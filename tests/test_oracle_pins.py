@@ -367,6 +367,23 @@ def test_neh_hand_worked():
     assert list(perm) == [1, 2, 0] and c == 12
 
 
+def test_neh_hand_worked_order_and_ties():
+    """Decreasing total time fixes the insertion order, and equal partial
+    makespans go to the earliest position (worked by hand, two machines:
+    C1 = running sum of a, C2 = max(C2, C1) + b)."""
+    # totals: job0 = 6, job1 = 9, job2 = 2 -> insertion order 1, 0, 2
+    # [1] -> insert 0: [0,1] = 12, [1,0] = 12 -> tie, earliest: [0,1]
+    # insert 2: [2,0,1] = 13, [0,2,1] = 13, [0,1,2] = 13 -> earliest: [2,0,1]
+    # (increasing totals would give [1,0,2]; latest ties would give [1,0,2])
+    p = np.array([[3, 3], [4, 5], [1, 1]], np.int32)
+    c, perm = oracle.neh(p)
+    assert list(perm) == [2, 0, 1] and c == 13
+    # two identical jobs: order 0, 1 (equal totals, smaller index first); both
+    # positions give 3, so job 1 goes in front
+    c, perm = oracle.neh(np.array([[1, 1], [1, 1]], np.int32))
+    assert list(perm) == [1, 0] and c == 3
+
+
 # --------------------------------------------------------- golden files ---
 def test_golden_files_reproduce():
     """tests/golden/*.json were written by tests/golden/make_golden.py from the
