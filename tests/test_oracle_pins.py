@@ -483,4 +483,27 @@ def test_feature_label_is_the_pair_that_gives_the_bound(n, m, seed):
         assert pv[y] == lb >= lb1 and y == int(np.flatnonzero(pv == pv.max())[0])
         assert x.dtype == np.float32 and x.shape == (2 * m + 1,)
         assert np.array_equal(x[:m], (oracle.release_times(p, perm, d).astype(np.float32) / T))
+        rest = sorted(set(range(n)) - set(int(j) for j in perm[:d]))  # the remaining jobs, by definition
+        S = np.array([sum(int(p[j, k]) for j in rest) for k in range(m)], np.float32)
+        assert np.array_equal(x[m:2 * m], S / T)
         assert x[2 * m] == np.float32(d) / np.float32(n)
+
+
+def test_mlp_oracle_forward_and_loss_hand_worked():
+    """A 2 -> 2 -> 2 -> 2 network with small integer weights (every value exact
+    in bf16), worked by hand: Z1 = x W1 + b1 = (1, -1), H1 = (1, 0);
+    Z2 = H1 W2 + b2 = (2, 2) = H2; scores = H2 W3 + b3 = (3, 2).  Cross-entropy:
+    label 0 gives log(1 + e^-1), label 1 gives log(1 + e)."""
+    from oracle import mlp as om
+    params = {"W1": np.array([[1.0, 0.0], [0.0, 1.0]]), "b1": np.array([0.0, -3.0]),
+              "W2": np.array([[2.0, 1.0], [5.0, 5.0]]), "b2": np.array([0.0, 1.0]),
+              "W3": np.array([[1.0, 0.0], [0.0, 1.0]]), "b3": np.array([1.0, 0.0])}
+    X = np.array([[1.0, 2.0]])
+    a = om.forward(params, X)
+    assert np.array_equal(a["H1"], [[1.0, 0.0]]) and np.array_equal(a["H2"], [[2.0, 2.0]])
+    assert np.array_equal(a["L"], [[3.0, 2.0]])
+    assert abs(om.loss(params, X, np.array([0])) - np.log1p(np.exp(-1.0))) < 1e-12
+    assert abs(om.loss(params, X, np.array([1])) - np.log1p(np.e)) < 1e-12
+    X2 = np.vstack([X, X])
+    want = (np.log1p(np.exp(-1.0)) + np.log1p(np.e)) / 2
+    assert abs(om.loss(params, X2, np.array([0, 1])) - want) < 1e-12
