@@ -272,6 +272,19 @@ int64_t fsp_tune_simulate(int64_t nodes_per_cta, int sms, int64_t max_pool,
                           double (*score)(int64_t pool, void *user), void *user, int64_t *pools_out,
                           int64_t cap, int64_t *best_out);
 
+/* The block-shape tuner of fsp_solve (pool_size = 0, after the pool tuner
+ * settles; the shape the paper's tuner also varies, Sec. III) run against a
+ * score function: candidate shapes 0..ncand-1 (the family kernel's warps per
+ * CTA, fewest first), one iteration per step.  It starts from the last
+ * candidate, discards one warm-up iteration, then gives every candidate in
+ * turn (last, 0, 1, ...) `window` iterations, adding score(cand, user) nodes
+ * per iteration, and keeps the highest nodes per iteration (ties: the one
+ * tried first).  cands_out (host, up to cap entries) receives the candidate
+ * of each iteration.  Returns the number of iterations and the kept
+ * candidate in *best_out (may be NULL), or FSP_ERR_ARG.  Pure host code. */
+int64_t fsp_block_tune_simulate(int ncand, int64_t window, double (*score)(int64_t cand, void *user), void *user,
+                                int64_t *cands_out, int64_t cap, int64_t *best_out);
+
 /* ---------------------------------------------------------------------
  * Learned pair ordering (not in the paper; see fsp_options.order).  A small MLP scores the m(m-1)/2
  * machine pairs of a node from its features so that the pair most likely to

@@ -15,6 +15,7 @@
 //   K3a       per block: survivors (non-leaf, bound < new UB) and leaves.
 //   K3b       stable compaction: survivors pushed in reverse pool order so
 //             the first survivor is on top; counters, trace, incumbent.
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -1355,6 +1356,30 @@ extern "C" int fsp_solve_noalloc(fsp_instance *I, int32_t ub0, int32_t *cmax, in
 }
 
 // The tuner's decisions against a caller-supplied score (no GPU involved).
+extern "C" int64_t fsp_block_tune_simulate(int ncand, int64_t window, double (*score)(int64_t cand, void *user),
+                                           void *user, int64_t *cands_out, int64_t cap, int64_t *best_out)
+{
+    if (ncand < 1 || window < 1 || !score || (cap > 0 && !cands_out)) {
+        fsp_set_error("fsp_block_tune_simulate: invalid argument");
+        return FSP_ERR_ARG;
+    }
+    BlockTuner b;
+    b.start(ncand, window);
+    long long bounded = 0;
+    double now = 0.0;
+    int64_t k = 0;
+    while (!b.settled && k < 4096) {  // one iteration per step: it runs with shape b.cur
+        const int c = b.cur;
+        if (k < cap) cands_out[k] = c;
+        ++k;
+        now += 1.0;
+        bounded += llround(score(c, user));
+        b.observe(bounded, now);
+    }
+    if (best_out) *best_out = b.cur;
+    return k;
+}
+
 extern "C" int64_t fsp_tune_simulate(int64_t nodes_per_cta, int sms, int64_t max_pool,
                                      double (*score)(int64_t pool, void *user), void *user, int64_t *pools_out,
                                      int64_t cap, int64_t *best_out)

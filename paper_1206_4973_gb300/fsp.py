@@ -25,7 +25,8 @@ _NAMES = {ERR_ARG: "FSP_ERR_ARG", ERR_CUDA: "FSP_ERR_CUDA", ERR_OOM: "FSP_ERR_OO
 # Every symbol include/fsp.h declares.
 EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp_destroy_instance",
            "fsp_instance_tables", "fsp_bound_pool", "fsp_check_status", "fsp_solve_workspace_bytes",
-           "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_node_features",
+           "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_block_tune_simulate",
+           "fsp_node_features",
            "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
            "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
@@ -102,6 +103,8 @@ def load(path: str | None = None):
         "fsp_neh": (ctypes.c_int, [vp, i32p, i32p]),
         "fsp_tune_simulate": (i64, [i64, ctypes.c_int, i64, SCORE_FN, vp, ctypes.POINTER(ctypes.c_int64), i64,
                                     ctypes.POINTER(ctypes.c_int64)]),
+        "fsp_block_tune_simulate": (i64, [ctypes.c_int, i64, SCORE_FN, vp, ctypes.POINTER(ctypes.c_int64), i64,
+                                          ctypes.POINTER(ctypes.c_int64)]),
         "fsp_node_features": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
         "fsp_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                                           ctypes.POINTER(vp)]),
@@ -245,6 +248,18 @@ def fsp_tune_simulate(nodes_per_cta: int, sms: int, max_pool: int, score):
     k = _check(int(load().fsp_tune_simulate(int(nodes_per_cta), int(sms), int(max_pool), cb, None,
                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 64,
                                             ctypes.byref(best))))
+    return out[:k].tolist(), int(best.value)
+
+
+def fsp_block_tune_simulate(ncand: int, window: int, score):
+    """Run the block-shape tuner against score(cand) -> nodes per iteration;
+    returns (candidate of every iteration, kept candidate)."""
+    cb = SCORE_FN(lambda cand, _u: float(score(int(cand))))
+    out = np.zeros(4096, np.int64)
+    best = ctypes.c_int64(0)
+    k = _check(int(load().fsp_block_tune_simulate(int(ncand), int(window), cb, None,
+                                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 4096,
+                                                  ctypes.byref(best))))
     return out[:k].tolist(), int(best.value)
 
 

@@ -1,5 +1,6 @@
 """Host logic of the pool-size tuner (Sec. III, Algorithm 1 restated on
-measured throughput), driven by synthetic throughput curves: no GPU."""
+measured throughput) and of the block-shape tuner that follows it, driven by
+synthetic throughput curves: no GPU."""
 import pytest
 
 from paper_1206_4973_gb300 import build as fsp_build
@@ -45,3 +46,25 @@ def test_stops_doubling_as_soon_as_the_score_drops():
 def test_rejects_bad_arguments():
     with pytest.raises(fsp.FspError):
         fsp.fsp_tune_simulate(0, SMS, MAXP, lambda p: 1.0)
+
+
+# ------------------------------------------------------- block-shape tuner ---
+def test_block_tuner_tries_every_shape_for_a_window_and_keeps_the_fastest():
+    scores = [5.0, 9.0, 7.0, 3.0]  # nodes per iteration of shapes 0..3
+    cands, best = fsp.fsp_block_tune_simulate(4, 2, lambda c: scores[c])
+    # one warm-up iteration on the last shape, then two iterations per shape: 3, 0, 1, 2
+    assert cands == [3, 3, 3, 0, 0, 1, 1, 2, 2]
+    assert best == 1
+
+
+def test_block_tuner_ties_keep_the_first_tried_and_one_shape_needs_no_trial():
+    cands, best = fsp.fsp_block_tune_simulate(3, 1, lambda c: 4.0)
+    assert cands == [2, 2, 0, 1] and best == 2
+    assert fsp.fsp_block_tune_simulate(1, 8, lambda c: 1.0) == ([], 0)
+
+
+def test_block_tuner_rejects_bad_arguments():
+    with pytest.raises(fsp.FspError):
+        fsp.fsp_block_tune_simulate(0, 8, lambda c: 1.0)
+    with pytest.raises(fsp.FspError):
+        fsp.fsp_block_tune_simulate(4, 0, lambda c: 1.0)
