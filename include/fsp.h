@@ -237,13 +237,18 @@ int fsp_solve(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp
  * arguments, options and results, but its scratch is a device array of
  * FSP_NOALLOC_SCRATCH_BYTES that the library defines at file scope; every
  * device that loads the library holds that array until the process exits.
- *   - It allocates nothing (no cudaMalloc, cudaFree, CUDA events or other
- *     allocating call) and therefore reports time_ms and the phase times as
- *     0; opt->profile has no effect.  opt->workspace must be NULL; the
- *     learned order and node logging are refused (FSP_ERR_ARG).
- *   - The instance's device must be current.  The first call on a device
- *     looks up the array's device address (cudaGetSymbolAddress) and keeps
- *     it; make that first call before any stream capture on that device.
+ *   - It allocates nothing (no cudaMalloc, cudaFree, cudaMallocHost, CUDA
+ *     event or other allocating call), from the first call on a newly
+ *     created instance on: its one pinned read-back block and two read-back
+ *     events are reserved by fsp_create_instance for this entry point alone
+ *     (fsp_instance_host_objects counts what an instance has created).  It
+ *     therefore reports time_ms and the phase times as 0; opt->profile has
+ *     no effect.  opt->workspace must be NULL; the learned order and node
+ *     logging are refused (FSP_ERR_ARG).
+ *   - The instance's device must be current.  Every call looks up the
+ *     array's device address (cudaGetSymbolAddress) with that device
+ *     current; the first call on a device also loads the library's device
+ *     code there, so make it before any stream capture on that device.
  *   - A search whose scratch (fsp_solve_workspace_bytes) exceeds
  *     FSP_NOALLOC_SCRATCH_BYTES is rejected with FSP_ERR_CAPACITY and a
  *     message; nothing runs.
@@ -253,6 +258,14 @@ int fsp_solve(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp
  *     Serialise them. */
 int fsp_solve_noalloc(fsp_instance *inst, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
                       const fsp_options *opt);
+
+/* Host-side CUDA objects an instance has created so far: pinned read-back
+ * blocks (cudaMallocHost) and CUDA events, counting the block and the two
+ * events fsp_create_instance reserves for fsp_solve_noalloc.  Either pointer
+ * (host) may be NULL.  A diagnostic with no counterpart in the paper: a
+ * caller checks with it that a call created nothing.  Errors: FSP_ERR_ARG
+ * (NULL inst). */
+int fsp_instance_host_objects(const fsp_instance *inst, int64_t *pinned_blocks, int64_t *events);
 
 /* NEH insertion heuristic on the device (an initial UB; the paper starts
  * from a given UB and has no counterpart): jobs by decreasing total time

@@ -169,6 +169,10 @@ extern "C" int fsp_bound_pool(fsp_instance *I, const uint8_t *nodes, int64_t cou
         fsp_set_error("fsp_bound_pool: nodes must be 16-byte aligned");
         return FSP_ERR_ARG;
     }
+    if (pool16_eligible(I) && !getenv("FSP_BOUND_V1") && !getenv("FSP_BOUND_V2")) {
+        const char *w = getenv("FSP_POOL16_WARPS");
+        return pool16_bound(I, nodes, count, lb_out, (cudaStream_t)stream, w ? atoi(w) : 0);
+    }
     BoundShape s;
     int rc = fsp_bound_shape(I, &s);
     if (rc != FSP_OK) return rc;

@@ -33,3 +33,9 @@ struct BoundShape {
 
 // Pick the kernel shape and CTA size whose shared memory fits the device.
 int fsp_bound_shape(const fsp_instance *I, BoundShape *s);
+
+// Packed kernel (fsp_pool16.cu): two nodes per register, one warp per 32
+// nodes; for n <= 31, m in {5, 10, 20} and (n + m) * max p <= 16383.
+int pool16_eligible(const fsp_instance *I);
+int pool16_bound(fsp_instance *I, const uint8_t *nodes, long long count, int32_t *lb_out, cudaStream_t st,
+                 int warps);

@@ -37,6 +37,7 @@ struct fsp_instance {
     int sm_count;
     int smem_optin;  // max dynamic shared memory per block
     long long total; // sum of all processing times
+    int pmax;        // largest processing time
     int32_t *d_p;    // [n][m] processing times
     int32_t *d_q;    // [n][m] tails: sum of p[j][h] for h > k
     int32_t *d_lag;  // [P][n]
@@ -45,6 +46,7 @@ struct fsp_instance {
     int2 *d_we;        // [n][P] position-major {w, e}: entry at position i of every pair
     uint8_t *d_rank;   // [P][n] position of job j in pair kl's order
     int *d_status;     // error flag of malformed records
+    uint8_t *d_p16;    // image of the packed bounding kernel (fsp_pool16.cu), or NULL
     int var;           // bound variant (FSP_BOUND_*)
     struct FspHostCache *cache;  // events and kernel attributes reused across calls
 };
@@ -62,6 +64,9 @@ int fsp_blocks_per_sm(fsp_instance *I, const void *kernel, int block, size_t sme
 #define FSP_PINNED_BYTES 1024
 int fsp_pinned_take(fsp_instance *I, void **p);
 void fsp_pinned_give(fsp_instance *I, void *p);
+// The pinned block and the two events an instance reserves at creation for
+// fsp_solve_noalloc (never handed to other calls).
+void fsp_noalloc_reserved(fsp_instance *I, void **pin, cudaEvent_t *ev);
 // The address at which kernels on the current device read p in place: p for
 // memory of this device, the mapped address of pinned host memory (read over
 // the host link), nullptr for anything else (pageable or managed memory,
@@ -75,6 +80,7 @@ struct DevInst {
     const FspEntry *ent;
     const int2 *we;
     const uint8_t *rank;
+    const uint8_t *order;  // [P][n] job at each position of the pair's Johnson order
     int *status;
     int var;  // bound variant (FSP_BOUND_*)
 };
@@ -84,10 +90,14 @@ static inline DevInst dev_view(const fsp_instance *I)
     DevInst d;
     d.n = I->n; d.m = I->m; d.P = I->P; d.stride = I->stride; d.mp = I->mp;
     d.p = I->d_p; d.q = I->d_q; d.ent = I->d_ent; d.status = I->d_status;
-    d.we = I->d_we; d.rank = I->d_rank;
+    d.we = I->d_we; d.rank = I->d_rank; d.order = I->d_order;
     d.var = I->var;
     return d;
 }
+
+// Image of the packed bounding kernel, built at creation when it applies
+// (fsp_pool16.cu).
+int pool16_build(fsp_instance *I);
 
 // --- host helpers (fsp_instance.cu) ---
 void fsp_set_error(const char *fmt, ...);

@@ -18,6 +18,10 @@ struct FspHostCache {
     std::mutex mu;
     std::vector<cudaEvent_t> events;
     std::vector<void *> pinned;
+    long long events_made = 0, pinned_made = 0;  // created by this instance so far
+    // reserved at creation for the search that allocates nothing (fsp_solve_noalloc)
+    void *rsv_pin = nullptr;
+    cudaEvent_t rsv_ev[2] = {nullptr, nullptr};
     std::unordered_map<const void *, size_t> smem;
     struct OccKey {
         const void *k;
@@ -45,6 +49,8 @@ int fsp_event_take(fsp_instance *I, cudaEvent_t *ev)
         }
     }
     FSP_CUDA(cudaEventCreate(ev));
+    std::lock_guard<std::mutex> g(I->cache->mu);
+    ++I->cache->events_made;
     return FSP_OK;
 }
 
@@ -66,6 +72,24 @@ int fsp_pinned_take(fsp_instance *I, void **p)
         }
     }
     FSP_CUDA(cudaMallocHost(p, FSP_PINNED_BYTES));
+    std::lock_guard<std::mutex> g(I->cache->mu);
+    ++I->cache->pinned_made;
+    return FSP_OK;
+}
+
+void fsp_noalloc_reserved(fsp_instance *I, void **pin, cudaEvent_t *ev)
+{
+    *pin = I->cache->rsv_pin;
+    ev[0] = I->cache->rsv_ev[0];
+    ev[1] = I->cache->rsv_ev[1];
+}
+
+extern "C" int fsp_instance_host_objects(const fsp_instance *I, int64_t *pinned_blocks, int64_t *events)
+{
+    if (!I) { fsp_set_error("fsp_instance_host_objects: inst is NULL"); return FSP_ERR_ARG; }
+    std::lock_guard<std::mutex> g(I->cache->mu);
+    if (pinned_blocks) *pinned_blocks = I->cache->pinned_made;
+    if (events) *events = I->cache->events_made;
     return FSP_OK;
 }
 
@@ -225,9 +249,13 @@ static void free_instance(fsp_instance *I)
     cudaFree(I->d_we);
     cudaFree(I->d_rank);
     cudaFree(I->d_status);
+    cudaFree(I->d_p16);
     if (I->cache) {
         for (cudaEvent_t ev : I->cache->events) cudaEventDestroy(ev);
         for (void *p : I->cache->pinned) cudaFreeHost(p);
+        for (cudaEvent_t ev : I->cache->rsv_ev)
+            if (ev) cudaEventDestroy(ev);
+        if (I->cache->rsv_pin) cudaFreeHost(I->cache->rsv_pin);
         delete I->cache;
     }
     free(I);
@@ -255,7 +283,10 @@ extern "C" int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance 
     I->P = m * (m - 1) / 2;
     I->stride = fsp_node_stride(n);
     I->mp = (m % 2 == 0) ? m + 1 : m;
-    for (long i = 0; i < (long)n * m; ++i) I->total += p[i];
+    for (long i = 0; i < (long)n * m; ++i) {
+        I->total += p[i];
+        if (p[i] > I->pmax) I->pmax = p[i];
+    }
     int rc = FSP_OK;
     cudaError_t e;
 #define TRY(call)                                              \
@@ -274,12 +305,19 @@ extern "C" int fsp_create_instance(int n, int m, const int32_t *p, fsp_instance 
     TRY(cudaMalloc(&I->d_we, sizeof(int2) * (size_t)I->P * n));
     TRY(cudaMalloc(&I->d_rank, (size_t)I->P * n));
     TRY(cudaMalloc(&I->d_status, sizeof(int)));
+    // the read-back block and events of fsp_solve_noalloc, which must not create them
+    TRY(cudaMallocHost(&I->cache->rsv_pin, FSP_PINNED_BYTES));
+    TRY(cudaEventCreateWithFlags(&I->cache->rsv_ev[0], cudaEventDisableTiming));
+    TRY(cudaEventCreateWithFlags(&I->cache->rsv_ev[1], cudaEventDisableTiming));
+    I->cache->pinned_made = 1;
+    I->cache->events_made = 2;
     TRY(cudaMemcpy(I->d_p, p, sizeof(int32_t) * n * m, cudaMemcpyHostToDevice));
     TRY(cudaMemset(I->d_status, 0, sizeof(int)));
     k_tails<<<(n * m + 255) / 256, 256>>>(n, m, I->d_p, I->d_q);
     TRY(cudaGetLastError());
     k_pair_tables<<<I->P, 256>>>(n, m, I->P, I->d_p, I->d_lag, I->d_order, I->d_ent, I->d_we, I->d_rank);
     TRY(cudaGetLastError());
+    if ((rc = pool16_build(I)) != FSP_OK) goto fail;
     TRY(cudaDeviceSynchronize());
 #undef TRY
     *out = I;

@@ -939,8 +939,11 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
 }
 
 // One search with its scratch at `base` (P->L.bytes bytes, 256-byte aligned).
-// timed: CUDA events give time_ms and, with opt->profile, the phase times;
-// without it the search creates no event and reports zero times.
+// timed: CUDA events give time_ms and, with opt->profile, the phase times,
+// and the read-back block and events come from the instance's cache (created
+// when the cache is empty); without it the search reports zero times and
+// uses only the block and events the instance reserved at creation, so it
+// creates nothing.
 static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm, fsp_stats *stats,
                      const SolvePlan *P, uint8_t *base, bool timed)
 {
@@ -1001,7 +1004,11 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     if (prof)
         for (int i = 0; i < 5; ++i)
             if ((rc = fsp_event_take(I, &pe[i])) != FSP_OK) goto out;
-    if ((rc = fsp_pinned_take(I, &pin)) != FSP_OK) goto out;
+    if (timed) {
+        if ((rc = fsp_pinned_take(I, &pin)) != FSP_OK) goto out;
+    } else {
+        fsp_noalloc_reserved(I, &pin, rb);
+    }
     if (timed) TRY(cudaEventRecord(ev0, st));
     if (o.pool_size == 0) tuner.start(per_cta, I->sm_count, tuner_max_pool(I), o.tune_window);
     if (o.pool_size == 0 && P->bf) btuner.start(P->nfam, o.tune_window);
@@ -1179,7 +1186,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if ((rc = launch_iter(pool)) != FSP_OK) goto out;
         }
         if (it0 >= 0) {
-            if ((rc = fsp_event_take(I, &rb[0])) != FSP_OK || (rc = fsp_event_take(I, &rb[1])) != FSP_OK) goto out;
+            if (timed && ((rc = fsp_event_take(I, &rb[0])) != FSP_OK || (rc = fsp_event_take(I, &rb[1])) != FSP_OK))
+                goto out;
             uint8_t *hb = reinterpret_cast<uint8_t *>(pin);
             if ((rc = launch_iter(pool_of(it0))) != FSP_OK) goto out;
             if (timed) TRY(cudaEventRecord(ev1, st));  // moved to each later read-back
@@ -1263,9 +1271,11 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
 out:
     fsp_event_give(I, ev0);
     fsp_event_give(I, ev1);
-    fsp_event_give(I, rb[0]);
-    fsp_event_give(I, rb[1]);
-    fsp_pinned_give(I, pin);
+    if (timed) {  // the reserved block and events stay with the instance
+        fsp_event_give(I, rb[0]);
+        fsp_event_give(I, rb[1]);
+        fsp_pinned_give(I, pin);
+    }
     for (int i = 0; i < 5; ++i) fsp_event_give(I, pe[i]);
     return rc;
 }
@@ -1297,30 +1307,20 @@ extern "C" int fsp_solve(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *p
 // FSP_NOALLOC_SCRATCH_BYTES on every device that loads this library, until
 // the process exits.
 // ---------------------------------------------------------------------------
-#define FSP_NOALLOC_MAX_DEVICES 64
-
 static __device__ __align__(256) uint8_t g_noalloc_scratch[FSP_NOALLOC_SCRATCH_BYTES];
-
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[FSP_NOALLOC_MAX_DEVICES];
 
 // Device address of the scratch array on the current device.  In host code
 // the array's name only stands for the symbol; the usable address comes from
-// cudaGetSymbolAddress, looked up once per device with that device current.
-static int noalloc_scratch(int dev, uint8_t **out)
+// cudaGetSymbolAddress with the device current.  It is looked up on every
+// call: a cached address would be stale after the device's context is torn
+// down and made again (cudaDeviceReset), and the lookup allocates nothing
+// once this library's device code is loaded on the device (the first call).
+static int noalloc_scratch(uint8_t **out)
 {
-    if (dev < 0 || dev >= FSP_NOALLOC_MAX_DEVICES) {
-        fsp_set_error("fsp_solve_noalloc: device %d out of range", dev);
-        return FSP_ERR_ARG;
-    }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return fsp_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_noalloc_addr[dev] = p;
-    }
-    *out = (uint8_t *)g_noalloc_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fsp_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    *out = (uint8_t *)p;
     return FSP_OK;
 }
 
@@ -1351,7 +1351,7 @@ extern "C" int fsp_solve_noalloc(fsp_instance *I, int32_t ub0, int32_t *cmax, in
         return FSP_ERR_ARG;
     }
     uint8_t *base = nullptr;
-    if ((rc = noalloc_scratch(dev, &base)) != FSP_OK) return rc;
+    if ((rc = noalloc_scratch(&base)) != FSP_OK) return rc;
     return solve_run(I, ub0, cmax, perm, stats, &P, base, false);
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp
            "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
            "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
-           "fsp_batch_tune_pools", "fsp_set_bound", "fsp_last_error")
+           "fsp_batch_tune_pools", "fsp_set_bound", "fsp_instance_host_objects", "fsp_last_error")
 BOUND_BASE, BOUND_HEADS = 0, 1
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -123,6 +123,8 @@ def load(path: str | None = None):
         "fsp_batch_results": (ctypes.c_int, [vp, vp, vp, vp]),
         "fsp_batch_tune_pools": (ctypes.c_int, [ctypes.c_int, vp, vp, i64, vp]),
         "fsp_set_bound": (ctypes.c_int, [vp, ctypes.c_int]),
+        "fsp_instance_host_objects": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64),
+                                                     ctypes.POINTER(ctypes.c_int64)]),
         "fsp_last_error": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -230,6 +232,13 @@ def _ptr(buf):
     if hasattr(buf, "data_ptr"):
         return buf.data_ptr()
     return np.asarray(buf).ctypes.data
+
+
+def fsp_instance_host_objects(inst: Instance):
+    """(pinned read-back blocks, CUDA events) the instance has created so far."""
+    pb, ev = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(load().fsp_instance_host_objects(inst.handle, ctypes.byref(pb), ctypes.byref(ev)))
+    return int(pb.value), int(ev.value)
 
 
 def fsp_neh(inst: Instance):

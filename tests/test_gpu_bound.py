@@ -129,17 +129,66 @@ def test_full_size_20x20_workload_sampled(F, count):
 
 
 @pytest.mark.parametrize("n,m,seed", [(20, 20, 1), (12, 5, 0), (33, 10, 21), (50, 20, 7), (15, 10, 22),
-                                      (47, 5, 23), (63, 20, 24), (31, 20, 25)])
-def test_v1_and_v2_kernels_agree_with_oracle(F, n, m, seed, monkeypatch):
-    """The shapes with a fast-path kernel, bounded by both kernel families."""
+                                      (47, 5, 23), (63, 20, 24), (31, 20, 25), (9, 5, 26), (16, 10, 27),
+                                      (31, 5, 28), (2, 5, 29)])
+def test_every_kernel_family_agrees_with_oracle(F, n, m, seed, monkeypatch):
+    """The shapes with a fast-path kernel, bounded by every kernel family:
+    the default (two nodes per register where eligible), the per-node
+    register kernel (FSP_BOUND_V2) and the generic one (FSP_BOUND_V1)."""
     import torch
     p = inputs.instance(n, m, seed)
     rec = edge_pool(n, 1500, seed + 77)
     want = oracle.bound_pool(p, rec)
     inst = F.fsp_create_instance(p)
     nodes = torch.from_numpy(rec).cuda()
-    v2 = F.fsp_bound_pool(inst, nodes).cpu().numpy()
+    got = {"default": F.fsp_bound_pool(inst, nodes).cpu().numpy()}
+    monkeypatch.setenv("FSP_BOUND_V2", "1")
+    got["v2"] = F.fsp_bound_pool(inst, nodes).cpu().numpy()
+    monkeypatch.delenv("FSP_BOUND_V2")
     monkeypatch.setenv("FSP_BOUND_V1", "1")
-    v1 = F.fsp_bound_pool(inst, nodes).cpu().numpy()
-    assert np.array_equal(v2, want)
-    assert np.array_equal(v1, want)
+    got["v1"] = F.fsp_bound_pool(inst, nodes).cpu().numpy()
+    for name, v in got.items():
+        assert np.array_equal(v, want), (name, np.nonzero(v != want)[0][:10])
+
+
+@pytest.mark.parametrize("warps", [1, 4, 8, 16])
+def test_packed_kernel_cta_shapes(F, warps, monkeypatch):
+    """The packed kernel gives the same bounds for every CTA shape, on a
+    ragged pool (not a multiple of 32 nodes) spanning many warps."""
+    import torch
+    n, m = 20, 20
+    p, _, rec = inputs.pool_workload(n, m, 1, 5003)
+    want = oracle.bound_pool(p, rec)
+    inst = F.fsp_create_instance(p)
+    monkeypatch.setenv("FSP_POOL16_WARPS", str(warps))
+    got = F.fsp_bound_pool(inst, torch.from_numpy(rec).cuda()).cpu().numpy()
+    assert np.array_equal(got, want)
+
+
+def test_packed_kernel_extreme_times(F):
+    """Instances at the edge of the packed kernel's 16-bit range
+    ((n + m) * max p <= 16383) and just past it (the 32-bit kernels take
+    over): processing times drawn near the largest allowed value."""
+    import torch
+    for n, m, pmax in ((20, 20, 409), (20, 20, 410), (31, 5, 455), (31, 5, 456), (12, 10, 744)):
+        rng = np.random.default_rng(n * 1000 + pmax)
+        p = rng.integers(max(1, pmax - 40), pmax + 1, size=(n, m)).astype(np.int32)
+        p[0, 0] = pmax
+        rec = edge_pool(n, 700, pmax)
+        want = oracle.bound_pool(p, rec)
+        inst = F.fsp_create_instance(p)
+        got = F.fsp_bound_pool(inst, torch.from_numpy(rec).cuda()).cpu().numpy()
+        F.fsp_check_status(inst)
+        assert np.array_equal(got, want), (n, m, pmax, np.nonzero(got != want)[0][:10])
+
+
+def test_full_2e18_pool_elementwise(F):
+    """The whole 2^18-node 20 x 20 bounding workload (seed 1), as the
+    benchmark launches it, against the oracle node by node."""
+    import torch
+    p, _, rec = inputs.pool_workload(20, 20, 1, 2**18)
+    inst = F.fsp_create_instance(p)
+    got = F.fsp_bound_pool(inst, torch.from_numpy(rec).cuda()).cpu().numpy()
+    F.fsp_check_status(inst)
+    want = oracle.bound_pool(p, rec)
+    assert np.array_equal(got, want), np.nonzero(got != want)[0][:10]
