@@ -39,9 +39,14 @@ METRIC = "subproblems bounded/s at 20x20 (plain vs learned pair order, bit-exact
 UNIT = "subproblems/s"
 L2_FLUSH_BYTES = 512 << 20
 SMS, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-# DRAM bytes (read + write) of one branch-and-bound launch of the step, from the ncu capture in
-# profiles/k_branch_family_20x20_2e18_full.md; None once that kernel has changed since the capture.
-BB_TRAFFIC_BYTES = 1083136
+# The ALU pipe (logic, min/max, the add-max instructions) retires 64 lanes per clock per SM: ncu
+# reports sm__inst_executed_pipe_alu.avg.peak_sustained = 0.5 warp instructions per cycle per
+# scheduler (4 schedulers x 16 lanes); the issue ceiling above is 4 x 32 lanes.
+ALU_LANES_PER_SM = 64
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of
+# `bench.py --profile-case` (dram__bytes_read.sum + dram__bytes_write.sum); None until a capture of
+# the current kernel is taken.
+BB_TRAFFIC_BYTES = None
 
 
 def work_ops(depth, n=N_JOBS, m=N_MACH):
@@ -423,9 +428,13 @@ def main():
     depths, n_children = children_depths(frontier, POOL)
     ops_per_step = int(work_ops(depths).sum())
 
+    # the step through the public API: a prepared fsp_solve (options, workspace and result
+    # buffers built once; every run() is one call into the library)
+    calls = {id(x): fsp.SolveCall(inst, ub0=ub, pool_size=POOL, init_nodes=x, max_iterations=1, workspace=ws,
+                                  profile=True) for x in (front_dev, front_host)}
+
     def step(init):
-        return fsp.fsp_solve(inst, ub0=ub, pool_size=POOL, init_nodes=init, max_iterations=1,
-                             workspace=ws, profile=True)
+        return calls[id(init)].run()
 
     if args.profile_case:
         r = step(front_dev)
@@ -506,11 +515,21 @@ def main():
         fsp.fsp_check_status(inst)
 
     achieved = ops_per_step / (statistics.mean(bound_ms) / 1e3)
+    alu_peak = SMS * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak_ops, "traffic": BB_TRAFFIC_BYTES,
                 "kernel": "k_branch_family (branching + bounding of the pool's children, one warp per parent)",
                 "ops_per_launch": ops_per_step, "children_per_launch": n_children,
-                "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz (issue ceiling)"}
+                "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz (issue ceiling)",
+                "alu_pipe": {"peak": alu_peak / 1e12, "frac": achieved / alu_peak,
+                             "basis": f"{SMS} SMs x {ALU_LANES_PER_SM} ALU-pipe lanes x {SM_MAX_MHZ:.0f} MHz"},
+                "work_equivalent": "achieved counts the full per-child bound (W ops); the kernels reach the same "
+                                   "integers with fewer instructions",
+                # fsp_bound_pool alone on the 20x20 bounding pools (arbitrary nodes, Sec. III Type 1)
+                "bound_pool": {k: {"ms": round(v["ms"], 4), "nodes_per_s": v["nodes_per_s"],
+                                   "frac": round(v["frac_of_int_peak"], 3),
+                                   "frac_alu_pipe": round(v["frac_of_int_peak"] * peak_ops / alu_peak, 3)}
+                               for k, v in bp.items()}}
 
     if rank == 0:
         line = {

@@ -94,8 +94,8 @@ typedef struct {
     int64_t pool_size;      /* children bounded per iteration (Sec. III pool); default 1024;
                                0 = tune it while searching (Sec. III, Algorithm 1): start at
                                (nodes per CTA) x (SM count), double every tune_window iterations
-                               while it improves the measured nodes bounded per second and stays
-                               within SMs x 2048, then refine around the best and keep it */
+                               while it stays within SMs x 2048, keeping the pool with the most
+                               nodes bounded per second, then refine around the best and keep it */
     int64_t node_budget;    /* stop (FSP_INCOMPLETE) before an iteration once this many
                                nodes are bounded; 0 = no limit */
     int64_t stack_capacity; /* node records in the device stack; 0 = init_count + n * (pool + n) */
@@ -277,8 +277,8 @@ int fsp_neh(fsp_instance *inst, int32_t *cmax, int32_t *perm);
 /* The pool-size tuner of fsp_solve (pool_size = 0; Sec. III, Algorithm 1)
  * run against a score function instead of measured throughput: trial k uses
  * pools_out[k] (host, up to cap entries) and receives score(pool, user).
- * Starts at nodes_per_cta x sms, doubles while the score improves and the
- * pool stays <= max_pool, then binary-searches around the best.  Returns the
+ * Starts at nodes_per_cta x sms, doubles while the pool stays <= max_pool
+ * (keeping the best score so far), then binary-searches around the best.  Returns the
  * number of trials (<= 64) and the best pool in *best_out (may be NULL), or
  * FSP_ERR_ARG.  Pure host code. */
 int64_t fsp_tune_simulate(int64_t nodes_per_cta, int sms, int64_t max_pool,

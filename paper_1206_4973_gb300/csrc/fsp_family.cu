@@ -216,12 +216,11 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_bound_pool_warp(DevIn
         // the pairs: forward scans over the remaining set
         int klc[NS];
         Mask pm[NS];
-        int32_t E[NS], M[NS];
+        int32_t M[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             klc[s] = min(lane + 32 * s, P - 1);
             pm[s] = 0;
-            E[s] = 0;
             M[s] = FSP_NEG;
         }
         for (int i = d; i < n; ++i) {
@@ -229,16 +228,14 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_bound_pool_warp(DevIn
 #pragma unroll
             for (int s = 0; s < NS; ++s) pm[s] |= (Mask)1 << V.rk8[klc[s] * V.rks8 + j];
         }
-        const int2 *wrow = V.we;
+        // each order from the back, one add-max per member: M <- max(M + e, w)
+        Mask bit = (Mask)1 << (n - 1);
 #pragma unroll 2
-        for (int pos = 0; pos < n; ++pos, wrow += P) {
+        for (int pos = n - 1; pos >= 0; --pos, bit >>= 1) {
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                const int2 v = wrow[klc[s]];
-                const bool b = pm[s] & 1u;
-                pm[s] >>= 1;
-                M[s] = __viaddmax_s32(E[s], b ? v.x : FSP_NEG, M[s]);
-                E[s] += b ? v.y : 0;
+                const int2 v = V.we[pos * P + klc[s]];
+                if (pm[s] & bit) M[s] = __viaddmax_s32(M[s], v.y, v.x);
             }
         }
 #pragma unroll

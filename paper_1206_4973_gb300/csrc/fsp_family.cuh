@@ -333,26 +333,32 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                     Mask pm = 0;
 #pragma unroll 4
                     for (int i = d; i < n; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
+                    // every lane at the same position (position-major rows and
+                    // the lane's own T column: no bank conflicts); a member
+                    // updates the running values, T is read at members only.
+                    // Forward: the prefix maximum before each position
                     int32_t E = 0, M = FSP_NEG;
-                    Mask pf = pm;
+                    Mask bit = 1;
 #pragma unroll 2
-                    for (int pos = 0; pos < n; ++pos) {
+                    for (int pos = 0; pos < n; ++pos, bit <<= 1) {
                         const int2 v = we_s[pos * P + kl];
-                        const bool b = pf & 1u;
-                        pf >>= 1;
                         T[pos * FAM_TS + lane] = M;
-                        M = __viaddmax_s32(E, b ? v.x : FSP_NEG, M);
-                        E += b ? v.y : 0;
+                        if (pm & bit) {
+                            M = __viaddmax_s32(E, v.x, M);
+                            E += v.y;
+                        }
                     }
+                    // backward: the suffix maximum after each position, less its e
                     int32_t R = E, Ms = FSP_NEG;
 #pragma unroll 2
                     for (int pos = n - 1; pos >= 0; --pos) {
                         const int2 v = we_s[pos * P + kl];
-                        const bool b = (pm >> pos) & 1u;
-                        int32_t *t = T + pos * FAM_TS + lane;
-                        *t = max(*t, Ms - v.y);
-                        R -= b ? v.y : 0;
-                        Ms = __viaddmax_s32(R, b ? v.x : FSP_NEG, Ms);
+                        int32_t *tp = T + pos * FAM_TS + lane;
+                        *tp = max(*tp, Ms - v.y);
+                        if ((pm >> pos) & 1u) {
+                            R -= v.y;
+                            Ms = __viaddmax_s32(R, v.x, Ms);
+                        }
                     }
                 }
                 __syncwarp();
@@ -384,14 +390,15 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
 #pragma unroll 4
                 for (int i = d; i < n; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
                 int32_t E = 0, M = FSP_NEG;
+                Mask bit = 1;
 #pragma unroll 2
-                for (int pos = 0; pos < n; ++pos) {
+                for (int pos = 0; pos < n; ++pos, bit <<= 1) {  // lanes in step: no bank conflicts
                     const int2 v = we_s[pos * P + kl];
-                    const bool b = pm & 1u;
-                    pm >>= 1;
                     T[pos * FAM_TS + lane] = M;
-                    M = __viaddmax_s32(E, b ? v.x : FSP_NEG, M);
-                    E += b ? v.y : 0;
+                    if (pm & bit) {
+                        M = __viaddmax_s32(E, v.x, M);
+                        E += v.y;
+                    }
                 }
             }
             __syncwarp();
@@ -454,12 +461,11 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
             {
                 int klc[NS];
                 Mask pm[NS];
-                int32_t E[NS], M[NS];
+                int32_t M[NS];
 #pragma unroll
                 for (int s = 0; s < NS; ++s) {
                     klc[s] = min(lane + 32 * s, P - 1);
                     pm[s] = 0;
-                    E[s] = 0;
                     M[s] = FSP_NEG;
                 }
 #pragma unroll 4
@@ -468,16 +474,17 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
 #pragma unroll
                     for (int s = 0; s < NS; ++s) pm[s] |= (Mask)1 << rk8[klc[s] * rks8 + j];
                 }
-                const int2 *wrow = we_s;
+                // M_U from the back of each order, one add-max per member:
+                // G <- max(G + e_i, w_i) gives max_i (E_{<i} + w_i) at the
+                // first; all lanes read the same position row (no bank conflicts)
+                Mask bit = (Mask)1 << (n - 1);
+                const int2 *wrow = we_s + (n - 1) * P;
 #pragma unroll 2
-                for (int pos = 0; pos < n; ++pos, wrow += P) {
+                for (int pos = n - 1; pos >= 0; --pos, wrow -= P, bit >>= 1) {
 #pragma unroll
                     for (int s = 0; s < NS; ++s) {
                         const int2 v = wrow[klc[s]];
-                        const bool b = pm[s] & 1u;
-                        pm[s] >>= 1;
-                        M[s] = __viaddmax_s32(E[s], b ? v.x : FSP_NEG, M[s]);
-                        E[s] += b ? v.y : 0;
+                        if (pm[s] & bit) M[s] = __viaddmax_s32(M[s], v.y, v.x);
                     }
                 }
 #pragma unroll

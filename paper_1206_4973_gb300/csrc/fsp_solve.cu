@@ -152,11 +152,9 @@ __device__ __forceinline__ int init_low(uint32_t x) { return __ffs((int)x) - 1; 
 __device__ __forceinline__ int init_low(unsigned long long x) { return __ffsll((long long)x) - 1; }
 
 template <int NV>
-__device__ __forceinline__ bool init_node_fast(const uint8_t *src, uint8_t *dst, int n, int d)
+__device__ __forceinline__ bool init_node_fast(FspRec<NV> &rec, bool same, uint8_t *dst, int n, int d)
 {
     typedef typename std::conditional<(NV <= 2), uint32_t, unsigned long long>::type M;
-    FspRec<NV> rec;
-    fsp_load_rec(rec, src);
     bool ok = d <= n - 2, sorted = true;
     M seen = 0, rem = 0;
     int prev = -1;
@@ -176,7 +174,7 @@ __device__ __forceinline__ bool init_node_fast(const uint8_t *src, uint8_t *dst,
     }
     if (!ok || init_popc(seen) != n) return false;
     if (sorted) {
-        if (src != dst) fsp_store_rec(rec, dst);
+        if (!same) fsp_store_rec(rec, dst);
         return true;
     }
 #pragma unroll
@@ -205,7 +203,21 @@ __global__ void __launch_bounds__(SOLVE_B) k_solve_init_nodes(SolveWs ws, const 
                                                               long long count, int ub0, int wide)
 {
     __shared__ long long red[SOLVE_B / 32];
+    // the block's records, copied with coalesced 16-byte loads (each warp
+    // instruction reads 512 contiguous bytes, which matters when src is pinned
+    // host memory read over the host link); a record stride of 16 (NV | 1)
+    // bytes keeps each thread's 16-byte reads of its own record conflict-free
+    constexpr int SS = 16 * (NV | 1);
+    __shared__ __align__(16) uint8_t recs[SOLVE_B * SS];
     const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
+    if (!wide) {
+        const long long first = (long long)blockIdx.x * SOLVE_B;
+        const long long nrec = count - first < SOLVE_B ? count - first : SOLVE_B;
+        const uint4 *g = reinterpret_cast<const uint4 *>(src + first * stride);
+        for (int c = threadIdx.x; c < nrec * NV; c += SOLVE_B)
+            *reinterpret_cast<uint4 *>(recs + (c / NV) * SS + (c % NV) * 16) = __ldg(g + c);
+        __syncthreads();
+    }
     if (t == 0) {
         SolveCtl c;
         memset(&c, 0, sizeof c);
@@ -218,9 +230,21 @@ __global__ void __launch_bounds__(SOLVE_B) k_solve_init_nodes(SolveWs ws, const 
     int d = 0;
     bool bad = false;
     if (t < count) {
-        d = src[t * stride + n];  // a byte load: no run-time index into the record's registers
         if (!wide) {  // records of n >= 64 jobs: k_solve_init_nodes_wide, on the stack
-            bad = !init_node_fast<NV>(src + t * stride, ws.stack + t * stride, n, d);
+            const uint8_t *mine = recs + threadIdx.x * SS;
+            d = mine[n];  // a byte read: no run-time index into the record's registers
+            FspRec<NV> rec;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const uint4 x = reinterpret_cast<const uint4 *>(mine)[v];
+                rec.w[4 * v + 0] = x.x;
+                rec.w[4 * v + 1] = x.y;
+                rec.w[4 * v + 2] = x.z;
+                rec.w[4 * v + 3] = x.w;
+            }
+            bad = !init_node_fast<NV>(rec, src == ws.stack, ws.stack + t * stride, n, d);
+        } else {
+            d = src[t * stride + n];
         }
     }
     const long long s = block_sum_ll(t < count ? n - d : 0, red);
@@ -782,7 +806,10 @@ struct PoolTuner {
         const long long tried = cur;
         if (eff > best_eff) { best_eff = eff; best = tried; }
         if (phase == 0) {
-            if (best == tried && tried * 2 <= max_pool) { cur = tried * 2; return; }
+            // Algorithm 1 doubles the blocks every nb_iterations while threads x
+            // blocks stays within the device's active threads, keeping the best
+            // pool so far (one slower trial does not end the doubling)
+            if (tried * 2 <= max_pool) { cur = tried * 2; return; }
             phase = 1;
             lo = round_unit(best / 2);
             hi = round_unit(best * 2);

@@ -400,6 +400,42 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     return res
 
 
+class SolveCall:
+    """A prepared fsp_solve: the options struct, the workspace (allocated here
+    when None) and the result buffers are built once, so a repeated call with
+    the same arguments costs only the call into the library.  run() returns
+    the dict fsp_solve returns (without trace and schedule)."""
+
+    def __init__(self, inst: Instance, ub0: int = UB_INF, workspace=None, **kw):
+        import torch
+        self.inst, self.ub0 = inst, int(ub0)
+        self.o, self._keep, _trace, self._out_count = _options(**kw)
+        nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(self.o))))
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        elif workspace.numel() < nbytes:
+            raise ValueError(f"workspace needs {nbytes} bytes")
+        self.workspace = workspace
+        self.o.workspace = workspace.data_ptr()
+        self.perm = np.empty(inst.n, np.int32)
+        self._cmax = ctypes.c_int32(0)
+        self._st = fsp_stats()
+        self._args = (inst.handle, self.ub0, ctypes.byref(self._cmax), self.perm.ctypes.data,
+                      ctypes.byref(self._st), ctypes.byref(self.o))
+        self._fn = load().fsp_solve
+
+    def run(self) -> dict:
+        self.perm.fill(-1)
+        rc = _check(self._fn(*self._args))
+        st = self._st
+        res = {k: getattr(st, k) for k in _RESULT_FIELDS}
+        res["stack_left"] = self._out_count.value
+        res["status"] = rc
+        res["cmax"] = self._cmax.value
+        res["perm"] = self.perm if self.perm[0] >= 0 else None
+        return res
+
+
 def fsp_solve_noalloc(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,
                       stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
                       init_nodes=None, init_count=None, max_iterations: int = 0, out_nodes=None):

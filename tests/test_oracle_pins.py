@@ -150,6 +150,24 @@ def test_johnson_orders_are_permutations_with_rule():
         assert o[: len(first)] == first
 
 
+def test_johnson_tie_break_hand_worked():
+    """Equal sort keys inside set A and inside set B go smaller job index
+    first, and a job with a == b belongs to set A (worked by hand).
+    Two machines: A = {a <= b} by increasing a: j1 (2), j0 (3), j2 (3),
+    j6 (4); B = {a > b} by decreasing b: j4 (5), j3 (2), j5 (2)."""
+    p = np.array([[3, 5], [2, 9], [3, 4], [7, 2], [6, 5], [8, 2], [4, 4]], np.int32)
+    _, lag, order = oracle.tables(p)
+    assert list(lag[0]) == [0] * 7
+    assert list(order[0]) == [1, 0, 2, 6, 4, 3, 5]
+    # Three machines, pair (0, 2) (index 1), lag = the time on machine 1:
+    # A by increasing a + lag: j2 (1+2=3), j0 (2+3=5), j1 (4+1=5), j5 (5+4=9);
+    # B by decreasing b + lag: j3 (1+2=3), j4 (2+1=3).
+    p = np.array([[2, 3, 9], [4, 1, 6], [1, 2, 7], [9, 2, 1], [8, 1, 2], [5, 4, 5]], np.int32)
+    _, lag, order = oracle.tables(p)
+    assert list(lag[1]) == [3, 1, 2, 2, 1, 4]
+    assert list(order[1]) == [2, 0, 1, 5, 3, 4]
+
+
 # ------------------------------------------------------------ the bound ---
 @pytest.mark.parametrize("n,m,seed", [(6, 3, 51), (7, 4, 52), (5, 6, 53), (7, 5, 54)])
 def test_bound_is_valid_and_exact_at_the_leaves(n, m, seed):

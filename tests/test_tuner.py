@@ -35,12 +35,29 @@ def test_refines_around_a_peaked_curve(peak):
     assert len(pools) <= 16
 
 
-def test_stops_doubling_as_soon_as_the_score_drops():
+def test_doubles_to_the_limit_even_when_the_score_drops():
+    """Algorithm 1 doubles until threads x blocks reaches the device limit and
+    keeps the best pool so far; only then does it search around the best."""
     start = UNIT * SMS
     pools, best = fsp.fsp_tune_simulate(UNIT, SMS, MAXP, lambda p: -float(p))
-    assert pools[:2] == [start, 2 * start]
-    assert 4 * start not in pools
+    assert pools[:4] == [start, 2 * start, 4 * start, 8 * start]
     assert best < start  # the refinement found smaller pools better
+    assert all(start // 2 <= q <= 2 * start for q in pools[4:])  # the search stays around the best
+
+
+def test_one_slower_trial_does_not_end_the_doubling():
+    """A score that dips once (a noisy measurement at the second pool) and
+    peaks at the fourth: the tuner keeps doubling past the dip and settles
+    near the peak."""
+    start = UNIT * SMS
+    peak = 8 * start
+    def score(p):
+        if p == 2 * start:
+            return 0.1  # one slow trial
+        return 1.0 / (1.0 + abs(p - peak) / peak)
+    pools, best = fsp.fsp_tune_simulate(UNIT, SMS, MAXP, score)
+    assert pools[:4] == [start, 2 * start, 4 * start, 8 * start]
+    assert best == peak
 
 
 def test_rejects_bad_arguments():
