@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-fno-strict-aliasing",
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-fno-strict-aliasing", "-fopenmp",
                         _SRC, "-o", tmp], check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -62,6 +62,11 @@ def _load():
                 "orc_makespan": (c_i32, [c_int, c_int, i32p, u8p, c_int]),
                 "orc_check_node": (c_int, [c_int, u8p, c_int]),
                 "orc_bound_pool": (c_int, [c_int, c_int, i32p, u8p, c_i64, c_int, c_int, i32p]),
+                "orc_bound_pool_threads": (c_int, [c_int, c_int, i32p, u8p, c_i64, c_int, c_int, i32p, c_int]),
+                "orc_bound_pool2": (c_int, [c_int, c_int, i32p, u8p, c_i64, c_int, i32p]),
+                "orc_lb2_parts": (c_int, [c_int, c_int, i32p, u8p, c_int, c_int, i32p, i32p, i32p, i32p]),
+                "orc_solve_bidir": (c_int, [c_int, c_int, i32p, c_i32, c_i64, c_i64, c_i64, i32p, u8p, i64p,
+                                            i64p, c_i64]),
                 "orc_lb_parts": (c_int, [c_int, c_int, i32p, u8p, c_int, c_int, i32p, i32p, i32p]),
                 "orc_tables_dump": (c_int, [c_int, c_int, i32p, i32p, i32p, u8p]),
                 "orc_bruteforce": (c_i32, [c_int, c_int, i32p, u8p]),
@@ -161,6 +166,20 @@ def bound_pool(p, nodes, bound: int = 0) -> np.ndarray:
     return out
 
 
+def bound_pool_threads(p, nodes, threads: int = 0, bound: int = 0):
+    """bound_pool with the nodes split over host threads (0 = all cores): the
+    same per-node bound.  Returns (bounds, threads used)."""
+    p, n, m = _inst(p)
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+    count, stride = nodes.shape
+    out = np.zeros(count, np.int32)
+    rc = _load().orc_bound_pool_threads(n, m, _p(p, ctypes.c_int32), _p(nodes, ctypes.c_uint8), count,
+                                        stride, int(bound), _p(out, ctypes.c_int32), int(threads))
+    if rc < 1:
+        raise ValueError(f"orc_bound_pool_threads failed ({rc})")
+    return out, int(rc)
+
+
 def bruteforce(p):
     """Optimum over all n! permutations and the lexicographically first optimal one."""
     p, n, m = _inst(p)
@@ -232,4 +251,65 @@ def solve(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, schedule=No
     res["stack_left"] = int(out_count.value)
     if export_stack:
         res["stack"] = stack
+    return res
+
+
+# --------------------------------------------------------------------------
+# Bidirectional branching (fsp_oracle.c, orc_*2 / orc_solve_bidir): a node is
+# a prefix perm[:d1], a suffix perm[n-d2:] and the remaining set between them.
+# --------------------------------------------------------------------------
+def stride2(n: int) -> int:
+    """Bytes of a bidirectional record: perm, d1, d2, padded to 16."""
+    return (n + 2 + 15) // 16 * 16
+
+
+def bound_pool2(p, nodes) -> np.ndarray:
+    """The bidirectional bound of every record (uint8 [count, stride]: perm[n],
+    d1 at byte n, d2 at byte n+1)."""
+    p, n, m = _inst(p)
+    nodes = np.ascontiguousarray(nodes, dtype=np.uint8)
+    count, stride = nodes.shape
+    out = np.zeros(count, np.int32)
+    rc = _load().orc_bound_pool2(n, m, _p(p, ctypes.c_int32), _p(nodes, ctypes.c_uint8), count, stride,
+                                 _p(out, ctypes.c_int32))
+    if rc != OK:
+        raise ValueError(f"orc_bound_pool2 failed ({rc})")
+    return out
+
+
+def lb2_parts(p, perm, d1: int, d2: int):
+    """(LB, LB1, [LB_kl per pair], [D_k per machine]) of one bidirectional node."""
+    p, n, m = _inst(p)
+    perm = np.ascontiguousarray(perm, dtype=np.uint8)
+    lb, lb1 = ctypes.c_int32(0), ctypes.c_int32(0)
+    pv = np.zeros(max(num_pairs(m), 1), np.int32)
+    D = np.zeros(m, np.int32)
+    rc = _load().orc_lb2_parts(n, m, _p(p, ctypes.c_int32), _p(perm, ctypes.c_uint8), int(d1), int(d2),
+                               ctypes.byref(lb), ctypes.byref(lb1), _p(pv, ctypes.c_int32), _p(D, ctypes.c_int32))
+    if rc != OK:
+        raise ValueError("invalid node")
+    return int(lb.value), int(lb1.value), pv[: num_pairs(m)], D
+
+
+def solve_bidir(p, ub0: int = INF, pool: int = 1024, node_budget: int = 0, max_iterations: int = 0,
+                trace_cap: int = 0):
+    """Pool-synchronous depth-first B&B with bidirectional branching (the
+    ends alternate: forward when d1 <= d2).  Same result dict as solve()."""
+    p, n, m = _inst(p)
+    perm = np.zeros(n, np.uint8)
+    stats = np.zeros(len(STATS), np.int64)
+    cmax = ctypes.c_int32(0)
+    trace = np.zeros((max(trace_cap, 1), 4), np.int64)
+    rc = _load().orc_solve_bidir(n, m, _p(p, ctypes.c_int32), int(ub0), int(pool), int(node_budget),
+                                 int(max_iterations), ctypes.byref(cmax), _p(perm, ctypes.c_uint8),
+                                 _p(stats, ctypes.c_int64), _p(trace, ctypes.c_int64) if trace_cap > 0 else None,
+                                 int(trace_cap))
+    if rc < 0:
+        raise RuntimeError(f"orc_solve_bidir failed ({rc})")
+    res = {k: int(v) for k, v in zip(STATS, stats)}
+    res["status"] = int(rc)
+    res["cmax"] = int(cmax.value)
+    res["perm"] = perm.copy() if res["incumbent_updates"] > 0 else None
+    if trace_cap > 0:
+        res["trace"] = trace[: min(res["iterations"], trace_cap)].copy()
     return res

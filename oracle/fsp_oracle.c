@@ -33,6 +33,7 @@
  *   The exact interleaving of a pool > 1 search once the incumbent improves
  *   has no independent pin: parity unpinned beyond the invariants above.
  */
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -308,6 +309,29 @@ int orc_bound_pool(int n, int m, const int32_t *p, const uint8_t *nodes, int64_t
     }
     tables_free(&t);
     return rc;
+}
+
+/* The same pool bound with the nodes split over `threads` host threads
+ * (OpenMP; 0 = all the host's cores): each node's bound is orc_lb exactly
+ * as above, only the loop over nodes runs in parallel.  For the all-core
+ * CPU baseline.  Returns the number of threads used, or ORC_ERR_ARG /
+ * ORC_ERR_OOM. */
+int orc_bound_pool_threads(int n, int m, const int32_t *p, const uint8_t *nodes, int64_t count, int stride,
+                           int variant, int32_t *lb_out, int threads)
+{
+    orc_tables t;
+    if (!shape_ok(n, m, p) || count < 0 || stride < n + 1 || threads < 0) return ORC_ERR_ARG;
+    if (tables_make(&t, n, m, p) != ORC_OK) { tables_free(&t); return ORC_ERR_OOM; }
+    int used = threads > 0 ? threads : omp_get_max_threads();
+    int bad = 0;
+#pragma omp parallel for num_threads(used) schedule(static) reduction(| : bad)
+    for (int64_t i = 0; i < count; i++) {
+        const uint8_t *rec = nodes + (size_t)i * stride;
+        if (!orc_check_node(n, rec, rec[n])) { bad = 1; continue; }
+        lb_out[i] = orc_lb(n, m, p, t.q, t.lag, t.order, rec, rec[n], variant, NULL, NULL);
+    }
+    tables_free(&t);
+    return bad ? ORC_ERR_ARG : used;
 }
 
 /* Per-node parts: LB1 and every LB_kl of one node (for pins). */
@@ -611,6 +635,299 @@ int orc_solve(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t
 
 done:
     free(st.rec);
+    free(parents);
+    free(children);
+    free(lbs);
+    tables_free(&t);
+    return rc;
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Bidirectional branching.  The paper branches forward only (a node is a    */
+/* scheduled prefix, Sec. II-B) and names other bounds and branchings as     */
+/* future work (Sec. VI).  Here a node is a prefix sigma1 = perm[0..d1), a   */
+/* suffix sigma2 = perm[n-d2..n) (both in schedule order) and the remaining  */
+/* set U = perm[d1..n-d2) between them; a parent branches either forward     */
+/* (append a job of U to sigma1) or backward (put a job of U in front of     */
+/* sigma2).                                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* 1 if perm[0..n) is a permutation of 0..n-1 and d1, d2 >= 0, d1 + d2 <= n. */
+int orc_check_node2(int n, const uint8_t *perm, int d1, int d2)
+{
+    if (d1 < 0 || d2 < 0 || d1 + d2 > n) return 0;
+    return orc_check_node(n, perm, 0);
+}
+
+/* Delivery times of a suffix (its jobs in schedule order): D_k = the length
+ * of the longest path from the suffix's first job on machine k to its last
+ * job on machine m-1, i.e. how long the schedule runs on after machine k
+ * starts the suffix.  The release-time recurrence run backwards: jobs from
+ * last to first, machines from m-1 down to 0, D_k = max(D_k, D_{k+1}) + p. */
+void orc_delivery_times(int n, int m, const int32_t *p, const uint8_t *suffix, int len, int32_t *D)
+{
+    (void)n;
+    for (int k = 0; k < m; k++) D[k] = 0;
+    for (int i = len - 1; i >= 0; i--) {
+        int j = suffix[i];
+        for (int k = m - 1; k >= 0; k--) {
+            int32_t later = k + 1 < m ? D[k + 1] : 0; /* this job, next machine */
+            D[k] = imax(D[k], later) + pt(p, m, j, k); /* D[k]: the next suffix job, same machine */
+        }
+    }
+}
+
+/* The bound of a bidirectional node.  With C_k the release times of sigma1,
+ * D_k the delivery times of sigma2, S_k and qmin_k the remaining sums and
+ * smallest tails over U as in orc_lb:
+ *   T_k    max(D_k, qmin_k): after machine k finishes U, it still runs sigma2
+ *          (at least D_k) and the last job of U still visits machines > k
+ *          (at least qmin_k);
+ *   LB1    max_k C_k + S_k + T_k;
+ *   LB_kl  the Johnson recurrence of orc_lb over U, t_l + T_l;
+ *   LB     max(LB1, max over pairs LB_kl).
+ * With sigma2 empty (D = 0, T = qmin) this is orc_lb's bound (variant 0);
+ * with U empty it is the makespan max_k C_k + D_k. */
+int32_t orc_lb2(int n, int m, const int32_t *p, const int32_t *q, const int32_t *lag, const uint8_t *order,
+                const uint8_t *perm, int d1, int d2, int32_t *lb1_out, int32_t *pair_out)
+{
+    int32_t C[ORC_MAXM], D[ORC_MAXM], S[ORC_MAXM], qmin[ORC_MAXM], T[ORC_MAXM];
+    int inU[ORC_MAXN + 1];
+
+    orc_release_times(n, m, p, perm, d1, C);
+    orc_delivery_times(n, m, p, perm + (n - d2), d2, D);
+    for (int j = 0; j < n; j++) inU[j] = 0;
+    for (int i = d1; i < n - d2; i++) inU[perm[i]] = 1;
+
+    for (int k = 0; k < m; k++) {
+        int32_t s = 0, mn = 0;
+        int first = 1;
+        for (int j = 0; j < n; j++) {
+            if (!inU[j]) continue;
+            s += pt(p, m, j, k);
+            if (first || q[(size_t)j * m + k] < mn) mn = q[(size_t)j * m + k];
+            first = 0;
+        }
+        S[k] = s;
+        qmin[k] = mn;
+        T[k] = imax(D[k], qmin[k]);
+    }
+
+    int32_t lb1 = 0;
+    for (int k = 0; k < m; k++) lb1 = imax(lb1, C[k] + S[k] + T[k]);
+    if (lb1_out) *lb1_out = lb1;
+
+    int32_t lb = lb1;
+    int kl = 0;
+    for (int k = 0; k < m; k++)
+        for (int l = k + 1; l < m; l++) {
+            const uint8_t *o = order + (size_t)kl * n;
+            const int32_t *lg = lag + (size_t)kl * n;
+            int32_t tk = C[k], tl = C[l];
+            for (int pos = 0; pos < n; pos++) {
+                int j = o[pos];
+                if (!inU[j]) continue;
+                tk = tk + pt(p, m, j, k);
+                tl = imax(tl, tk + lg[j]) + pt(p, m, j, l);
+            }
+            int32_t v = tl + T[l];
+            if (pair_out) pair_out[kl] = v;
+            lb = imax(lb, v);
+            kl++;
+        }
+    return lb;
+}
+
+/* Bound a pool of bidirectional records: perm bytes 0..n-1, d1 at byte n,
+ * d2 at byte n+1.  ORC_ERR_ARG if any record is invalid. */
+int orc_bound_pool2(int n, int m, const int32_t *p, const uint8_t *nodes, int64_t count, int stride,
+                    int32_t *lb_out)
+{
+    orc_tables t;
+    if (!shape_ok(n, m, p) || count < 0 || stride < n + 2) return ORC_ERR_ARG;
+    if (tables_make(&t, n, m, p) != ORC_OK) { tables_free(&t); return ORC_ERR_OOM; }
+    int rc = ORC_OK;
+    for (int64_t i = 0; i < count; i++) {
+        const uint8_t *rec = nodes + (size_t)i * stride;
+        if (!orc_check_node2(n, rec, rec[n], rec[n + 1])) { rc = ORC_ERR_ARG; break; }
+        lb_out[i] = orc_lb2(n, m, p, t.q, t.lag, t.order, rec, rec[n], rec[n + 1], NULL, NULL);
+    }
+    tables_free(&t);
+    return rc;
+}
+
+/* One bidirectional node's bound and parts (for pins). */
+int orc_lb2_parts(int n, int m, const int32_t *p, const uint8_t *perm, int d1, int d2, int32_t *lb_out,
+                  int32_t *lb1_out, int32_t *pair_out, int32_t *D_out)
+{
+    orc_tables t;
+    if (!shape_ok(n, m, p) || !orc_check_node2(n, perm, d1, d2)) return ORC_ERR_ARG;
+    if (tables_make(&t, n, m, p) != ORC_OK) { tables_free(&t); return ORC_ERR_OOM; }
+    *lb_out = orc_lb2(n, m, p, t.q, t.lag, t.order, perm, d1, d2, lb1_out, pair_out);
+    if (D_out) orc_delivery_times(n, m, p, perm + (n - d2), d2, D_out);
+    tables_free(&t);
+    return ORC_OK;
+}
+
+/*
+ * Search with bidirectional branching: the rules of orc_solve with these
+ * changes (records of n+2 bytes: perm, d1, d2):
+ *   - root: identity permutation, d1 = d2 = 0; a node has r = n - d1 - d2
+ *     children;
+ *   - direction: a parent with d1 <= d2 branches forward (children append a
+ *     job of U to sigma1), otherwise backward (children put a job of U in
+ *     front of sigma2): the two ends alternate;
+ *   - children of a parent by increasing index of the placed job; U stays in
+ *     increasing job order between sigma1 and sigma2;
+ *   - a child with one job left (d1 + d2 = n - 1) has a single completion:
+ *     it is a complete schedule whose value is that completion's makespan;
+ *     every other child gets orc_lb2.
+ * Selection, incumbent updates (first in L order wins ties), elimination
+ * (bound >= UB) and the push order are those of orc_solve.
+ */
+int orc_solve_bidir(int n, int m, const int32_t *p, int32_t ub0, int64_t pool, int64_t node_budget,
+                    int64_t max_iterations, int32_t *cmax, uint8_t *perm_out, int64_t *stats, int64_t *trace,
+                    int64_t trace_cap)
+{
+    if (!shape_ok(n, m, p) || pool < 1) return ORC_ERR_ARG;
+    for (int i = 0; i < ST_N; i++) stats[i] = 0;
+    int32_t UB = ub0;
+    if (n == 1) {
+        uint8_t only = 0;
+        int32_t c = orc_makespan(n, m, p, &only, 1);
+        if (c < UB) { UB = c; perm_out[0] = 0; stats[ST_UPDATES] = 1; }
+        *cmax = UB;
+        return ORC_OK;
+    }
+    orc_tables t;
+    if (tables_make(&t, n, m, p) != ORC_OK) { tables_free(&t); return ORC_ERR_OOM; }
+    const int w = n + 2;
+    uint8_t *stack = NULL, *parents = NULL, *children = NULL;
+    int32_t *lbs = NULL;
+    int64_t ssz = 0, scap = 0, par_cap = 0, ch_cap = 0;
+    int rc = ORC_OK;
+
+    scap = 1024;
+    stack = (uint8_t *)malloc((size_t)scap * w);
+    if (!stack) { rc = ORC_ERR_OOM; goto done; }
+    for (int i = 0; i < n; i++) stack[i] = (uint8_t)i;
+    stack[n] = 0;
+    stack[n + 1] = 0;
+    ssz = 1;
+
+    int64_t it = 0;
+    while (ssz > 0) {
+        if (node_budget > 0 && stats[ST_BOUNDED] >= node_budget) { rc = ORC_INCOMPLETE; break; }
+        if (max_iterations > 0 && it >= max_iterations) { rc = ORC_INCOMPLETE; break; }
+
+        /* selection: deepest parents while their children fit */
+        int64_t np = 0, nch = 0;
+        while (ssz > 0) {
+            const uint8_t *top = stack + (size_t)(ssz - 1) * w;
+            int64_t r = n - top[n] - top[n + 1];
+            if (np > 0 && nch + r > pool) break;
+            if (np == par_cap) {
+                par_cap = par_cap ? par_cap * 2 : 256;
+                uint8_t *x = (uint8_t *)realloc(parents, (size_t)par_cap * w);
+                if (!x) { rc = ORC_ERR_OOM; goto done; }
+                parents = x;
+            }
+            memcpy(parents + (size_t)np * w, top, (size_t)w);
+            np++;
+            nch += r;
+            ssz--;
+        }
+
+        /* branching */
+        if (nch > ch_cap) {
+            ch_cap = nch;
+            uint8_t *x = (uint8_t *)realloc(children, (size_t)ch_cap * w);
+            int32_t *y = (int32_t *)realloc(lbs, sizeof(int32_t) * (size_t)ch_cap);
+            if (x) children = x;
+            if (y) lbs = y;
+            if (!x || !y) { rc = ORC_ERR_OOM; goto done; }
+        }
+        int64_t c = 0;
+        for (int64_t a = 0; a < np; a++) {
+            const uint8_t *par = parents + (size_t)a * w;
+            const int d1 = par[n], d2 = par[n + 1];
+            const int forward = d1 <= d2;
+            uint8_t rem[ORC_MAXN];
+            int r = 0;
+            for (int i = d1; i < n - d2; i++) rem[r++] = par[i];
+            for (int x = 1; x < r; x++) { /* increasing job index */
+                uint8_t v = rem[x];
+                int y = x;
+                while (y > 0 && rem[y - 1] > v) { rem[y] = rem[y - 1]; y--; }
+                rem[y] = v;
+            }
+            for (int ci = 0; ci < r; ci++) {
+                uint8_t *ch = children + (size_t)c * w;
+                memcpy(ch, par, (size_t)w);
+                int o = d1;
+                if (forward) ch[o++] = rem[ci];
+                for (int x = 0; x < r; x++)
+                    if (x != ci) ch[o++] = rem[x];
+                if (!forward) ch[o++] = rem[ci];
+                ch[n] = (uint8_t)(forward ? d1 + 1 : d1);
+                ch[n + 1] = (uint8_t)(forward ? d2 : d2 + 1);
+                c++;
+            }
+        }
+
+        /* bounding: a child with one job left is its completion */
+        for (int64_t i = 0; i < nch; i++) {
+            const uint8_t *ch = children + (size_t)i * w;
+            if (ch[n] + ch[n + 1] == n - 1) lbs[i] = orc_makespan(n, m, p, ch, n);
+            else lbs[i] = orc_lb2(n, m, p, t.q, t.lag, t.order, ch, ch[n], ch[n + 1], NULL, NULL);
+        }
+        stats[ST_BOUNDED] += nch;
+        stats[ST_BRANCHED] += np;
+
+        const int32_t ub_start = UB;
+        for (int64_t i = 0; i < nch; i++) {
+            const uint8_t *ch = children + (size_t)i * w;
+            if (ch[n] + ch[n + 1] != n - 1) continue;
+            stats[ST_LEAVES]++;
+            if (lbs[i] < UB) {
+                UB = lbs[i];
+                memcpy(perm_out, ch, (size_t)n);
+            }
+        }
+        if (UB < ub_start) stats[ST_UPDATES]++;
+
+        int64_t nsurv = 0;
+        for (int64_t i = 0; i < nch; i++) {
+            const uint8_t *ch = children + (size_t)i * w;
+            if (ch[n] + ch[n + 1] == n - 1) continue;
+            if (lbs[i] < UB) nsurv++;
+            else stats[ST_PRUNED]++;
+        }
+        for (int64_t i = nch - 1; i >= 0; i--) {
+            const uint8_t *ch = children + (size_t)i * w;
+            if (ch[n] + ch[n + 1] == n - 1 || lbs[i] >= UB) continue;
+            if (ssz == scap) {
+                scap *= 2;
+                uint8_t *x = (uint8_t *)realloc(stack, (size_t)scap * w);
+                if (!x) { rc = ORC_ERR_OOM; goto done; }
+                stack = x;
+            }
+            memcpy(stack + (size_t)ssz * w, ch, (size_t)w);
+            ssz++;
+        }
+        if (trace && it < trace_cap) {
+            trace[it * 4 + 0] = np;
+            trace[it * 4 + 1] = nch;
+            trace[it * 4 + 2] = nsurv;
+            trace[it * 4 + 3] = UB;
+        }
+        it++;
+        stats[ST_ITERATIONS] = it;
+    }
+    *cmax = UB;
+done:
+    free(stack);
     free(parents);
     free(children);
     free(lbs);

@@ -525,3 +525,18 @@ def test_mlp_oracle_forward_and_loss_hand_worked():
     X2 = np.vstack([X, X])
     want = (np.log1p(np.exp(-1.0)) + np.log1p(np.e)) / 2
     assert abs(om.loss(params, X2, np.array([0, 1])) - want) < 1e-12
+
+
+def test_threaded_pool_bound_equals_the_serial_one():
+    """The all-core baseline splits the nodes over host threads; every bound
+    is the serial oracle's."""
+    p, _, rec = inputs.pool_workload(20, 20, 1, 3001)
+    want = oracle.bound_pool(p, rec)
+    for threads in (1, 3, 0):
+        got, used = oracle.bound_pool_threads(p, rec, threads)
+        assert np.array_equal(got, want)
+        assert used >= 1 and (threads == 0 or used == threads)
+    bad = rec.copy()
+    bad[5, 0] = bad[5, 1]
+    with pytest.raises(ValueError):
+        oracle.bound_pool_threads(p, bad, 2)
