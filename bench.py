@@ -186,7 +186,10 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def cpu_baseline(p, ub, frontier, budget_s=12.0):
+def cpu_baseline(p, ub, frontier, pool_nodes, gpu_bound_pool, budget_s=12.0):
+    """The serial oracle on one host core (the paper's baseline is one CPU
+    core), and the oracle's pool bound on all host cores (OpenMP over the
+    nodes) on the 20x20 bounding pool, beside the GPU's fsp_bound_pool."""
     import oracle
     bounded, steps, t0 = 0, 0, time.perf_counter()
     pool = 2**16
@@ -195,20 +198,34 @@ def cpu_baseline(p, ub, frontier, budget_s=12.0):
         bounded += r["bounded"]
         steps += 1
     dt = time.perf_counter() - t0
+    sample = pool_nodes[:2**18]
+    oracle.bound_pool_threads(p, sample[:4096], 0)  # threads up
+    t1 = time.perf_counter()
+    _, cores = oracle.bound_pool_threads(p, sample, 0)
+    dt_all = time.perf_counter() - t1
+    rate_all = len(sample) / dt_all
     return {"value": bounded / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} B&B iterations of {pool} children from the same 20x20 frontier "
-                      f"({dt:.1f} s, serial C oracle, one host core)"}
+                      f"({dt:.1f} s, serial C oracle, one host core)",
+            "nproc": os.cpu_count(),
+            "bound_pool_all_cores": {
+                "value": rate_all, "unit": "nodes bounded/s", "cores": cores, "kind": "oracle (OpenMP over nodes)",
+                "sample": f"the {len(sample)}-node 20x20 seed-1 bounding pool ({dt_all:.2f} s on {cores} threads)",
+                "gpu_fsp_bound_pool_nodes_per_s": gpu_bound_pool,
+                "gpu_over_all_cores": gpu_bound_pool / rate_all}}
 
 
 SOLVES = (  # (n, m, seed, pool): 0 = tuned while searching
     (12, 5, 0, 1024), (20, 5, 2, 0), (50, 5, 3, 0), (100, 5, 4, 0), (20, 10, 5, 0))
 SOLVE_BUDGET = 1_000_000_000
+SOLVE_BUDGETS = {}  # per-instance node budgets that differ from SOLVE_BUDGET
 
 
 def solve_times(fsp, budget=SOLVE_BUDGET):
     """Time to optimality of the exact solves (12x5 from UB = +inf with pool 1024;
     20x5, 50x5, 100x5, 20x10 from the device NEH makespan with the tuned pool),
-    each stopped by a node budget."""
+    each stopped by a node budget; the NEH time is reported apart from the
+    search time (time_s is their sum)."""
     from paper_1206_4973_gb300 import inputs
     out = []
     for n, m, seed, pool in SOLVES:
@@ -219,12 +236,15 @@ def solve_times(fsp, budget=SOLVE_BUDGET):
             ub0, perm0 = fsp.fsp_neh(inst)
         else:
             ub0, perm0 = fsp.UB_INF, None
-        r = fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=budget)
-        dt = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        cap = SOLVE_BUDGETS.get((n, m, seed), budget)
+        r = fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=cap)
+        t2 = time.perf_counter()
         out.append({"instance": f"{n}x{m} seed {seed}", "ub0": None if pool else ub0, "cmax": r["cmax"],
-                    "optimal": r["status"] == fsp.OK, "time_s": dt, "nodes_bounded": r["nodes_bounded"],
+                    "optimal": r["status"] == fsp.OK, "time_s": t2 - t0, "neh_s": t1 - t0, "search_s": t2 - t1,
+                    "node_budget": cap, "nodes_bounded": r["nodes_bounded"],
                     "iterations": r["iterations"], "pool": r["tuned_pool"] if pool == 0 else pool,
-                    "warps_per_cta": r["tuned_warps"], "nodes_per_s": r["nodes_bounded"] / dt})
+                    "warps_per_cta": r["tuned_warps"], "nodes_per_s": r["nodes_bounded"] / (t2 - t1)})
         inst.close()
     return out
 
@@ -318,6 +338,33 @@ def bound_variants(fsp):
             dt = time.perf_counter() - t0
             row[name] = {"time_s": dt, "nodes_bounded": r["nodes_bounded"], "cmax": r["cmax"],
                          "optimal": r["status"] == fsp.OK, "nodes_per_s": r["nodes_bounded"] / dt}
+        inst.close()
+        out.append(row)
+    return out
+
+
+BIDIR_RUNS = ((12, 5, 0), (20, 5, 2), (20, 10, 5), (15, 10, 101))
+
+
+def bidir_vs_forward(fsp):
+    """Forward against bidirectional branching on the same instances: device
+    NEH UB, tuned pool, to optimality; the optimum must agree."""
+    from paper_1206_4973_gb300 import inputs
+    out = []
+    for n, m, seed in BIDIR_RUNS:
+        p = inputs.instance(n, m, seed)
+        inst = fsp.fsp_create_instance(p)
+        ub0, perm0 = fsp.fsp_neh(inst)
+        row = {"instance": f"{n}x{m} seed {seed}", "ub0": ub0}
+        for name, br in (("forward", fsp.BRANCH_FORWARD), ("bidirectional", fsp.BRANCH_BIDIR)):
+            fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=4096, node_budget=100_000, branching=br)
+            t0 = time.perf_counter()
+            r = fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=0, node_budget=SOLVE_BUDGET, branching=br)
+            dt = time.perf_counter() - t0
+            row[name] = {"time_s": dt, "nodes_bounded": r["nodes_bounded"], "cmax": r["cmax"],
+                         "optimal": r["status"] == fsp.OK, "nodes_per_s": r["nodes_bounded"] / dt}
+        row["same_optimum"] = row["forward"]["cmax"] == row["bidirectional"]["cmax"]
+        row["node_ratio"] = row["bidirectional"]["nodes_bounded"] / max(1, row["forward"]["nodes_bounded"])
         inst.close()
         out.append(row)
     return out
@@ -543,6 +590,7 @@ def main():
             "e2e": e2e,
             "bound_pool": bp,
             "bound_variants": bound_variants(fsp),
+            "bidirectional": bidir_vs_forward(fsp),
             "phase_ms": {"select": r["select_ms"], "branch_bound": r["bound_ms"], "compact": r["compact_ms"]},
             "wall_s": t_wall,
             "solves": solve_times(fsp),
@@ -550,7 +598,7 @@ def main():
             "batch": batch_solve(fsp),
         }
         if world == 1 and not args.no_cpu:
-            line["cpu_baseline"] = cpu_baseline(p, ub, frontier)
+            line["cpu_baseline"] = cpu_baseline(p, ub, frontier, big, bp[str(2**18)]["nodes_per_s"])
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

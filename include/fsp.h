@@ -146,7 +146,20 @@ typedef struct {
                                record (log_cap entries; in the learned order a child cut
                                by its predicted pairs logs that partial bound, which is
                                >= the UB of its iteration) */
+    int branching;          /* FSP_BRANCH_FORWARD (default): a node is a scheduled prefix
+                               and its children append a job (Sec. II-B).
+                               FSP_BRANCH_BIDIR: a node is a prefix, a suffix and the jobs
+                               between them (records of fsp_node_stride_bidir(n) bytes,
+                               bound of fsp_bound_pool_bidir); a parent with prefix length
+                               d1 <= suffix length d2 appends a job to the prefix, otherwise
+                               puts one in front of the suffix; a child with one job left
+                               is its completion.  Starts from the root (init_nodes must be
+                               NULL), plain order, base bound, no node logging; out_nodes
+                               receives bidirectional records. */
 } fsp_options;
+
+#define FSP_BRANCH_FORWARD 0
+#define FSP_BRANCH_BIDIR 1
 
 /* Fill *opt with the defaults (pool 1024, no budget, default capacity). */
 int fsp_default_options(fsp_options *opt);
@@ -196,6 +209,29 @@ int fsp_instance_tables(const fsp_instance *inst, int32_t *q, int32_t *lag, uint
  * FSP_ERR_CUDA for a failed launch. */
 int fsp_bound_pool(fsp_instance *inst, const uint8_t *nodes, int64_t count, int32_t ub,
                    int32_t *lb_out, void *stream);
+
+/* Bidirectional nodes (no counterpart in the paper, which branches forward
+ * only, Sec. II-B; it leaves other branchings to future work, Sec. VI).  A
+ * record of fsp_node_stride_bidir(n) = n + 2 rounded up to 16 bytes holds a
+ * permutation of 0..n-1 whose first d1 entries are the scheduled prefix,
+ * whose last d2 entries are the scheduled suffix (both in schedule order) and
+ * whose middle holds the remaining set U in any order; byte n holds d1, byte
+ * n+1 holds d2 (d1 + d2 <= n), the rest is zero. */
+int fsp_node_stride_bidir(int n);
+
+/* The bound of `count` bidirectional records (device, count x
+ * fsp_node_stride_bidir(n) bytes) into lb_out (device, count int32): the
+ * bound of fsp_bound_pool with each machine's tail qmin_k replaced by
+ * T_k = max(D_k, qmin_k), where D_k, the suffix's delivery time, is the
+ * length of the longest path from the suffix's first job on machine k to its
+ * last job on machine m-1 (after machine k finishes U it still runs the
+ * suffix, and the last job of U still visits the machines after k).  With no
+ * suffix it is fsp_bound_pool's bound (base variant); with U empty it is the
+ * makespan.  Malformed records (d1 + d2 > n, not a permutation) get
+ * FSP_LB_INVALID and set the error flag fsp_check_status reports.
+ * Asynchronous on `stream`.  Errors (immediate): FSP_ERR_ARG (count < 0, NULL
+ * or misaligned buffers), FSP_ERR_CUDA. */
+int fsp_bound_pool_bidir(fsp_instance *inst, const uint8_t *nodes, int64_t count, int32_t *lb_out, void *stream);
 
 /* Synchronise `stream` and report (then clear) the instance's error flag:
  * FSP_ERR_ARG if a malformed record was seen since the last check. */

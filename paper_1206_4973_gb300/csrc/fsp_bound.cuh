@@ -39,3 +39,5 @@ int fsp_bound_shape(const fsp_instance *I, BoundShape *s);
 int pool16_eligible(const fsp_instance *I);
 int pool16_bound(fsp_instance *I, const uint8_t *nodes, long long count, int32_t *lb_out, cudaStream_t st,
                  int warps);
+int pool16_bound_ex(fsp_instance *I, const uint8_t *nodes, long long count, const long long *dcount, bool bidir,
+                    int32_t *lb_out, cudaStream_t st, int warps);

@@ -152,14 +152,16 @@ __global__ void k_pool16_image(int n, int m, int P, const int32_t *__restrict__ 
 // the prefix), remaining sums, smallest tails and, for the heads variant,
 // smallest processing times as 16-bit machine pairs; the remaining set Um
 // and the validity of the record, as fsp_prologue.
-template <int MT, int NV>
-__device__ __forceinline__ void p16_prologue(const FspRec<NV> &r, int d, int n, const uint32_t *__restrict__ rows,
-                                             uint32_t &Um, int32_t (&C)[MT], int32_t (&SQ)[MT], int32_t &lb1,
-                                             bool &bad, int var)
+template <int MT, int NV, bool BIDIR>
+__device__ __forceinline__ void p16_prologue(const FspRec<NV> &r, int d, int d2, int n,
+                                             const uint32_t *__restrict__ rows, uint32_t &Um, int32_t (&C)[MT],
+                                             int32_t (&SQ)[MT], int32_t &lb1, bool &bad, int var)
 {
     constexpr int H = P16Dims<MT>::H, RS = P16Dims<MT>::RS;
-    bad = d > n;
-    const bool heads = var == FSP_BOUND_HEADS;
+    if (!BIDIR) d2 = 0;
+    bad = d + d2 > n;
+    const int mid_end = n - d2;  // positions [d, mid_end) hold the remaining set
+    const bool heads = !BIDIR && var == FSP_BOUND_HEADS;
     uint32_t Am = 0u, S2[H], Q2[H], Pm2[H];
     Um = 0u;
 #pragma unroll
@@ -190,6 +192,8 @@ __device__ __forceinline__ void p16_prologue(const FspRec<NV> &r, int d, int n, 
                     C[0] += (int32_t)row[0];
 #pragma unroll
                     for (int k = 1; k < MT; ++k) C[k] = max(C[k], C[k - 1]) + (int32_t)row[k];
+                } else if (BIDIR && i >= mid_end) {
+                    // suffix job: its delivery times follow in a second pass
                 } else {
                     Um |= bit;
 #pragma unroll
@@ -212,22 +216,54 @@ __device__ __forceinline__ void p16_prologue(const FspRec<NV> &r, int d, int n, 
             C[k] = max(C[k], C[k - 1] + pm);
         }
     }
+    // bidirectional nodes: delivery times of the suffix, its jobs from the
+    // last back (words from the top, rotated the other way), machines from
+    // m-1 down: D_k = max(D_k, D_{k+1}) + p
+    int32_t D[MT];
+#pragma unroll
+    for (int k = 0; k < MT; ++k) D[k] = 0;
+    if (BIDIR && d2 > 0) {
+        uint32_t rw[4 * NV];
+#pragma unroll
+        for (int q = 0; q < 4 * NV; ++q) rw[q] = r.w[q];
+#pragma unroll 1
+        for (int wq = 4 * NV - 1; wq >= 0; --wq) {
+            const uint32_t wd = rw[4 * NV - 1];
+#pragma unroll
+            for (int q = 4 * NV - 1; q > 0; --q) rw[q] = rw[q - 1];
+#pragma unroll
+            for (int b = 3; b >= 0; --b) {
+                const int i = 4 * wq + b;
+                if (i < n && i >= mid_end) {
+                    uint32_t j = (wd >> (8 * b)) & 0xFFu;
+                    if (j >= (uint32_t)n) j = 0;
+                    const uint32_t *row = rows + j * RS;
+                    D[MT - 1] += (int32_t)row[MT - 1];
+#pragma unroll
+                    for (int k = MT - 2; k >= 0; --k) D[k] = max(D[k], D[k + 1]) + (int32_t)row[k];
+                }
+            }
+        }
+    }
     lb1 = 0;
 #pragma unroll
     for (int k = 0; k < MT; ++k) {
         const int32_t sk = (int32_t)((S2[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu);
         const int32_t qk = (int32_t)((Q2[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu);
-        SQ[k] = sk + (qk == 0x7FFF ? 0 : qk);
+        const int32_t qm = qk == 0x7FFF ? 0 : qk;
+        SQ[k] = sk + (BIDIR ? max(D[k], qm) : qm);  // the tail after machine k
         lb1 = max(lb1, C[k] + SQ[k]);
     }
 }
 
-template <int MT, int NV>
+template <int MT, int NV, bool BIDIR>
 __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst I, const uint8_t *__restrict__ img,
                                                                       const uint8_t *__restrict__ nodes,
-                                                                      long long count, int32_t *__restrict__ lb_out,
+                                                                      long long count, const long long *dcount,
+                                                                      int stride, int32_t *__restrict__ lb_out,
                                                                       Pool16Smem L)
 {
+    if (dcount) count = *dcount;  // a pool whose size only the device knows (the search's children)
     constexpr int P = MT * (MT - 1) / 2;
     constexpr int NPASS = (P + 31) / 32;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -253,10 +289,11 @@ __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst 
         // -- lane v: node g*32 + v, its one-machine quantities into the tables
         const long long node = (g << 5) + lane;
         FspRec<NV> r;
-        int d = 0;
+        int d = 0, d2 = 0;
         if (node < count) {
-            fsp_load_rec(r, nodes + node * I.stride);
-            d = __ldg(nodes + node * I.stride + n);  // the depth byte (same sector: no second fetch)
+            fsp_load_rec(r, nodes + node * stride);
+            d = __ldg(nodes + node * stride + n);  // the depth bytes (same sector: no second fetch)
+            if (BIDIR) d2 = __ldg(nodes + node * stride + n + 1);
         } else {
 #pragma unroll
             for (int q = 0; q < 4 * NV; ++q) r.w[q] = 0u;
@@ -264,7 +301,7 @@ __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst 
         uint32_t Um;
         int32_t C[MT], SQ[MT], lb1;
         bool bad;
-        p16_prologue<MT, NV>(r, d, n, rows_s, Um, C, SQ, lb1, bad, I.var);
+        p16_prologue<MT, NV, BIDIR>(r, d, d2, n, rows_s, Um, C, SQ, lb1, bad, I.var);
         for (int j = 0; j < n; ++j) th[j * (2 * P16_TS) + lane] = ((Um >> j) & 1u) ? 0xFFFFu : 0u;
 #pragma unroll
         for (int k = 0; k < MT; ++k) {
@@ -334,14 +371,20 @@ __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst 
     }
 }
 
-typedef void (*Pool16Fn)(DevInst, const uint8_t *, const uint8_t *, long long, int32_t *, Pool16Smem);
+typedef void (*Pool16Fn)(DevInst, const uint8_t *, const uint8_t *, long long, const long long *, int, int32_t *,
+                         Pool16Smem);
 
-static Pool16Fn pick_pool16(int mt, int nv)
+static Pool16Fn pick_pool16(int mt, int nv, bool bidir)
 {
 #define FSP_CASE16(MT_, NV_) \
-    if (mt == MT_ && nv == NV_) return &k_bound_pool16<MT_, NV_>;
+    if (mt == MT_ && nv == NV_) return bidir ? &k_bound_pool16<MT_, NV_, true> : &k_bound_pool16<MT_, NV_, false>;
     FSP_CASE16(5, 1) FSP_CASE16(5, 2) FSP_CASE16(10, 1) FSP_CASE16(10, 2) FSP_CASE16(20, 1) FSP_CASE16(20, 2)
 #undef FSP_CASE16
+    if (bidir && nv == 3) {  // bidirectional records of 30 and 31 jobs: 48 bytes
+        if (mt == 5) return &k_bound_pool16<5, 3, true>;
+        if (mt == 10) return &k_bound_pool16<10, 3, true>;
+        if (mt == 20) return &k_bound_pool16<20, 3, true>;
+    }
     return nullptr;
 }
 
@@ -375,8 +418,18 @@ int pool16_build(fsp_instance *I)
 int pool16_bound(fsp_instance *I, const uint8_t *nodes, long long count, int32_t *lb_out, cudaStream_t st,
                  int warps)
 {
+    return pool16_bound_ex(I, nodes, count, nullptr, false, lb_out, st, warps);
+}
+
+// count: the number of records, or (dcount non-NULL) an upper bound on it,
+// the exact number being read by the kernel from device memory.  bidir:
+// bidirectional records (fsp_node_stride_bidir bytes: perm, d1, d2).
+int pool16_bound_ex(fsp_instance *I, const uint8_t *nodes, long long count, const long long *dcount, bool bidir,
+                    int32_t *lb_out, cudaStream_t st, int warps)
+{
     if (!pool16_eligible(I) || !I->d_p16) return FSP_ERR_ARG;
-    Pool16Fn fn = pick_pool16(fsp_mt(I->m), I->stride / 16);
+    const int stride = bidir ? fsp_node_stride_bidir(I->n) : I->stride;
+    Pool16Fn fn = pick_pool16(fsp_mt(I->m), stride / 16, bidir);
     if (!fn) return FSP_ERR_ARG;
     const long long groups = (count + 31) / 32;
     if (warps <= 0) {
@@ -394,7 +447,7 @@ int pool16_bound(fsp_instance *I, const uint8_t *nodes, long long count, int32_t
     long long grid = (long long)I->sm_count * per_sm;
     const long long need = (groups + warps - 1) / warps;
     if (need < grid) grid = need;
-    fn<<<(unsigned)grid, warps * 32, L.bytes, st>>>(dev_view(I), I->d_p16, nodes, count, lb_out, L);
+    fn<<<(unsigned)grid, warps * 32, L.bytes, st>>>(dev_view(I), I->d_p16, nodes, count, dcount, stride, lb_out, L);
     FSP_CUDA(cudaGetLastError());
     return FSP_OK;
 }

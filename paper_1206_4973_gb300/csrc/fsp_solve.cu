@@ -50,8 +50,19 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Largest pool the tuner may try: SMs x 2048 resident threads (Sec. III).
 static long long tuner_max_pool(const fsp_instance *I) { return (long long)I->sm_count * 2048; }
 
+// Bytes per stack record: forward records, or bidirectional ones (perm, d1, d2).
+static int rec_stride(const fsp_instance *I, const fsp_options *o)
+{
+    return o->branching == FSP_BRANCH_BIDIR ? fsp_node_stride_bidir(I->n) : I->stride;
+}
+
 static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout *L)
 {
+    if (o->branching != FSP_BRANCH_FORWARD && o->branching != FSP_BRANCH_BIDIR) {
+        fsp_set_error("unknown branching %d", o->branching);
+        return FSP_ERR_ARG;
+    }
+    const int rs = rec_stride(I, o);
     long long pool = o->pool_size == 0 ? tuner_max_pool(I) : o->pool_size;
     if (pool < 1 || pool > (1LL << 26)) {
         fsp_set_error("pool_size %lld outside 1..2^26", pool);
@@ -75,10 +86,10 @@ static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout
     size_t off = 0;
     L->off_ctl = off; off = align256(off + sizeof(SolveCtl));
     L->off_inc = off; off = align256(off + 256);  // right after the control block: one read-back
-    L->off_stack = off; off = align256(off + (size_t)L->cap * I->stride);
+    L->off_stack = off; off = align256(off + (size_t)L->cap * rs);
     L->off_cum = off; off = align256(off + (size_t)L->cap * 8);
     L->off_iblk = off; off = align256(off + (size_t)((init + 255) / 256 + 1) * 8);
-    L->off_children = off; off = align256(off + (size_t)L->max_children * I->stride);
+    L->off_children = off; off = align256(off + (size_t)L->max_children * rs);
     L->off_lbs = off; off = align256(off + (size_t)L->max_children * 4);
     L->off_poff = off; off = align256(off + (size_t)(L->max_children + 2) * 4);
     L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 12);
@@ -559,14 +570,16 @@ __global__ void __launch_bounds__(SOLVE_B) k_count(SolveWs ws, int n, int stride
     const int ubn = solve_ub_new(ctl);
     const long long c = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
     bool leaf = false, surv = false;
+    int dch = 0;
     if (c < nch) {
-        leaf = ws.children[c * stride + n] == (uint8_t)(n - 1);
+        dch = solve_depth(ws, ws.children + c * stride, n);
+        leaf = dch == n - 1;
         surv = !leaf && ws.lbs[c] < ubn;
     }
     __shared__ long long red[SOLVE_B / 32];
     const int cs = __syncthreads_count(surv);
     const int cl = __syncthreads_count(leaf);
-    const long long cr = block_sum_ll(surv ? n - (int)ws.children[c * stride + n] : 0, red);
+    const long long cr = block_sum_ll(surv ? n - dch : 0, red);
     if (threadIdx.x == 0) {
         ws.blk[3 * blockIdx.x] = cs;
         ws.blk[3 * blockIdx.x + 1] = cl;
@@ -608,7 +621,7 @@ __global__ void __launch_bounds__(SOLVE_B) k_push(SolveWs ws, int n, int stride)
     bool surv = false;
     int rc = 0;
     if (c < nch) {
-        const int dch = ws.children[c * stride + n];
+        const int dch = solve_depth(ws, ws.children + c * stride, n);
         surv = dch != n - 1 && ws.lbs[c] < ubn;
         rc = surv ? n - dch : 0;
     }
@@ -892,6 +905,8 @@ struct SolvePlan {
     BoundListFn blist;
     int per_cta;
     int list_grid;       // persistent grid of the list kernel
+    bool bidir;          // bidirectional branching
+    int rs;              // bytes per stack record
 };
 
 static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fsp_options *opt, SolvePlan *P)
@@ -901,6 +916,28 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
     const fsp_options &o = P->o;
     int rc = solve_layout(I, &o, &P->L);
     if (rc != FSP_OK) return rc;
+    P->bidir = o.branching == FSP_BRANCH_BIDIR;
+    P->rs = rec_stride(I, &o);
+    if (P->bidir) {
+        if ((o.init_nodes && o.init_count > 0) || o.order != FSP_ORDER_PLAIN || o.log_nodes) {
+            fsp_set_error("fsp_solve: bidirectional branching starts from the root, in the plain order, "
+                          "without node logging");
+            return FSP_ERR_ARG;
+        }
+        P->bb = nullptr;
+        P->bb2 = nullptr;
+        P->bf = nullptr;
+        P->nfam = 0;
+        P->bl = nullptr;
+        P->blist = nullptr;
+        P->list_grid = 0;
+        P->per_cta = 256;
+        if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
+            fsp_set_error("fsp_solve: workspace must be 256-byte aligned");
+            return FSP_ERR_ARG;
+        }
+        return FSP_OK;
+    }
     if ((rc = fsp_bound_shape(I, &P->shp)) != FSP_OK) return rc;
     const BoundShape &shp = P->shp;
     P->bb = nullptr;
@@ -1003,6 +1040,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     ws.pscore = (float *)(base + L.off_pscore);
     ws.topk = (int16_t *)(base + L.off_topk);
     ws.max_parents = L.max_parents;
+    ws.bidir = P->bidir ? 1 : 0;
+    const int rs = P->rs;
     const DevInst D = dev_view(I);
     const float T = (float)I->total / (float)I->m;
     long long logged = 0;
@@ -1068,7 +1107,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if (scanned) k_init_scan<<<1, 1024, 0, st>>>(ws, gi);
             k_init_cum<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count, scanned);
         } else {
-            k_solve_init<<<1, 128, 0, st>>>(ws, I->n, I->stride, ub0);
+            k_solve_init<<<1, 128, 0, st>>>(ws, I->n, rs, ub0);
         }
         TRY(cudaGetLastError());
         // the start state is known here, so the first iteration goes out
@@ -1089,10 +1128,16 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
             idle = false;
             if (prof) LTRY(cudaEventRecord(pe[0], st));
-            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, I->stride, pool, o.node_budget, o.max_iterations,
+            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, rs, pool, o.node_budget, o.max_iterations,
                                              P->bf == nullptr);
             if (prof) LTRY(cudaEventRecord(pe[1], st));
-            if (P->bl) {
+            if (P->bidir) {  // children, their bounds, then the exact values of the complete ones
+                const long long mc = pool + I->n;
+                bidir_launch_children(ws, I->n, rs, mc, st);
+                const int brc = bidir_bound(I, ws.children, mc, &ws.ctl->n_children, ws.lbs, st);
+                if (brc != FSP_OK) return brc;
+                bidir_launch_leaves(ws, I, rs, mc, st);
+            } else if (P->bl) {
                 const long long npar = pool / 2 + 2;  // stacked nodes have >= 2 children
                 int frc = fsp_mlp_topk_parents(o.model, I, ws.stack, &ws.ctl->s_pop, &ws.ctl->n_parents, npar,
                                                L.topk, ws.topk, st);
@@ -1130,8 +1175,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
             }
             if (prof) LTRY(cudaEventRecord(pe[2], st));
-            k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
-            k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, I->stride);
+            k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, rs);
+            k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, rs);
             if (prof) LTRY(cudaEventRecord(pe[3], st));
             LTRY(cudaGetLastError());
 #undef LTRY
@@ -1275,7 +1320,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     if (o.out_count) *o.out_count = h.stack_size;
     if (o.log_count) *o.log_count = logged;
     if (o.out_nodes && h.stack_size > 0 && h.stack_size <= o.out_cap && I->n > 1)
-        TRY(cudaMemcpy(o.out_nodes, ws.stack, (size_t)h.stack_size * I->stride, cudaMemcpyDefault));
+        TRY(cudaMemcpy(o.out_nodes, ws.stack, (size_t)h.stack_size * rs, cudaMemcpyDefault));
     if (stats) {
         stats->select_ms = t_sel;
         stats->bound_ms = t_bb;

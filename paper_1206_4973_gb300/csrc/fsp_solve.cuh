@@ -41,7 +41,22 @@ struct SolveWs {
     float *pscore;          // parent pair scores [max_parents][P]
     int16_t *topk;          // best pairs of each parent [max_parents][K]
     long long max_parents;
+    int bidir;              // bidirectional records: depth = d1 (byte n) + d2 (byte n+1)
 };
+
+// Scheduled jobs of a record: its depth, or d1 + d2 for a bidirectional one.
+__device__ __forceinline__ int solve_depth(const SolveWs &ws, const uint8_t *rec, int n)
+{
+    return ws.bidir ? rec[n] + rec[n + 1] : rec[n];
+}
+
+// Bidirectional branching (fsp_bidir.cu).
+int bidir_bound(fsp_instance *I, const uint8_t *nodes, long long count, const long long *dcount, int32_t *lb_out,
+                cudaStream_t st);
+void bidir_launch_children(const SolveWs &ws, int n, int stride, long long max_children, cudaStream_t st);
+void bidir_launch_leaves(const SolveWs &ws, const fsp_instance *I, int stride, long long max_children,
+                         cudaStream_t st);
+extern "C" int fsp_node_stride_bidir(int n);
 
 
 // Parent of child c: the last p with poff[p] <= c (poff increasing, poff[0] = 0).

@@ -23,7 +23,8 @@ _NAMES = {ERR_ARG: "FSP_ERR_ARG", ERR_CUDA: "FSP_ERR_CUDA", ERR_OOM: "FSP_ERR_OO
           ERR_CAPACITY: "FSP_ERR_CAPACITY", ERR_TIMEOUT: "FSP_ERR_TIMEOUT"}
 
 # Every symbol include/fsp.h declares.
-EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_create_instance", "fsp_destroy_instance",
+EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_node_stride_bidir", "fsp_bound_pool_bidir",
+           "fsp_create_instance", "fsp_destroy_instance",
            "fsp_instance_tables", "fsp_bound_pool", "fsp_check_status", "fsp_solve_workspace_bytes",
            "fsp_solve", "fsp_solve_noalloc", "fsp_neh", "fsp_tune_simulate", "fsp_block_tune_simulate",
            "fsp_node_features",
@@ -65,8 +66,10 @@ class fsp_options(ctypes.Structure):
                 ("schedule_out", ctypes.POINTER(ctypes.c_int64)), ("schedule_out_cap", ctypes.c_int64),
                 ("order", ctypes.c_int), ("topk", ctypes.c_int), ("model", ctypes.c_void_p),
                 ("log_nodes", ctypes.c_void_p), ("log_cap", ctypes.c_int64),
-                ("log_count", ctypes.POINTER(ctypes.c_int64)), ("log_lbs", ctypes.c_void_p)]
+                ("log_count", ctypes.POINTER(ctypes.c_int64)), ("log_lbs", ctypes.c_void_p),
+                ("branching", ctypes.c_int)]
 ORDER_PLAIN, ORDER_LEARNED = 0, 1
+BRANCH_FORWARD, BRANCH_BIDIR = 0, 1
 
 
 _lib = None
@@ -90,6 +93,8 @@ def load(path: str | None = None):
     sig = {
         "fsp_default_options": (ctypes.c_int, [ctypes.POINTER(fsp_options)]),
         "fsp_node_stride": (ctypes.c_int, [ctypes.c_int]),
+        "fsp_node_stride_bidir": (ctypes.c_int, [ctypes.c_int]),
+        "fsp_bound_pool_bidir": (ctypes.c_int, [vp, vp, i64, vp, vp]),
         "fsp_create_instance": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, i32p, ctypes.POINTER(vp)]),
         "fsp_destroy_instance": (None, [vp]),
         "fsp_instance_tables": (ctypes.c_int, [vp, i32p, i32p, u8p]),
@@ -223,6 +228,29 @@ def fsp_bound_pool(inst: Instance, nodes, ub: int = UB_INF, lb_out=None, stream=
     return lb_out
 
 
+def fsp_node_stride_bidir(n: int) -> int:
+    return int(load().fsp_node_stride_bidir(int(n)))
+
+
+def fsp_bound_pool_bidir(inst: Instance, nodes, lb_out=None, stream=None, count=None):
+    """Bound bidirectional records (CUDA uint8 tensor [count, fsp_node_stride_bidir(n)]:
+    perm, d1 at byte n, d2 at byte n+1) into lb_out (CUDA int32 [count]).  Asynchronous."""
+    import torch
+    if count is None:
+        count = nodes.shape[0]
+    if lb_out is None:
+        lb_out = torch.empty(count, dtype=torch.int32, device=nodes.device)
+    if nodes.dtype != torch.uint8 or not nodes.is_cuda or not lb_out.is_cuda or lb_out.dtype != torch.int32:
+        raise ValueError("nodes must be a CUDA uint8 tensor and lb_out a CUDA int32 tensor")
+    if not nodes.is_contiguous() or not lb_out.is_contiguous():
+        raise ValueError("nodes and lb_out must be contiguous")
+    if count and (nodes.numel() < count * fsp_node_stride_bidir(inst.n) or lb_out.numel() < count):
+        raise ValueError("buffers smaller than count records")
+    _check(load().fsp_bound_pool_bidir(inst.handle, nodes.data_ptr(), int(count), lb_out.data_ptr(),
+                                       _stream(stream)))
+    return lb_out
+
+
 def fsp_check_status(inst: Instance, stream=None) -> None:
     _check(load().fsp_check_status(inst.handle, _stream(stream)))
 
@@ -278,7 +306,7 @@ _default_options = None  # fsp_default_options' struct, as bytes
 def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
              schedule=None, stream=None, init_nodes=None, init_count=None, max_iterations=0,
              out_nodes=None, profile=False, tune_window=0, schedule_out=None, model=None, topk=0,
-             log_nodes=None, log_lbs=None):
+             log_nodes=None, log_lbs=None, branching=0):
     global _default_options
     if _default_options is None:
         d = fsp_options()
@@ -287,6 +315,7 @@ def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, tra
     o = fsp_options.from_buffer_copy(_default_options)
     o.pool_size = int(pool_size)
     o.tune_window = int(tune_window)
+    o.branching = int(branching)
     if model is not None:
         o.order = ORDER_LEARNED
         o.model = model.handle
@@ -359,7 +388,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
               stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
               workspace=None, init_nodes=None, init_count=None, max_iterations: int = 0,
               out_nodes=None, profile: bool = False, tune_window: int = 0, schedule_cap: int = 0,
-              model=None, topk: int = 0, log_nodes=None, log_lbs=None):
+              model=None, topk: int = 0, log_nodes=None, log_lbs=None, branching: int = BRANCH_FORWARD):
     """Exact B&B on the device.  The scratch is a torch uint8 tensor (allocated
     here when `workspace` is None).  init_nodes (host array or device tensor of
     records) starts the search from that stack; out_nodes (host array or
@@ -372,7 +401,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     o, keep, trace, out_count = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap,
                                          schedule, stream, init_nodes, init_count, max_iterations,
                                          out_nodes, profile, tune_window, sched_out, model, topk, log_nodes,
-                                         log_lbs)
+                                         log_lbs, branching)
     nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
