@@ -240,11 +240,20 @@ def solve_times(fsp, budget=SOLVE_BUDGET):
         cap = SOLVE_BUDGETS.get((n, m, seed), budget)
         r = fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=pool, node_budget=cap)
         t2 = time.perf_counter()
-        out.append({"instance": f"{n}x{m} seed {seed}", "ub0": None if pool else ub0, "cmax": r["cmax"],
-                    "optimal": r["status"] == fsp.OK, "time_s": t2 - t0, "neh_s": t1 - t0, "search_s": t2 - t1,
-                    "node_budget": cap, "nodes_bounded": r["nodes_bounded"],
-                    "iterations": r["iterations"], "pool": r["tuned_pool"] if pool == 0 else pool,
-                    "warps_per_cta": r["tuned_warps"], "nodes_per_s": r["nodes_bounded"] / (t2 - t1)})
+        row = {"instance": f"{n}x{m} seed {seed}", "ub0": None if pool else ub0, "cmax": r["cmax"],
+               "optimal": r["status"] == fsp.OK, "time_s": t2 - t0, "neh_s": t1 - t0, "search_s": t2 - t1,
+               "node_budget": cap, "nodes_bounded": r["nodes_bounded"],
+               "iterations": r["iterations"], "pool": r["tuned_pool"] if pool == 0 else pool,
+               "warps_per_cta": r["tuned_warps"], "nodes_per_s": r["nodes_bounded"] / (t2 - t1)}
+        if pool == 0:  # the same solve with bidirectional branching (the ends alternate)
+            t3 = time.perf_counter()
+            b = fsp.fsp_solve(inst, ub0=ub0, ub0_perm=perm0, pool_size=0, node_budget=cap,
+                              branching=fsp.BRANCH_BIDIR)
+            t4 = time.perf_counter()
+            row["bidirectional"] = {"cmax": b["cmax"], "optimal": b["status"] == fsp.OK, "search_s": t4 - t3,
+                                    "time_s": t4 - t3 + (t1 - t0), "nodes_bounded": b["nodes_bounded"],
+                                    "pool": b["tuned_pool"], "nodes_per_s": b["nodes_bounded"] / (t4 - t3)}
+        out.append(row)
         inst.close()
     return out
 
@@ -395,6 +404,21 @@ def batch_solve(fsp):
     t_batch = time.perf_counter() - t1
     solved = sum(r["status"] == fsp.OK for r in res)
     nodes = sum(r["nodes_bounded"] for r in res)
+    # split mode: the roots' subtrees as work items, a shared UB per instance
+    B.set_split(True)
+    B.run()
+    B.results()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    B.run()
+    res_s = B.results()
+    t_split = time.perf_counter() - t1
+    B.set_split(False)
+    split = {"batch_s": t_split, "solved_in_batch": sum(r["status"] == fsp.OK for r in res_s),
+             "batch_nodes_bounded": sum(r["nodes_bounded"] for r in res_s),
+             "batch_nodes_per_s": sum(r["nodes_bounded"] for r in res_s) / t_split,
+             "same_optima": all(a["cmax"] == b["cmax"] for a, b in zip(res, res_s)
+                                if a["status"] == fsp.OK and b["status"] == fsp.OK)}
     t2 = time.perf_counter()
     finished, left_nodes = 0, 0
     for i, r in enumerate(res):
@@ -414,6 +438,7 @@ def batch_solve(fsp):
     B.close()
     return {"instances": BATCH_COUNT, "solved_in_batch": solved, "batch_s": t_batch,
             "batch_nodes_bounded": nodes, "batch_nodes_per_s": nodes / t_batch, "tune_s": t_tune,
+            "split": split,
             "node_budget_per_instance": BATCH_BUDGET, "leftovers": BATCH_COUNT - solved,
             "leftovers_finished": finished, "leftover_s": t_left, "leftover_nodes": left_nodes,
             "leftover_budget_each": LEFTOVER_BUDGET, "per_shape": per_shape}

@@ -415,6 +415,20 @@ int fsp_batch_run(fsp_batch *batch, void *stream);
  * (host or NULL, count x 255 int32: instance i's permutation at i*255; valid
  * when the UB came from NEH or improved). */
 int fsp_batch_results(fsp_batch *batch, fsp_batch_result *res, int32_t *perms, void *stream);
+/* Split mode (on != 0; off by default, and again with on = 0): the work
+ * queue holds the subtrees of the roots instead of whole instances -- for
+ * each instance (the ones with the most jobs first) the n subtrees whose
+ * schedules start with job 0, 1, ..., n-1 -- so idle CTAs take parts of the
+ * instances still being searched instead of waiting for them.  The CTAs
+ * working on an instance share its UB (an atomic minimum, read before every
+ * iteration) and its node count: the node budget then caps the instance's
+ * total.  Results: the optimum (status FSP_OK) and a schedule attaining
+ * cmax, like the whole-instance mode; the counters are the instance's
+ * totals over its subtrees, explored in another order than one stack's, so
+ * they differ from the whole-instance search's.  Re-captures the graph.
+ * Errors: FSP_ERR_ARG, FSP_ERR_OOM, FSP_ERR_CUDA. */
+int fsp_batch_set_split(fsp_batch *batch, int on);
+
 /* Pool size per shape on measured throughput (Algorithm 1's purpose, per
  * shape): up to 8 instances of each shape run with pools 128 .. 4096 under
  * probe_budget nodes each; the fastest pool (nodes bounded per second) is

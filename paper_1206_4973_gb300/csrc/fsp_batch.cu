@@ -11,6 +11,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <vector>
 
@@ -43,6 +44,18 @@ struct BatchWs {  // per-CTA scratch in global memory
     int32_t *lbs;
     long long cap;  // records per stack
     int stride_max;
+};
+
+// Split mode: the work items are (instance, first job) pairs, the subtrees of
+// the root; every CTA working on an instance shares its UB and counters.
+struct BatchSplit {
+    const int *item_inst, *item_job;  // per item
+    int items;
+    int *ub;                  // per instance: best makespan so far (atomicMin)
+    unsigned long long *key;  // per instance: (best makespan << 32) | item that found it, ~0 = none
+    long long *cnt;           // per instance: bounded, branched, pruned, leaves, iterations, updates
+    int *flags;               // per instance: 1 = a node budget stopped an item, 2 = a stack filled up
+    uint8_t *item_perm;       // per item: the best schedule it found (FSP_MAX_JOBS bytes)
 };
 
 __device__ __forceinline__ int b_block_incl_scan(int v, int *warp_tot)
@@ -112,9 +125,65 @@ __host__ __device__ inline size_t batch_smem_nm(int n, int m)
     return fsp_align16(family_smem_layout_nm(n, m, mp, m, nv, BB / 32).bytes) + (size_t)(POOL_MAX / 2 + 4) * 4;
 }
 
-template <int MT, int NV, int NW>
+// NEH upper bound: jobs by decreasing total time, each inserted at the
+// position of smallest partial makespan, earliest on ties; the sequence is
+// left in sh.seq.  All threads of the CTA call it.
+template <int MT>
+__device__ int b_neh(const int32_t *__restrict__ p, int n, BatchShared &sh)
+{
+    const int tid = threadIdx.x;
+    uint8_t *seq = sh.seq, *ord = sh.ord;
+    int32_t *tot = sh.tot;
+    unsigned long long &best_key = sh.best_key;
+    for (int j = tid; j < n; j += BB) {
+        int32_t s = 0;
+        for (int k = 0; k < MT; ++k) s += p[j * MT + k];
+        tot[j] = s;
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += BB) {
+        int rank = 0;
+        for (int i = 0; i < n; ++i) rank += (tot[i] > tot[j]) || (tot[i] == tot[j] && i < j);
+        ord[rank] = (uint8_t)j;
+    }
+    __syncthreads();
+    for (int len = 0; len < n; ++len) {
+        const int job = ord[len];
+        if (tid == 0) best_key = ~0ull;
+        __syncthreads();
+        for (int pos = tid; pos <= len; pos += BB) {
+            int32_t C[MT];
+#pragma unroll
+            for (int k = 0; k < MT; ++k) C[k] = 0;
+            for (int i = 0; i <= len; ++i) {
+                const int j = i < pos ? seq[i] : (i == pos ? job : seq[i - 1]);
+                C[0] += p[j * MT];
+#pragma unroll
+                for (int k = 1; k < MT; ++k) C[k] = max(C[k], C[k - 1]) + p[j * MT + k];
+            }
+            atomicMin(&best_key, ((unsigned long long)(uint32_t)C[MT - 1] << 32) | (unsigned)pos);
+        }
+        __syncthreads();
+        const int at = (int)(best_key & 0xffffffffu);
+        if (tid == 0) {
+            for (int i = len; i > at; --i) seq[i] = seq[i - 1];
+            seq[at] = (uint8_t)job;
+        }
+        __syncthreads();
+    }
+    const int ub = (int)(best_key >> 32);
+    __syncthreads();
+    return ub;
+}
+
+// One instance's search (whole instance), or (SPLIT) the subtree of the
+// root whose schedule starts with job `job`, sharing the instance's UB and
+// counters with the other CTAs; tables_ready: this CTA's shared memory
+// already holds the instance's tables.
+template <int MT, int NV, int NW, bool SPLIT>
 __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, BatchOut *out, uint8_t *perm_out,
-                        const BatchWs &W, unsigned char *smem, BatchShared &sh)
+                        const BatchWs &W, unsigned char *smem, BatchShared &sh, const BatchSplit &X, int inst,
+                        int item, int job, bool tables_ready)
 {
     const int n = D.n, tid = threadIdx.x;
     const int P = MT * (MT - 1) / 2, mp = (MT % 2 == 0) ? MT + 1 : MT;
@@ -129,6 +198,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
     unsigned long long &best_key = sh.best_key;
 
     // tables: {p, tail} rows and the Johnson entries of every pair
+    if (!SPLIT || !tables_ready) {
     for (int i = tid; i < n * MT; i += BB) {
         const int j = i / MT, k = i - j * MT;
         int32_t q = 0;
@@ -154,48 +224,14 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
     }
     __syncthreads();
     fam_tables_finish<MT>(V, n, mp);
+    }
 
-    // NEH upper bound (unless given): jobs by decreasing total time, each
-    // inserted at the position of smallest partial makespan, earliest on ties
+    // the UB: NEH unless given (whole instances), or the instance's shared UB (split)
     int ub = D.ub0;
-    if (ub <= 0) {
-        for (int j = tid; j < n; j += BB) {
-            int32_t s = 0;
-            for (int k = 0; k < MT; ++k) s += p[j * MT + k];
-            tot[j] = s;
-        }
-        __syncthreads();
-        for (int j = tid; j < n; j += BB) {
-            int rank = 0;
-            for (int i = 0; i < n; ++i) rank += (tot[i] > tot[j]) || (tot[i] == tot[j] && i < j);
-            ord[rank] = (uint8_t)j;
-        }
-        __syncthreads();
-        for (int len = 0; len < n; ++len) {
-            const int job = ord[len];
-            if (tid == 0) best_key = ~0ull;
-            __syncthreads();
-            for (int pos = tid; pos <= len; pos += BB) {
-                int32_t C[MT];
-#pragma unroll
-                for (int k = 0; k < MT; ++k) C[k] = 0;
-                for (int i = 0; i <= len; ++i) {
-                    const int j = i < pos ? seq[i] : (i == pos ? job : seq[i - 1]);
-                    C[0] += p[j * MT];
-#pragma unroll
-                    for (int k = 1; k < MT; ++k) C[k] = max(C[k], C[k - 1]) + p[j * MT + k];
-                }
-                atomicMin(&best_key, ((unsigned long long)(uint32_t)C[MT - 1] << 32) | (unsigned)pos);
-            }
-            __syncthreads();
-            const int at = (int)(best_key & 0xffffffffu);
-            if (tid == 0) {
-                for (int i = len; i > at; --i) seq[i] = seq[i - 1];
-                seq[at] = (uint8_t)job;
-            }
-            __syncthreads();
-        }
-        ub = (int)(best_key >> 32);
+    if (SPLIT) {
+        ub = *(volatile int *)&X.ub[inst];
+    } else if (ub <= 0) {
+        ub = b_neh<MT>(p, n, sh);
         for (int i = tid; i < n; i += BB) inc[i] = seq[i];
     }
     __syncthreads();
@@ -204,12 +240,32 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
     long long bounded = 0, branched = 0, pruned = 0, leaves = 0, iters = 0, updates = 0;
     int status = FSP_OK;
     long long S = 1;
-    for (int i = tid; i < stride; i += BB) W.stack[i] = (uint8_t)(i < n ? i : 0);
+    if (SPLIT && job >= 0) {  // the root's child that schedules `job` first (the rest in increasing order)
+        for (int i = tid; i < stride; i += BB)
+            W.stack[i] = (uint8_t)(i == 0 ? job : i < n ? (i - 1 < job ? i - 1 : i) : i == n ? 1 : 0);
+    } else {
+        for (int i = tid; i < stride; i += BB) W.stack[i] = (uint8_t)(i < n ? i : 0);
+    }
+    bool improved = false;
+    __shared__ int s_ub;
     __syncthreads();
     const int pool = D.pool;
     const int warp = tid >> 5, lane = tid & 31;
     while (S > 0) {
-        if (D.budget > 0 && bounded >= D.budget) { status = FSP_INCOMPLETE; break; }
+        if (SPLIT) {  // the instance's UB and node count, as the other CTAs left them
+            if (tid == 0) {
+                s_ub = min(ub, *(volatile int *)&X.ub[inst]);
+                if (D.budget > 0 && *(volatile long long *)&X.cnt[6 * inst] >= D.budget) s_ub = -1;
+            }
+            __syncthreads();
+            const int u = s_ub;
+            __syncthreads();
+            if (u < 0) { status = FSP_INCOMPLETE; break; }
+            ub = u;
+        } else if (D.budget > 0 && bounded >= D.budget) {
+            status = FSP_INCOMPLETE;
+            break;
+        }
         // selection: deepest parents while their children fit (at least one)
         const long long cand = S < pool ? S : pool;
         long long running = 0, np = 0;
@@ -259,6 +315,13 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
             const long long idx = (long long)(bk & 0xffffffffull);
             for (int i = tid; i < n; i += BB) inc[i] = W.children[idx * stride + i];
             updates++;
+            if (SPLIT) {
+                improved = true;
+                if (tid == 0) {
+                    atomicMin(&X.ub[inst], ub_new);
+                    atomicMin(&X.key[inst], ((unsigned long long)(uint32_t)ub_new << 32) | (unsigned)item);
+                }
+            }
         }
         ub = ub_new;
         // elimination: survivors (non-leaf, bound < UB), pushed in reverse order
@@ -289,7 +352,24 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         leaves += nleaf;
         pruned += nch - nleaf - total;
         iters++;
+        if (SPLIT && tid == 0) atomicAdd((unsigned long long *)&X.cnt[6 * inst], (unsigned long long)nch);
         __syncthreads();
+    }
+    if (SPLIT) {  // this item's share of the counters, its flags and its best schedule
+        if (tid == 0) {
+            unsigned long long *c = (unsigned long long *)&X.cnt[6 * inst];
+            atomicAdd(c + 1, (unsigned long long)branched);
+            atomicAdd(c + 2, (unsigned long long)pruned);
+            atomicAdd(c + 3, (unsigned long long)leaves);
+            atomicAdd(c + 4, (unsigned long long)iters);
+            atomicAdd(c + 5, (unsigned long long)updates);
+            if (status == FSP_INCOMPLETE) atomicOr(&X.flags[inst], 1);
+            if (status == FSP_ERR_CAPACITY) atomicOr(&X.flags[inst], 2);
+        }
+        if (improved)
+            for (int i = tid; i < n; i += BB) X.item_perm[(size_t)item * FSP_MAX_JOBS + i] = inc[i];
+        __syncthreads();
+        return;
     }
     if (tid == 0) {
         out->cmax = ub;
@@ -326,11 +406,104 @@ __global__ void __launch_bounds__(BB) k_batch(const BatchDesc *__restrict__ desc
         const int32_t *p = p_flat + D.p_off;
         const int nv = (D.n + 1 + 15) / 16, nw = D.n <= 32 ? 1 : 2;
         uint8_t *po = perms + (size_t)i * FSP_MAX_JOBS;
-#define B_CASE(MT_, NV_, NW_) \
-    if (D.m == MT_ && nv == NV_ && nw == NW_) { b_solve<MT_, NV_, NW_>(p, D, out + i, po, w, smem, sh); continue; }
+#define B_CASE(MT_, NV_, NW_)                                                                          \
+    if (D.m == MT_ && nv == NV_ && nw == NW_) {                                                        \
+        b_solve<MT_, NV_, NW_, false>(p, D, out + i, po, w, smem, sh, BatchSplit{}, i, 0, 0, false);   \
+        continue;                                                                                      \
+    }
         FSP_SHAPES_BATCH(B_CASE)
 #undef B_CASE
         if (threadIdx.x == 0) out[i].status = FSP_ERR_ARG;  // shape without a kernel (checked on the host)
+    }
+}
+
+// Split mode, before the items: each instance's UB (NEH unless given), its
+// NEH schedule as the permutation to report if no item improves on it, and
+// its shared counters cleared.  One CTA per instance.
+__global__ void __launch_bounds__(BB) k_batch_split_init(const BatchDesc *__restrict__ desc,
+                                                         const int32_t *__restrict__ p_flat, uint8_t *perms,
+                                                         BatchSplit X)
+{
+    __shared__ BatchShared sh;
+    const int i = blockIdx.x;
+    const BatchDesc D = desc[i];
+    const int32_t *p = p_flat + D.p_off;
+    int ub = D.ub0;
+    if (ub <= 0) {
+        ub = D.m == 5 ? b_neh<5>(p, D.n, sh) : D.m == 10 ? b_neh<10>(p, D.n, sh) : b_neh<20>(p, D.n, sh);
+        for (int j = threadIdx.x; j < D.n; j += BB) perms[(size_t)i * FSP_MAX_JOBS + j] = sh.seq[j];
+    }
+    if (threadIdx.x == 0) {
+        X.ub[i] = ub;
+        X.key[i] = ~0ull;
+        X.flags[i] = 0;
+        for (int k = 0; k < 6; ++k) X.cnt[6 * i + k] = 0;
+    }
+}
+
+// Split mode: the persistent kernel over the work items; a CTA keeps the
+// tables of the instance it last worked on (the items of an instance are
+// consecutive in the queue).
+__global__ void __launch_bounds__(BB) k_batch_split(const BatchDesc *__restrict__ desc,
+                                                    const int32_t *__restrict__ p_flat, int *queue, BatchWs W,
+                                                    BatchSplit X)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    __shared__ BatchShared sh;
+    BatchWs w = W;
+    w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
+    w.children = W.children + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS) * W.stride_max;
+    w.lbs = W.lbs + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS);
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= X.items) break;
+        const int i = X.item_inst[item], job = X.item_job[item];
+        const BatchDesc D = desc[i];
+        const int32_t *p = p_flat + D.p_off;
+        const int nv = (D.n + 1 + 15) / 16, nw = D.n <= 32 ? 1 : 2;
+        const bool ready = cur == i;
+        cur = i;
+#define B_CASE(MT_, NV_, NW_)                                                                   \
+    if (D.m == MT_ && nv == NV_ && nw == NW_) {                                                 \
+        b_solve<MT_, NV_, NW_, true>(p, D, nullptr, nullptr, w, smem, sh, X, i, item, job, ready); \
+        continue;                                                                               \
+    }
+        FSP_SHAPES_BATCH(B_CASE)
+#undef B_CASE
+        cur = -1;
+    }
+}
+
+// Split mode, after the items: each instance's result from its shared state.
+__global__ void k_batch_split_finish(const BatchDesc *__restrict__ desc, int count, BatchOut *out, uint8_t *perms,
+                                     BatchSplit X)
+{
+    const int i = blockIdx.x;
+    if (i >= count) return;
+    const unsigned long long key = X.key[i];
+    if (key != ~0ull) {
+        const int item = (int)(key & 0xffffffffull);
+        for (int j = threadIdx.x; j < desc[i].n; j += blockDim.x)
+            perms[(size_t)i * FSP_MAX_JOBS + j] = X.item_perm[(size_t)item * FSP_MAX_JOBS + j];
+    }
+    if (threadIdx.x == 0) {
+        BatchOut o;
+        o.cmax = X.ub[i];
+        o.status = (X.flags[i] & 2) ? FSP_ERR_CAPACITY : (X.flags[i] & 1) ? FSP_INCOMPLETE : FSP_OK;
+        o.ub0 = 0;
+        o.pad = 0;
+        o.bounded = X.cnt[6 * i];
+        o.branched = X.cnt[6 * i + 1];
+        o.pruned = X.cnt[6 * i + 2];
+        o.leaves = X.cnt[6 * i + 3];
+        o.iterations = X.cnt[6 * i + 4];
+        o.updates = X.cnt[6 * i + 5];
+        out[i] = o;
     }
 }
 
@@ -348,6 +521,9 @@ struct fsp_batch {
     std::vector<BatchDesc> desc;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
+    bool split = false;
+    BatchSplit X{};
+    int *d_item = nullptr;  // item instances, then item jobs
 };
 
 static bool batch_shape_ok(int n, int m)
@@ -368,6 +544,8 @@ static void batch_free(fsp_batch *B)
     if (B->graph) cudaGraphDestroy(B->graph);
     cudaFree(B->d_desc); cudaFree(B->d_p); cudaFree(B->d_out); cudaFree(B->d_perms); cudaFree(B->d_queue);
     cudaFree(B->ws.stack); cudaFree(B->ws.children); cudaFree(B->ws.lbs);
+    cudaFree(B->d_item); cudaFree(B->X.ub); cudaFree(B->X.key); cudaFree(B->X.cnt); cudaFree(B->X.flags);
+    cudaFree(B->X.item_perm);
     delete B;
 }
 
@@ -379,8 +557,13 @@ static int batch_capture(fsp_batch *B)
     FSP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !B->split) {
         k_batch<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->count, B->d_p, B->d_out, B->d_perms, B->d_queue, B->ws);
+        e = cudaGetLastError();
+    } else if (e == cudaSuccess) {
+        k_batch_split_init<<<B->count, BB, 0, st>>>(B->d_desc, B->d_p, B->d_perms, B->X);
+        k_batch_split<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->d_p, B->d_queue, B->ws, B->X);
+        k_batch_split_finish<<<B->count, 64, 0, st>>>(B->d_desc, B->count, B->d_out, B->d_perms, B->X);
         e = cudaGetLastError();
     }
     cudaGraph_t g = nullptr;
@@ -447,6 +630,8 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
             goto fail;
         }
         TRYB(cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
+        TRYB(cudaFuncSetAttribute((const void *)k_batch_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)B->smem));
         int per_sm = 0;
         TRYB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BB, B->smem));
         B->grid = B->sm_count * (per_sm > 0 ? per_sm : 1);
@@ -471,6 +656,42 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
 fail:
     batch_free(B);
     return rc;
+}
+
+extern "C" int fsp_batch_set_split(fsp_batch *B, int on)
+{
+    if (!B) { fsp_set_error("fsp_batch_set_split: NULL batch"); return FSP_ERR_ARG; }
+    if (on && !B->d_item) {
+        // the work items, the instances with the most jobs (the longest searches) first
+        std::vector<int> order(B->count);
+        for (int i = 0; i < B->count; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (long long)B->desc[a].n * B->desc[a].m > (long long)B->desc[b].n * B->desc[b].m;
+        });
+        std::vector<int> inst, job;
+        for (int i : order) {
+            if (B->desc[i].n <= 2) {  // the root's children are complete schedules: one item, the root
+                inst.push_back(i);
+                job.push_back(-1);
+                continue;
+            }
+            for (int j = 0; j < B->desc[i].n; ++j) { inst.push_back(i); job.push_back(j); }
+        }
+        const int items = (int)inst.size();
+        FSP_CUDA(cudaMalloc(&B->d_item, sizeof(int) * 2 * (size_t)items));
+        FSP_CUDA(cudaMemcpy(B->d_item, inst.data(), sizeof(int) * items, cudaMemcpyHostToDevice));
+        FSP_CUDA(cudaMemcpy(B->d_item + items, job.data(), sizeof(int) * items, cudaMemcpyHostToDevice));
+        FSP_CUDA(cudaMalloc(&B->X.ub, sizeof(int) * B->count));
+        FSP_CUDA(cudaMalloc(&B->X.key, sizeof(unsigned long long) * B->count));
+        FSP_CUDA(cudaMalloc(&B->X.cnt, sizeof(long long) * 6 * B->count));
+        FSP_CUDA(cudaMalloc(&B->X.flags, sizeof(int) * B->count));
+        FSP_CUDA(cudaMalloc(&B->X.item_perm, (size_t)FSP_MAX_JOBS * items));
+        B->X.item_inst = B->d_item;
+        B->X.item_job = B->d_item + items;
+        B->X.items = items;
+    }
+    B->split = on != 0;
+    return batch_capture(B);
 }
 
 extern "C" void fsp_batch_destroy(fsp_batch *B)

@@ -93,3 +93,39 @@ def test_pool_tuning_per_shape(F):
         for j in range(16):
             if shapes[i][:2] == shapes[j][:2]:
                 assert pools[i] == pools[j]
+
+
+def test_split_mode_reaches_the_same_optima(F):
+    """Split mode (the roots' subtrees as work items, a shared UB per
+    instance): every instance solved to optimality gives the oracle's
+    optimum and a schedule attaining it; counters are totals over the
+    subtrees (another exploration order), so only their consistency is
+    checked."""
+    shapes = [(9, 5, 1), (10, 10, 2), (12, 5, 4), (7, 5, 5), (11, 10, 6), (2, 5, 7), (3, 10, 8), (12, 5, 9),
+              (10, 5, 10), (9, 10, 11)] + list(inputs.batch_shapes(12, first_seed=100)[:8])
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    k = len(instances)
+    pools = np.array([(64, 256, 1024, 7)[i % 4] for i in range(k)], np.int64)
+    budgets = np.zeros(k, np.int64)
+    budgets[-8:] = 400000  # the 20- and 50-job shapes: capped, checked for consistency only
+    whole = F.Batch(instances, pools, budgets)
+    whole.run()
+    ref = whole.results()
+    B = F.Batch(instances, pools, budgets, split=True)
+    for _ in range(2):  # the graph replays from scratch
+        B.run()
+        res = B.results()
+        for i, (p, r, w) in enumerate(zip(instances, res, ref)):
+            assert r["status"] in (F.OK, F.INCOMPLETE), i
+            assert oracle.makespan(p, r["perm"]) == r["cmax"], i
+            assert r["nodes_bounded"] >= r["nodes_pruned"] + r["leaves"], i  # the rest survived
+            if r["status"] == F.OK and p.shape[0] <= 12:  # small enough for the serial oracle
+                best = oracle.solve(p, pool=4096)["cmax"] if p.shape[0] > 9 else oracle.bruteforce(p)[0]
+                assert r["cmax"] == best, i
+            if r["status"] == F.OK and w["status"] == F.OK:  # the whole-instance search equals the oracle's
+                assert r["cmax"] == w["cmax"], i
+            if budgets[i] == 0:
+                assert r["status"] == F.OK, i
+    B.set_split(False)  # back to whole instances: the bit-exact search
+    B.run()
+    check(F, instances, B.results(), pools, budgets)
