@@ -55,7 +55,7 @@ __device__ __forceinline__ void fam_fetch(const SolveWs &ws, long long S, int st
     asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
 
-template <int MT, int NV, bool LRN, bool HEADS>
+template <int MT, int NV, bool LRN, bool HEADS, bool BIDIR>
 __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst I, SolveWs ws, FamSmem L)
 {
     constexpr int P = MT * (MT - 1) / 2;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         if (lane == 0) fn = (int)atomicAdd(next_f, 1ull);
         fn = __shfl_sync(0xffffffffu, fn, 0);
         if (fn < np) fam_fetch<NV>(ws, S, stride, fn, lane, V.recb + (buf ^ 1) * 16 * NV, V.pofs + (buf ^ 1));
-        fam_bound<MT, NV, LRN, HEADS>(V, rec_s, c0, n, mp, stride, ub_iter, ws.children, ws.lbs,
+        fam_bound<MT, NV, LRN, HEADS, BIDIR>(V, rec_s, c0, n, mp, stride, ub_iter, ws.children, ws.lbs,
                                       &ws.ctl->best_key, LRN ? ws.topk + (long long)f * L.K : nullptr, L.K,
                                       reinterpret_cast<unsigned long long *>(&ws.ctl->early));
         __syncwarp();
@@ -108,12 +108,16 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
     }
 }
 
-BranchFamilyFn pick_branch_family(int mt, int nv, bool learned, bool heads)
+BranchFamilyFn pick_branch_family(int mt, int nv, bool learned, bool heads, bool bidir)
 {
-#define FSP_CASEF(MT_, NV_)                                                                          \
-    if (mt == MT_ && nv == NV_)                                                                      \
-        return learned ? (heads ? &k_branch_family<MT_, NV_, true, true> : &k_branch_family<MT_, NV_, true, false>) \
-                       : (heads ? &k_branch_family<MT_, NV_, false, true> : &k_branch_family<MT_, NV_, false, false>);
+#define FSP_CASEF(MT_, NV_)                                                                                  \
+    if (mt == MT_ && nv == NV_) {                                                                            \
+        if (bidir) return (learned || heads) ? nullptr : &k_branch_family<MT_, NV_, false, false, true>;    \
+        return learned ? (heads ? &k_branch_family<MT_, NV_, true, true, false>                              \
+                                : &k_branch_family<MT_, NV_, true, false, false>)                            \
+                       : (heads ? &k_branch_family<MT_, NV_, false, true, false>                             \
+                                : &k_branch_family<MT_, NV_, false, false, false>);                          \
+    }
     FSP_SHAPES_FAMILY(FSP_CASEF)
 #undef FSP_CASEF
     return nullptr;

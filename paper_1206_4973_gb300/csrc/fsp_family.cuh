@@ -39,7 +39,7 @@ struct FamMask<2> {
 // the list of pairs still to evaluate.
 struct FamSmem {
     size_t we_off, rk8_off, en_off, gam_off, klm_off, pq_off, warp_off, warp_bytes, bytes;
-    size_t w_ps, w_psa, w_pp, w_ab, w_rec, w_pofs, w_cc, w_sq, w_lb, w_T, w_lkl, w_lm;
+    size_t w_ps, w_psa, w_pp, w_ab, w_pd, w_rec, w_pofs, w_cc, w_sq, w_lb, w_T, w_lkl, w_lm;
     int rks8, mtp, warps;
     int K;  // learned order: predicted pairs per parent
 };
@@ -73,6 +73,7 @@ __host__ __device__ inline FamSmem family_smem_layout_nm(int n, int m, int mp, i
     L.w_psa = w; w += fsp_align16((size_t)MT * 4);
     L.w_pp = w; w += (size_t)MT * 16;
     L.w_ab = w; w += fsp_align16((size_t)MT * 8);
+    L.w_pd = w; w += fsp_align16((size_t)MT * 4);
     L.w_rec = w; w += 32 * (size_t)NV;
     L.w_pofs = w; w += 16;
     L.w_cc = w; w += fsp_align16((size_t)n * L.mtp * 4);  // a family has at most n children
@@ -99,7 +100,7 @@ int fam_bound_pool(fsp_instance *I, int mt, int nv, const uint8_t *nodes, long l
 #define FAM_POOL_SMALL 16384  // fsp_bound_pool uses one warp per node up to this many nodes
 
 typedef void (*BranchFamilyFn)(DevInst, SolveWs, FamSmem);
-BranchFamilyFn pick_branch_family(int mt, int nv, bool learned, bool heads);
+BranchFamilyFn pick_branch_family(int mt, int nv, bool learned, bool heads, bool bidir = false);
 
 // One warp's view of the family shared memory.
 struct FamView {
@@ -110,7 +111,7 @@ struct FamView {
     uint16_t *klm;
     int2 *pq;
     int4 *ps, *pp;
-    int32_t *psa, *ab, *cc, *sq, *lbv, *T, *lm;
+    int32_t *psa, *ab, *pd, *cc, *sq, *lbv, *T, *lm;
     uint16_t *lkl;
     uint8_t *recb;
     long long *pofs;
@@ -131,6 +132,7 @@ __device__ __forceinline__ FamView fam_view(unsigned char *smem, const FamSmem &
     V.psa = reinterpret_cast<int32_t *>(wb + L.w_psa);
     V.pp = reinterpret_cast<int4 *>(wb + L.w_pp);  // heads variant: smallest p per machine
     V.ab = reinterpret_cast<int32_t *>(wb + L.w_ab);  // alpha[MT], beta[MT]
+    V.pd = reinterpret_cast<int32_t *>(wb + L.w_pd);  // bidirectional: the suffix's delivery times
     V.recb = wb + L.w_rec;                            // two record buffers
     V.pofs = reinterpret_cast<long long *>(wb + L.w_pofs);  // and the running counts below them
     V.cc = reinterpret_cast<int32_t *>(wb + L.w_cc);
@@ -193,6 +195,30 @@ __device__ __forceinline__ void fam_make_child(const FspRec<NV> &par, int n, int
     }
 }
 
+// Record of the child of a bidirectional parent (prefix d1, suffix starting
+// at byte e = n - d2) that puts its remaining job of rank ci, c, in front of
+// the suffix: the bytes in [d1 + ci, e - 1) are the parent's shifted down by
+// one, byte e - 1 is c and the suffix length byte n + 1 grows by one.
+template <int NV>
+__device__ __forceinline__ void fam_make_child_back(const FspRec<NV> &par, int n, int d1, int e, int ci, int c,
+                                                    FspRec<NV> &ch)
+{
+#pragma unroll
+    for (int q = 0; q < 4 * NV; ++q) {
+        const uint32_t w = par.w[q];
+        const uint32_t sh = __funnelshift_r(w, q + 1 < 4 * NV ? par.w[q + 1] : 0u, 8);
+        const int lo = min(max(d1 + ci - 4 * q, 0), 4), hi = min(max(e - 1 - 4 * q, 0), 4);
+        const uint32_t mlo = lo >= 4 ? 0xFFFFFFFFu : (1u << (8 * lo)) - 1u;
+        const uint32_t mhi = hi >= 4 ? 0xFFFFFFFFu : (1u << (8 * hi)) - 1u;
+        const uint32_t m = mhi & ~mlo;
+        uint32_t x = (w & ~m) | (sh & m);
+        const int be = e - 1 - 4 * q;
+        if (be >= 0 && be < 4) x = (x & ~(0xFFu << (8 * be))) | ((uint32_t)c << (8 * be));
+        if (((n + 1) >> 2) == q) x += 1u << (8 * ((n + 1) & 3));
+        ch.w[q] = x;
+    }
+}
+
 // p[job at prefix position t - lane][k], or 0 outside the prefix
 __device__ __forceinline__ int32_t fam_prefix_p(int t, int lane, int d, int k, int mp,
                                                 const uint8_t *__restrict__ rec_s, const int2 *__restrict__ pq_s)
@@ -212,7 +238,17 @@ __device__ __forceinline__ int32_t fam_prefix_p(int t, int lane, int d, int k, i
 // child is left do the certification and the remaining pairs run, for the
 // children left.  A cut child keeps its partial bound (>= the UB); the
 // others get the exact bound, so the search is the plain one.
-template <int MT, int NV, bool LRN, bool HEADS>
+// BIDIR: bidirectional records (prefix d1 at byte n, suffix d2 at byte n+1,
+// the remaining set between them); the family's direction is forward when
+// d1 <= d2, else backward (its children put a job in front of the suffix).
+// Both directions remove the same job c from the remaining set, so the pair
+// terms X_c and the certification are those of the forward family; only the
+// one-machine quantities differ: a forward child's release times advance by c
+// and its tail after machine k is max(D_k, qmin_k) with the parent's delivery
+// times D; a backward child keeps the parent's release times and its delivery
+// times advance by c.  A child with one job left gets its completion's
+// makespan, max_k (C''_k + D'_k) with C'' its release times after that job.
+template <int MT, int NV, bool LRN, bool HEADS, bool BIDIR = false>
 __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s, long long c0, int n, int mp,
                                           int stride, int ub_iter, uint8_t *children, int32_t *lbs,
                                           unsigned long long *best_key, const int16_t *topk_row, int K,
@@ -244,14 +280,18 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
         par.w[4 * v + 3] = x.w;
     }
     const int d = rec_s[n];
-    const int r = n - d;
+    const int d2 = BIDIR ? rec_s[n + 1] : 0;
+    const int e = n - d2;  // the remaining set: positions [d, e)
+    const int r = e - d;
+    const bool fwd = !BIDIR || d <= d2;
+    int32_t *pd = V.pd;
 
         // -- parent state on machine k = lane: remaining sum, smallest and
         // second smallest tail (and a job attaining the smallest), release time
         {
             const int k = lane < MT ? lane : MT - 1;
             int32_t Sk = 0, Q1 = 0x7fffffff, Q2 = 0x7fffffff, A = 0;
-            for (int i = d; i < n; ++i) {
+            for (int i = d; i < e; ++i) {
                 const int j = rec_s[i];
                 const int2 v = pq_s[j * mp + k];
                 Sk += v.x;
@@ -279,9 +319,21 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 ps[lane] = make_int4(Ck, Sk, Q1, Q2);
                 psa[lane] = A;
             }
+            if (BIDIR) {
+                // delivery times of the suffix: lane k takes the suffix job t - (MT-1-k)
+                // from the last at step t, after lane k+1 has finished it on machine k+1
+                int32_t Dk = 0;
+                for (int t = 0; t < d2 + MT - 1; ++t) {
+                    int32_t down = __shfl_down_sync(0xffffffffu, Dk, 1);
+                    if (lane == MT - 1) down = 0;
+                    const int si = t - (MT - 1 - lane);
+                    if (lane < MT && si >= 0 && si < d2) Dk = max(Dk, down) + pq_s[rec_s[n - 1 - si] * mp + k].x;
+                }
+                if (lane < MT) pd[lane] = Dk;
+            }
             if (heads) {  // smallest and second smallest p on machine k, and a job attaining it
                 int32_t P1 = 0x7fffffff, P2 = 0x7fffffff, AP = 0;
-                for (int i = d; i < n; ++i) {
+                for (int i = d; i < e; ++i) {
                     const int j = rec_s[i];
                     const int32_t v = pq_s[j * mp + k].x;
                     if (v < P1) { P2 = P1; P1 = v; AP = j; }
@@ -296,6 +348,44 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
         for (int ci = lane; ci < r; ci += 32) {
             const int c = rec_s[d + ci];
             const int2 *prow = pq_s + c * mp;
+            if (BIDIR) {
+                int32_t lb = 0;
+                // the child's delivery times: the parent's (forward), or advanced by
+                // c from machine m-1 down (backward; parked in the child's sq row)
+                int32_t *dc = fwd ? pd : sq + ci * mtp;
+                if (!fwd) {
+                    int32_t nxt = 0;
+#pragma unroll
+                    for (int k = MT - 1; k >= 0; --k) {
+                        nxt = max(pd[k], nxt) + prow[k].x;
+                        dc[k] = nxt;
+                    }
+                }
+                int32_t prev = 0, cm = 0, best = 0;
+                const int2 *jrow = pq_s + rec_s[d + (r == 2 ? 1 - ci : 0)] * mp;  // the last job (r == 2)
+#pragma unroll
+                for (int k = 0; k < MT; ++k) {
+                    const int4 st = ps[k];
+                    const int32_t px = prow[k].x;
+                    const int32_t ck = fwd ? max(st.x, prev) + px : st.x;
+                    prev = ck;
+                    const int32_t dk = dc[k];
+                    const int32_t qm = psa[k] == c ? st.w : st.z;  // smallest tail over U \ {c}
+                    const int32_t sqk = st.y - px + max(dk, qm == 0x7fffffff ? 0 : qm);
+                    cm = max(ck, cm) + jrow[k].x;  // one job left: its completion's release times
+                    best = max(best, cm + dk);
+                    cc[ci * mtp + k] = ck;
+                    sq[ci * mtp + k] = sqk;
+                    lb = max(lb, ck + sqk);
+                }
+                if (r == 2) lb = best;  // one job left: the makespan of the child's completion
+                lbv[ci] = lb;
+                FspRec<NV> ch;
+                if (fwd) fam_make_child<NV>(par, n, d, ci, c, ch);
+                else fam_make_child_back<NV>(par, n, d, e, ci, c, ch);
+                fsp_store_rec(ch, children + (c0 + ci) * stride);
+                continue;
+            }
             int32_t lb = 0, prev = 0, rprev = 0;
 #pragma unroll
             for (int k = 0; k < MT; ++k) {
@@ -332,7 +422,7 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                     const int kl = lkl[b0 + lane];
                     Mask pm = 0;
 #pragma unroll 4
-                    for (int i = d; i < n; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
+                    for (int i = d; i < e; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
                     // every lane at the same position (position-major rows and
                     // the lane's own T column: no bank conflicts); a member
                     // updates the running values, T is read at members only.
@@ -388,7 +478,7 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 const int kl = lkl[lane];
                 Mask pm = 0;
 #pragma unroll 4
-                for (int i = d; i < n; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
+                for (int i = d; i < e; ++i) pm |= (Mask)1 << rk8[kl * rks8 + rec_s[i]];
                 int32_t E = 0, M = FSP_NEG;
                 Mask bit = 1;
 #pragma unroll 2
@@ -425,7 +515,7 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
             return __any_sync(0xffffffffu, any);
         };
 
-        const bool leaves = d + 1 == n - 1;
+        const bool leaves = r == 2;  // the children have one job left: complete schedules
         bool open = !leaves;
         if (LRN) {
             if (open) open = open_any();
@@ -469,7 +559,7 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                     M[s] = FSP_NEG;
                 }
 #pragma unroll 4
-                for (int i = d; i < n; ++i) {
+                for (int i = d; i < e; ++i) {
                     const int j = rec_s[i];
 #pragma unroll
                     for (int s = 0; s < NS; ++s) pm[s] |= (Mask)1 << rk8[klc[s] * rks8 + j];

@@ -932,6 +932,20 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
         P->blist = nullptr;
         P->list_grid = 0;
         P->per_cta = 256;
+        // the family kernel with bidirectional records where its tables fit
+        // (FSP_FAMILY=0: children, the pool bound and the leaf pass, one by one)
+        const int mt = fsp_mt(I->m), nv = P->rs / 16;
+        const char *ev = getenv("FSP_FAMILY");
+        const int w = (mt == 0 || nv > 4 || (ev && ev[0] == '0')) ? 0 : family_warps(I, mt, nv);
+        if (w > 0 && (P->bf = pick_branch_family(mt, nv, false, false, true)) != nullptr) {
+            P->famL = family_smem_layout(I, mt, nv, w);
+            P->famL.K = 0;
+            const int cand[3] = {4, 8, 12};
+            for (int c = 0; c < 3; ++c)
+                if (cand[c] < w) P->famC[P->nfam++] = family_smem_layout(I, mt, nv, cand[c]);
+            P->famC[P->nfam++] = P->famL;
+            if ((rc = fsp_allow_smem(I, (const void *)P->bf, P->famL.bytes)) != FSP_OK) return rc;
+        }
         if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
             fsp_set_error("fsp_solve: workspace must be 256-byte aligned");
             return FSP_ERR_ARG;
@@ -1131,7 +1145,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, rs, pool, o.node_budget, o.max_iterations,
                                              P->bf == nullptr);
             if (prof) LTRY(cudaEventRecord(pe[1], st));
-            if (P->bidir) {  // children, their bounds, then the exact values of the complete ones
+            if (P->bidir && !P->bf) {  // children, their bounds, then the exact values of the complete ones
                 const long long mc = pool + I->n;
                 bidir_launch_children(ws, I->n, rs, mc, st);
                 const int brc = bidir_bound(I, ws.children, mc, &ws.ctl->n_children, ws.lbs, st);
@@ -1168,7 +1182,9 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 const FamSmem &FL = P->famC[fam_i];
                 const long long fam = (pool / 2 + 1 + FL.warps - 1) / FL.warps;
                 const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
-                P->bf<<<grid_f, FL.warps * 32, FL.bytes, st>>>(D, ws, FL);
+                DevInst Df = D;
+                Df.stride = rs;  // bidirectional records are wider
+                P->bf<<<grid_f, FL.warps * 32, FL.bytes, st>>>(Df, ws, FL);
             } else if (bb2) {
                 bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             } else {

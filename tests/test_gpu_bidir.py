@@ -99,9 +99,15 @@ KEYS = {"nodes_bounded": "bounded", "nodes_branched": "branched", "nodes_pruned"
         "iterations": "iterations", "incumbent_updates": "incumbent_updates"}
 
 
+@pytest.mark.parametrize("family", [True, False])
 @pytest.mark.parametrize("n,m,seed,pool", [(12, 5, 0, 1024), (10, 4, 21, 1), (10, 4, 21, 7), (11, 20, 22, 300),
-                                           (14, 10, 23, 4096), (9, 3, 24, 64), (16, 5, 25, 20000)])
-def test_bidir_search_matches_oracle(F, n, m, seed, pool):
+                                           (14, 10, 23, 4096), (9, 3, 24, 64), (16, 5, 25, 20000),
+                                           (15, 10, 26, 500), (13, 20, 27, 3000), (17, 5, 28, 2)])
+def test_bidir_search_matches_oracle(F, n, m, seed, pool, family, monkeypatch):
+    """Whole searches, on the family kernel (children of a parent bounded
+    together, both directions) and on the per-child kernels (FSP_FAMILY=0)."""
+    if not family:
+        monkeypatch.setenv("FSP_FAMILY", "0")
     p = inputs.instance(n, m, seed)
     inst = F.fsp_create_instance(p)
     got = F.fsp_solve(inst, pool_size=pool, trace_cap=100000, branching=F.BRANCH_BIDIR)
@@ -148,3 +154,19 @@ def test_bidir_rejects_start_records(F):
     rec[0, :8] = np.arange(8)
     with pytest.raises(F.FspError):
         F.fsp_solve(inst, init_nodes=rec, branching=F.BRANCH_BIDIR)
+
+
+def test_bidir_family_on_the_20x20_frontier_matches_oracle(F):
+    """Bidirectional records with prefixes and suffixes of every length as
+    start records are not accepted; instead a budgeted 20 x 20 search runs a
+    few thousand iterations of both directions against the oracle."""
+    p = inputs.instance(20, 20, 1)
+    inst = F.fsp_create_instance(p)
+    ub = oracle.neh(p)[0]
+    got = F.fsp_solve(inst, ub0=ub, pool_size=2048, node_budget=300000, trace_cap=100000,
+                      branching=F.BRANCH_BIDIR)
+    want = oracle.solve_bidir(p, ub0=ub, pool=2048, node_budget=300000, trace_cap=100000)
+    for k, ko in KEYS.items():
+        assert got[k] == want[ko], k
+    assert got["cmax"] == want["cmax"]
+    assert np.array_equal(got["trace"], want["trace"])
