@@ -414,6 +414,25 @@ def batch_solve(fsp):
     res_s = B.results()
     t_split = time.perf_counter() - t1
     B.set_split(False)
+    # bidirectional branching in the batch, whole instances and split
+    bidir = {}
+    for mode in ("whole", "split"):
+        B.set_bidir(True)
+        B.set_split(mode == "split")
+        B.run()
+        B.results()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        B.run()
+        rb = B.results()
+        tb = time.perf_counter() - t1
+        bidir[mode] = {"batch_s": tb, "solved_in_batch": sum(r["status"] == fsp.OK for r in rb),
+                       "batch_nodes_bounded": sum(r["nodes_bounded"] for r in rb),
+                       "batch_nodes_per_s": sum(r["nodes_bounded"] for r in rb) / tb,
+                       "same_optima_as_forward": all(a["cmax"] == b["cmax"] for a, b in zip(res, rb)
+                                                     if a["status"] == fsp.OK and b["status"] == fsp.OK)}
+    B.set_bidir(False)
+    B.set_split(False)
     split = {"batch_s": t_split, "solved_in_batch": sum(r["status"] == fsp.OK for r in res_s),
              "batch_nodes_bounded": sum(r["nodes_bounded"] for r in res_s),
              "batch_nodes_per_s": sum(r["nodes_bounded"] for r in res_s) / t_split,
@@ -421,11 +440,12 @@ def batch_solve(fsp):
                                 if a["status"] == fsp.OK and b["status"] == fsp.OK)}
     t2 = time.perf_counter()
     finished, left_nodes = 0, 0
-    for i, r in enumerate(res):
+    for i, r in enumerate(res):  # the instances the forward batch left, by the bidirectional search
         if r["status"] == fsp.OK:
             continue
         inst = fsp.fsp_create_instance(instances[i])
-        q = fsp.fsp_solve(inst, ub0=r["cmax"], ub0_perm=r["perm"], pool_size=0, node_budget=LEFTOVER_BUDGET)
+        q = fsp.fsp_solve(inst, ub0=r["cmax"], ub0_perm=r["perm"], pool_size=0, node_budget=LEFTOVER_BUDGET,
+                          branching=fsp.BRANCH_BIDIR)
         finished += q["status"] == fsp.OK
         left_nodes += q["nodes_bounded"]
         inst.close()
@@ -438,9 +458,10 @@ def batch_solve(fsp):
     B.close()
     return {"instances": BATCH_COUNT, "solved_in_batch": solved, "batch_s": t_batch,
             "batch_nodes_bounded": nodes, "batch_nodes_per_s": nodes / t_batch, "tune_s": t_tune,
-            "split": split,
+            "split": split, "bidirectional": bidir,
             "node_budget_per_instance": BATCH_BUDGET, "leftovers": BATCH_COUNT - solved,
-            "leftovers_finished": finished, "leftover_s": t_left, "leftover_nodes": left_nodes,
+            "leftovers_finished": finished, "leftover_branching": "bidirectional", "leftover_s": t_left,
+            "leftover_nodes": left_nodes,
             "leftover_budget_each": LEFTOVER_BUDGET, "per_shape": per_shape}
 
 

@@ -429,6 +429,15 @@ int fsp_batch_results(fsp_batch *batch, fsp_batch_result *res, int32_t *perms, v
  * Errors: FSP_ERR_ARG, FSP_ERR_OOM, FSP_ERR_CUDA. */
 int fsp_batch_set_split(fsp_batch *batch, int on);
 
+/* Bidirectional branching (on != 0; FSP_BRANCH_BIDIR of fsp_options) for
+ * every instance of the batch, in either mode; off again with on = 0.
+ * Whole-instance mode then runs the search of fsp_solve with branching =
+ * FSP_BRANCH_BIDIR (from the root, NEH UB or the given ub0).  Needs a
+ * bidirectional batch shape for every instance (records of n + 2 bytes: not
+ * n = 30, 31 or 63).  Re-captures the graph.  Errors: FSP_ERR_ARG (a shape
+ * without the kernel; nothing changes), FSP_ERR_CUDA. */
+int fsp_batch_set_bidir(fsp_batch *batch, int on);
+
 /* Pool size per shape on measured throughput (Algorithm 1's purpose, per
  * shape): up to 8 instances of each shape run with pools 128 .. 4096 under
  * probe_budget nodes each; the fastest pool (nodes bounded per second) is

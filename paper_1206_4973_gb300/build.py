@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfsp.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["fsp_instance.cu", "fsp_bound.cu", "fsp_solve.cu", "fsp_neh.cu", "fsp_mlp.cu", "fsp_batch.cu", "fsp_learned.cu",
-           "fsp_family.cu", "fsp_pool16.cu", "fsp_bidir.cu"]
+           "fsp_family.cu", "fsp_pool16.cu", "fsp_bidir.cu", "fsp_batch_bidir.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
          "-I", INCLUDE, "-I", CSRC]

@@ -1,421 +1,21 @@
-// fsp_batch.cu -- many instances of mixed shape in one persistent launch.
-//
-// Each CTA takes instance indices from a device work queue (one atomic
-// counter) and solves each instance completely with CTA-local barriers only:
-// per-instance tables built in shared memory, the NEH upper bound, then the
-// same pool-synchronous depth-first search as fsp_solve (Sec. II-A
-// operators, Sec. III pool of deepest nodes) on its own stack in global
-// memory.  A per-instance pool size (tuned per shape on measured
-// throughput) and node budget apply.  The queue reset and the persistent
-// kernel are captured once in a CUDA graph and replayed.
-#include <stdlib.h>
-#include <string.h>
-
+// fsp_batch.cu -- many instances of mixed shape in one persistent launch:
+// the host side, the forward-branching kernels and the split-mode passes
+// (device code in fsp_batch.cuh; the bidirectional kernels in
+// fsp_batch_bidir.cu).
 #include <algorithm>
 #include <chrono>
 #include <vector>
 
-#include "fsp_family.cuh"
+#include "fsp_batch.cuh"
 
-#define BB 256        // threads per CTA
+template __global__ void k_batch<false>(const BatchDesc *, int, const int32_t *, BatchOut *, uint8_t *, int *, BatchWs);
+template __global__ void k_batch_split<false>(const BatchDesc *, const int32_t *, int *, BatchWs, BatchSplit);
 
-// Shapes of the batch kernel: machines MT x record vectors NV x mask words NW
-// (n <= 15, <= 31, <= 63 jobs; m = 5, 10, 20).
-#define FSP_SHAPES_BATCH(X) \
-    X(5, 1, 1) X(5, 2, 1) X(5, 4, 2) X(10, 1, 1) X(10, 2, 1) X(10, 4, 2) X(20, 2, 1)
-#define SEL_Q 4       // selection candidates per thread per chunk
-#define POOL_MAX 4096 // largest per-instance pool
-
-struct BatchDesc {  // one instance (device)
-    int n, m;
-    long long p_off;  // offset of p (n x m int32) in the flat array
-    int pool;
-    int ub0;          // 0 = compute NEH
-    long long budget; // 0 = none
-};
-
-struct BatchOut {  // one result (device; mirrored by fsp_batch_result)
-    int cmax, status, ub0, pad;
-    long long bounded, branched, pruned, leaves, iterations, updates;
-};
-
-struct BatchWs {  // per-CTA scratch in global memory
-    uint8_t *stack, *children;
-    int32_t *lbs;
-    long long cap;  // records per stack
-    int stride_max;
-};
-
-// Split mode: the work items are (instance, first job) pairs, the subtrees of
-// the root; every CTA working on an instance shares its UB and counters.
-struct BatchSplit {
-    const int *item_inst, *item_job;  // per item
-    int items;
-    int *ub;                  // per instance: best makespan so far (atomicMin)
-    unsigned long long *key;  // per instance: (best makespan << 32) | item that found it, ~0 = none
-    long long *cnt;           // per instance: bounded, branched, pruned, leaves, iterations, updates
-    int *flags;               // per instance: 1 = a node budget stopped an item, 2 = a stack filled up
-    uint8_t *item_perm;       // per item: the best schedule it found (FSP_MAX_JOBS bytes)
-};
-
-__device__ __forceinline__ int b_block_incl_scan(int v, int *warp_tot)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    if (lane == 31) warp_tot[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        int t = lane < BB / 32 ? warp_tot[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += u;
-        }
-        if (lane < BB / 32) warp_tot[lane] = t;
-    }
-    __syncthreads();
-    const int add = wid > 0 ? warp_tot[wid - 1] : 0;
-    __syncthreads();
-    return v + add;
-}
-
-__device__ __forceinline__ int b_block_sum(int v, int *warp_tot)
-{
-    const int incl = b_block_incl_scan(v, warp_tot);
-    __shared__ int s_total;
-    if (threadIdx.x == BB - 1) s_total = incl;
-    __syncthreads();
-    const int t = s_total;
-    __syncthreads();
-    return t;
-}
-
-// Johnson precedence with lags (same rule as the instance tables).
-__device__ __forceinline__ bool b_precedes(int i, int32_t ai, int32_t bi, int32_t li, int j, int32_t aj, int32_t bj,
-                                           int32_t lj)
-{
-    const bool late_i = ai > bi, late_j = aj > bj;
-    if (late_i != late_j) return !late_i;
-    if (!late_i) {
-        const int32_t ki = ai + li, kj = aj + lj;
-        if (ki != kj) return ki < kj;
-    } else {
-        const int32_t ki = bi + li, kj = bj + lj;
-        if (ki != kj) return ki > kj;
-    }
-    return i < j;
-}
-
-struct BatchShared {  // static shared state of a CTA
-    int warp_tot[BB / 32];
-    uint8_t inc[FSP_MAX_JOBS + 1], seq[FSP_MAX_JOBS + 1], ord[FSP_MAX_JOBS + 1];
-    int32_t tot[FSP_MAX_JOBS + 1];
-    unsigned long long best_key;
-};
-
-// Shared memory of a batch CTA for an n x m instance: the family layout
-// (fsp_family.cuh) for the CTA's warps, then the parents' first-child offsets.
-__host__ __device__ inline size_t batch_smem_nm(int n, int m)
-{
-    const int mp = (m % 2 == 0) ? m + 1 : m, nv = (n + 1 + 15) / 16;
-    return fsp_align16(family_smem_layout_nm(n, m, mp, m, nv, BB / 32).bytes) + (size_t)(POOL_MAX / 2 + 4) * 4;
-}
-
-// NEH upper bound: jobs by decreasing total time, each inserted at the
-// position of smallest partial makespan, earliest on ties; the sequence is
-// left in sh.seq.  All threads of the CTA call it.
-template <int MT>
-__device__ int b_neh(const int32_t *__restrict__ p, int n, BatchShared &sh)
-{
-    const int tid = threadIdx.x;
-    uint8_t *seq = sh.seq, *ord = sh.ord;
-    int32_t *tot = sh.tot;
-    unsigned long long &best_key = sh.best_key;
-    for (int j = tid; j < n; j += BB) {
-        int32_t s = 0;
-        for (int k = 0; k < MT; ++k) s += p[j * MT + k];
-        tot[j] = s;
-    }
-    __syncthreads();
-    for (int j = tid; j < n; j += BB) {
-        int rank = 0;
-        for (int i = 0; i < n; ++i) rank += (tot[i] > tot[j]) || (tot[i] == tot[j] && i < j);
-        ord[rank] = (uint8_t)j;
-    }
-    __syncthreads();
-    for (int len = 0; len < n; ++len) {
-        const int job = ord[len];
-        if (tid == 0) best_key = ~0ull;
-        __syncthreads();
-        for (int pos = tid; pos <= len; pos += BB) {
-            int32_t C[MT];
-#pragma unroll
-            for (int k = 0; k < MT; ++k) C[k] = 0;
-            for (int i = 0; i <= len; ++i) {
-                const int j = i < pos ? seq[i] : (i == pos ? job : seq[i - 1]);
-                C[0] += p[j * MT];
-#pragma unroll
-                for (int k = 1; k < MT; ++k) C[k] = max(C[k], C[k - 1]) + p[j * MT + k];
-            }
-            atomicMin(&best_key, ((unsigned long long)(uint32_t)C[MT - 1] << 32) | (unsigned)pos);
-        }
-        __syncthreads();
-        const int at = (int)(best_key & 0xffffffffu);
-        if (tid == 0) {
-            for (int i = len; i > at; --i) seq[i] = seq[i - 1];
-            seq[at] = (uint8_t)job;
-        }
-        __syncthreads();
-    }
-    const int ub = (int)(best_key >> 32);
-    __syncthreads();
-    return ub;
-}
-
-// One instance's search (whole instance), or (SPLIT) the subtree of the
-// root whose schedule starts with job `job`, sharing the instance's UB and
-// counters with the other CTAs; tables_ready: this CTA's shared memory
-// already holds the instance's tables.
-template <int MT, int NV, int NW, bool SPLIT>
-__device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, BatchOut *out, uint8_t *perm_out,
-                        const BatchWs &W, unsigned char *smem, BatchShared &sh, const BatchSplit &X, int inst,
-                        int item, int job, bool tables_ready)
-{
-    const int n = D.n, tid = threadIdx.x;
-    const int P = MT * (MT - 1) / 2, mp = (MT % 2 == 0) ? MT + 1 : MT;
-    const int stride = (n + 1 + 15) / 16 * 16;
-    const FamSmem L = family_smem_layout_nm(n, MT, mp, MT, NV, BB / 32);
-    const FamView V = fam_view(smem, L, tid >> 5);
-    int2 *pq_s = V.pq;
-    int *poff = reinterpret_cast<int *>(smem + fsp_align16(L.bytes));
-    int *warp_tot = sh.warp_tot;
-    uint8_t *inc = sh.inc, *seq = sh.seq, *ord = sh.ord;
-    int32_t *tot = sh.tot;
-    unsigned long long &best_key = sh.best_key;
-
-    // tables: {p, tail} rows and the Johnson entries of every pair
-    if (!SPLIT || !tables_ready) {
-    for (int i = tid; i < n * MT; i += BB) {
-        const int j = i / MT, k = i - j * MT;
-        int32_t q = 0;
-        for (int h = k + 1; h < MT; ++h) q += p[j * MT + h];
-        pq_s[j * mp + k] = make_int2(p[i], q);
-    }
-    for (int e = tid; e < P * n; e += BB) {
-        const int kl = e / n, j = e - kl * n;
-        int k = 0, rem = kl;
-        while (rem >= MT - 1 - k) { rem -= MT - 1 - k; ++k; }
-        const int l = k + 1 + rem;
-        int32_t aj = p[j * MT + k], bj = p[j * MT + l], lj = 0;
-        for (int h = k + 1; h < l; ++h) lj += p[j * MT + h];
-        int rank = 0;
-        for (int i = 0; i < n; ++i) {
-            if (i == j) continue;
-            int32_t li = 0;
-            for (int h = k + 1; h < l; ++h) li += p[i * MT + h];
-            rank += b_precedes(i, p[i * MT + k], p[i * MT + l], li, j, aj, bj, lj);
-        }
-        V.we[rank * P + kl] = make_int2(aj + lj, aj - bj);  // position-major entries
-        V.rk8[kl * V.rks8 + j] = (uint8_t)rank;             // each job's position
-    }
-    __syncthreads();
-    fam_tables_finish<MT>(V, n, mp);
-    }
-
-    // the UB: NEH unless given (whole instances), or the instance's shared UB (split)
-    int ub = D.ub0;
-    if (SPLIT) {
-        ub = *(volatile int *)&X.ub[inst];
-    } else if (ub <= 0) {
-        ub = b_neh<MT>(p, n, sh);
-        for (int i = tid; i < n; i += BB) inc[i] = seq[i];
-    }
-    __syncthreads();
-
-    // the search
-    long long bounded = 0, branched = 0, pruned = 0, leaves = 0, iters = 0, updates = 0;
-    int status = FSP_OK;
-    long long S = 1;
-    if (SPLIT && job >= 0) {  // the root's child that schedules `job` first (the rest in increasing order)
-        for (int i = tid; i < stride; i += BB)
-            W.stack[i] = (uint8_t)(i == 0 ? job : i < n ? (i - 1 < job ? i - 1 : i) : i == n ? 1 : 0);
-    } else {
-        for (int i = tid; i < stride; i += BB) W.stack[i] = (uint8_t)(i < n ? i : 0);
-    }
-    bool improved = false;
-    __shared__ int s_ub;
-    __syncthreads();
-    const int pool = D.pool;
-    const int warp = tid >> 5, lane = tid & 31;
-    while (S > 0) {
-        if (SPLIT) {  // the instance's UB and node count, as the other CTAs left them
-            if (tid == 0) {
-                s_ub = min(ub, *(volatile int *)&X.ub[inst]);
-                if (D.budget > 0 && *(volatile long long *)&X.cnt[6 * inst] >= D.budget) s_ub = -1;
-            }
-            __syncthreads();
-            const int u = s_ub;
-            __syncthreads();
-            if (u < 0) { status = FSP_INCOMPLETE; break; }
-            ub = u;
-        } else if (D.budget > 0 && bounded >= D.budget) {
-            status = FSP_INCOMPLETE;
-            break;
-        }
-        // selection: deepest parents while their children fit (at least one)
-        const long long cand = S < pool ? S : pool;
-        long long running = 0, np = 0;
-        for (long long base = 0; base < cand; base += (long long)BB * SEL_Q) {
-            int r[SEL_Q], tsum = 0;
-#pragma unroll
-            for (int q = 0; q < SEL_Q; ++q) {
-                const long long i = base + (long long)tid * SEL_Q + q;
-                r[q] = i < cand ? n - (int)W.stack[(S - 1 - i) * stride + n] : 0;
-                tsum += r[q];
-            }
-            int run = b_block_incl_scan(tsum, warp_tot) - tsum, taken = 0, tsum_taken = 0;
-#pragma unroll
-            for (int q = 0; q < SEL_Q; ++q) {
-                const long long i = base + (long long)tid * SEL_Q + q;
-                if (i < cand && (i == 0 || running + run + r[q] <= pool)) {
-                    poff[i] = (int)(running + run);
-                    taken++;
-                    tsum_taken += r[q];
-                }
-                run += r[q];
-            }
-            const int ct = b_block_sum(taken, warp_tot), cts = b_block_sum(tsum_taken, warp_tot);
-            np += ct;
-            running += cts;
-            if (ct < BB * SEL_Q) break;
-        }
-        const long long nch = running;
-        if (tid == 0) poff[np] = (int)nch;
-        if (S - np + nch > W.cap) { status = FSP_ERR_CAPACITY; break; }
-        if (tid == 0) best_key = ~0ull;
-        __syncthreads();
-        // branching + bounding: each warp bounds a parent's children together
-        for (long long f = warp; f < np; f += BB / 32) {
-            if (lane < NV)
-                reinterpret_cast<uint4 *>(V.recb)[lane] =
-                    reinterpret_cast<const uint4 *>(W.stack + (S - 1 - f) * stride)[lane];
-            __syncwarp();
-            fam_bound<MT, NV, false, false>(V, V.recb, poff[f], n, mp, stride, ub, W.children, W.lbs, &best_key,
-                                            nullptr, 0, nullptr);
-            __syncwarp();
-        }
-        __syncthreads();
-        const unsigned long long bk = best_key;
-        const int ub_new = (bk != ~0ull && (int)(bk >> 32) < ub) ? (int)(bk >> 32) : ub;
-        if (ub_new < ub) {
-            const long long idx = (long long)(bk & 0xffffffffull);
-            for (int i = tid; i < n; i += BB) inc[i] = W.children[idx * stride + i];
-            updates++;
-            if (SPLIT) {
-                improved = true;
-                if (tid == 0) {
-                    atomicMin(&X.ub[inst], ub_new);
-                    atomicMin(&X.key[inst], ((unsigned long long)(uint32_t)ub_new << 32) | (unsigned)item);
-                }
-            }
-        }
-        ub = ub_new;
-        // elimination: survivors (non-leaf, bound < UB), pushed in reverse order
-        int my_s = 0, my_l = 0;
-        for (long long c = tid; c < nch; c += BB) {
-            const bool leaf = W.children[c * stride + n] == (uint8_t)(n - 1);
-            my_l += leaf;
-            my_s += !leaf && W.lbs[c] < ub;
-        }
-        const int total = b_block_sum(my_s, warp_tot), nleaf = b_block_sum(my_l, warp_tot);
-        const long long base_s = S - np;
-        long long done = 0;
-        for (long long c0 = 0; c0 < nch; c0 += BB) {
-            const long long c = c0 + tid;
-            const bool surv = c < nch && W.children[c * stride + n] != (uint8_t)(n - 1) && W.lbs[c] < ub;
-            const int incl = b_block_incl_scan(surv ? 1 : 0, warp_tot);
-            if (surv) {
-                const long long q = done + incl - 1;
-                const uint4 *src = reinterpret_cast<const uint4 *>(W.children + c * stride);
-                uint4 *dst = reinterpret_cast<uint4 *>(W.stack + (base_s + total - 1 - q) * stride);
-                for (int v = 0; v < stride / 16; ++v) dst[v] = src[v];
-            }
-            done += b_block_sum(surv ? 1 : 0, warp_tot);
-        }
-        S = base_s + total;
-        bounded += nch;
-        branched += np;
-        leaves += nleaf;
-        pruned += nch - nleaf - total;
-        iters++;
-        if (SPLIT && tid == 0) atomicAdd((unsigned long long *)&X.cnt[6 * inst], (unsigned long long)nch);
-        __syncthreads();
-    }
-    if (SPLIT) {  // this item's share of the counters, its flags and its best schedule
-        if (tid == 0) {
-            unsigned long long *c = (unsigned long long *)&X.cnt[6 * inst];
-            atomicAdd(c + 1, (unsigned long long)branched);
-            atomicAdd(c + 2, (unsigned long long)pruned);
-            atomicAdd(c + 3, (unsigned long long)leaves);
-            atomicAdd(c + 4, (unsigned long long)iters);
-            atomicAdd(c + 5, (unsigned long long)updates);
-            if (status == FSP_INCOMPLETE) atomicOr(&X.flags[inst], 1);
-            if (status == FSP_ERR_CAPACITY) atomicOr(&X.flags[inst], 2);
-        }
-        if (improved)
-            for (int i = tid; i < n; i += BB) X.item_perm[(size_t)item * FSP_MAX_JOBS + i] = inc[i];
-        __syncthreads();
-        return;
-    }
-    if (tid == 0) {
-        out->cmax = ub;
-        out->status = status;
-        out->bounded = bounded;
-        out->branched = branched;
-        out->pruned = pruned;
-        out->leaves = leaves;
-        out->iterations = iters;
-        out->updates = updates;
-    }
-    for (int i = tid; i < n; i += BB) perm_out[i] = inc[i];
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(BB) k_batch(const BatchDesc *__restrict__ desc, int count,
-                                              const int32_t *__restrict__ p_flat, BatchOut *out, uint8_t *perms,
-                                              int *queue, BatchWs W)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_inst;
-    __shared__ BatchShared sh;
-    BatchWs w = W;
-    w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
-    w.children = W.children + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS) * W.stride_max;
-    w.lbs = W.lbs + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS);
-    for (;;) {
-        if (threadIdx.x == 0) s_inst = atomicAdd(queue, 1);
-        __syncthreads();
-        const int i = s_inst;
-        __syncthreads();
-        if (i >= count) break;
-        const BatchDesc D = desc[i];
-        const int32_t *p = p_flat + D.p_off;
-        const int nv = (D.n + 1 + 15) / 16, nw = D.n <= 32 ? 1 : 2;
-        uint8_t *po = perms + (size_t)i * FSP_MAX_JOBS;
-#define B_CASE(MT_, NV_, NW_)                                                                          \
-    if (D.m == MT_ && nv == NV_ && nw == NW_) {                                                        \
-        b_solve<MT_, NV_, NW_, false>(p, D, out + i, po, w, smem, sh, BatchSplit{}, i, 0, 0, false);   \
-        continue;                                                                                      \
-    }
-        FSP_SHAPES_BATCH(B_CASE)
-#undef B_CASE
-        if (threadIdx.x == 0) out[i].status = FSP_ERR_ARG;  // shape without a kernel (checked on the host)
-    }
-}
+// The bidirectional instantiations (fsp_batch_bidir.cu).
+typedef void (*BatchFn)(const BatchDesc *, int, const int32_t *, BatchOut *, uint8_t *, int *, BatchWs);
+typedef void (*BatchSplitFn)(const BatchDesc *, const int32_t *, int *, BatchWs, BatchSplit);
+BatchFn batch_kernel_bidir();
+BatchSplitFn batch_split_kernel_bidir();
 
 // Split mode, before the items: each instance's UB (NEH unless given), its
 // NEH schedule as the permutation to report if no item improves on it, and
@@ -438,44 +38,6 @@ __global__ void __launch_bounds__(BB) k_batch_split_init(const BatchDesc *__rest
         X.key[i] = ~0ull;
         X.flags[i] = 0;
         for (int k = 0; k < 6; ++k) X.cnt[6 * i + k] = 0;
-    }
-}
-
-// Split mode: the persistent kernel over the work items; a CTA keeps the
-// tables of the instance it last worked on (the items of an instance are
-// consecutive in the queue).
-__global__ void __launch_bounds__(BB) k_batch_split(const BatchDesc *__restrict__ desc,
-                                                    const int32_t *__restrict__ p_flat, int *queue, BatchWs W,
-                                                    BatchSplit X)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
-    __shared__ BatchShared sh;
-    BatchWs w = W;
-    w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
-    w.children = W.children + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS) * W.stride_max;
-    w.lbs = W.lbs + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS);
-    int cur = -1;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= X.items) break;
-        const int i = X.item_inst[item], job = X.item_job[item];
-        const BatchDesc D = desc[i];
-        const int32_t *p = p_flat + D.p_off;
-        const int nv = (D.n + 1 + 15) / 16, nw = D.n <= 32 ? 1 : 2;
-        const bool ready = cur == i;
-        cur = i;
-#define B_CASE(MT_, NV_, NW_)                                                                   \
-    if (D.m == MT_ && nv == NV_ && nw == NW_) {                                                 \
-        b_solve<MT_, NV_, NW_, true>(p, D, nullptr, nullptr, w, smem, sh, X, i, item, job, ready); \
-        continue;                                                                               \
-    }
-        FSP_SHAPES_BATCH(B_CASE)
-#undef B_CASE
-        cur = -1;
     }
 }
 
@@ -507,6 +69,7 @@ __global__ void k_batch_split_finish(const BatchDesc *__restrict__ desc, int cou
     }
 }
 
+
 // ------------------------------------------------------------------ host --
 
 struct fsp_batch {
@@ -521,14 +84,14 @@ struct fsp_batch {
     std::vector<BatchDesc> desc;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
-    bool split = false;
+    bool split = false, bidir = false;
     BatchSplit X{};
     int *d_item = nullptr;  // item instances, then item jobs
 };
 
-static bool batch_shape_ok(int n, int m)
+static bool batch_shape_ok(int n, int m, bool bidir = false)
 {
-    const int nv = (n + 1 + 15) / 16, nw = n <= 32 ? 1 : 2;
+    const int nv = (n + (bidir ? 2 : 1) + 15) / 16, nw = n <= 32 ? 1 : 2;
     if (n < 2 || n > 63) return false;
 #define B_OK(MT_, NV_, NW_) if (m == MT_ && nv == NV_ && nw == NW_) return true;
     FSP_SHAPES_BATCH(B_OK)
@@ -557,12 +120,14 @@ static int batch_capture(fsp_batch *B)
     FSP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
+    const BatchFn kb = B->bidir ? batch_kernel_bidir() : &k_batch<false>;
+    const BatchSplitFn ks = B->bidir ? batch_split_kernel_bidir() : &k_batch_split<false>;
     if (e == cudaSuccess && !B->split) {
-        k_batch<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->count, B->d_p, B->d_out, B->d_perms, B->d_queue, B->ws);
+        kb<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->count, B->d_p, B->d_out, B->d_perms, B->d_queue, B->ws);
         e = cudaGetLastError();
     } else if (e == cudaSuccess) {
         k_batch_split_init<<<B->count, BB, 0, st>>>(B->d_desc, B->d_p, B->d_perms, B->X);
-        k_batch_split<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->d_p, B->d_queue, B->ws, B->X);
+        ks<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->d_p, B->d_queue, B->ws, B->X);
         k_batch_split_finish<<<B->count, 64, 0, st>>>(B->d_desc, B->count, B->d_out, B->d_perms, B->X);
         e = cudaGetLastError();
     }
@@ -611,8 +176,8 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
         off += (long long)n * m;
         if (n > n_max) n_max = n;
         if (m > m_max) m_max = m;
-        if (batch_smem_nm(n, m) > smem_max) smem_max = batch_smem_nm(n, m);
-        const int s = (n + 1 + 15) / 16 * 16;
+        smem_max = std::max(smem_max, std::max(batch_smem_nm(n, m), batch_smem_nm(n, m, true)));
+        const int s = (n + 2 + 15) / 16 * 16;  // wide enough for bidirectional records
         if (s > s_max) s_max = s;
     }
     int rc = FSP_OK;
@@ -629,11 +194,14 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
             rc = FSP_ERR_ARG;
             goto fail;
         }
-        TRYB(cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
-        TRYB(cudaFuncSetAttribute((const void *)k_batch_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)B->smem));
-        int per_sm = 0;
-        TRYB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BB, B->smem));
+        const void *kern[4] = {(const void *)&k_batch<false>, (const void *)&k_batch_split<false>,
+                               (const void *)batch_kernel_bidir(), (const void *)batch_split_kernel_bidir()};
+        for (const void *k : kern)
+            TRYB(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
+        int per_sm = 0, per_sm_b = 0;
+        TRYB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[0], BB, B->smem));
+        TRYB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, kern[2], BB, B->smem));
+        per_sm = std::min(per_sm, per_sm_b);
         B->grid = B->sm_count * (per_sm > 0 ? per_sm : 1);
         if (B->grid > count) B->grid = count;
     }
@@ -656,6 +224,20 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
 fail:
     batch_free(B);
     return rc;
+}
+
+extern "C" int fsp_batch_set_bidir(fsp_batch *B, int on)
+{
+    if (!B) { fsp_set_error("fsp_batch_set_bidir: NULL batch"); return FSP_ERR_ARG; }
+    if (on)
+        for (int i = 0; i < B->count; ++i)
+            if (!batch_shape_ok(B->desc[i].n, B->desc[i].m, true)) {
+                fsp_set_error("fsp_batch_set_bidir: instance %d (%dx%d) has no bidirectional batch kernel", i,
+                              B->desc[i].n, B->desc[i].m);
+                return FSP_ERR_ARG;
+            }
+    B->bidir = on != 0;
+    return batch_capture(B);
 }
 
 extern "C" int fsp_batch_set_split(fsp_batch *B, int on)

@@ -31,7 +31,7 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_node_stride_bidir", "f
            "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
            "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
-           "fsp_batch_tune_pools", "fsp_batch_set_split", "fsp_set_bound", "fsp_instance_host_objects",
+           "fsp_batch_tune_pools", "fsp_batch_set_split", "fsp_batch_set_bidir", "fsp_set_bound", "fsp_instance_host_objects",
            "fsp_last_error")
 BOUND_BASE, BOUND_HEADS = 0, 1
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
@@ -129,6 +129,7 @@ def load(path: str | None = None):
         "fsp_batch_results": (ctypes.c_int, [vp, vp, vp, vp]),
         "fsp_batch_tune_pools": (ctypes.c_int, [ctypes.c_int, vp, vp, i64, vp]),
         "fsp_batch_set_split": (ctypes.c_int, [vp, ctypes.c_int]),
+        "fsp_batch_set_bidir": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_set_bound": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_instance_host_objects": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64),
                                                      ctypes.POINTER(ctypes.c_int64)]),
@@ -630,6 +631,10 @@ class Batch:
     def set_split(self, on: bool):
         """Work items = the subtrees of the roots (fsp_batch_set_split)."""
         _check(load().fsp_batch_set_split(self.handle, 1 if on else 0))
+
+    def set_bidir(self, on: bool):
+        """Bidirectional branching for every instance (fsp_batch_set_bidir)."""
+        _check(load().fsp_batch_set_bidir(self.handle, 1 if on else 0))
 
     def close(self):
         if self.handle:

@@ -129,3 +129,35 @@ def test_split_mode_reaches_the_same_optima(F):
     B.set_split(False)  # back to whole instances: the bit-exact search
     B.run()
     check(F, instances, B.results(), pools, budgets)
+
+
+def test_bidirectional_batch_matches_oracle(F):
+    """Bidirectional branching in the batch: each instance's search equals
+    oracle.solve_bidir with the same pool, NEH UB and node budget (every
+    counter, the optimum); split mode reaches the same optima."""
+    shapes = list(inputs.batch_shapes(16, first_seed=200)) + [(9, 5, 1), (12, 10, 2), (2, 5, 3), (14, 5, 4)]
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    k = len(instances)
+    pools = np.array([(64, 256, 1024, 3)[i % 4] for i in range(k)], np.int64)
+    budgets = np.array([20000] * 16 + [0] * 4, np.int64)
+    B = F.Batch(instances, pools, budgets)
+    B.set_bidir(True)
+    B.run()
+    res = B.results()
+    for i, (p, r) in enumerate(zip(instances, res)):
+        u, _ = oracle.neh(p)
+        ref = oracle.solve_bidir(p, ub0=u, pool=int(pools[i]), node_budget=int(budgets[i]))
+        assert r["status"] == ref["status"], i
+        assert r["cmax"] == ref["cmax"], i
+        for key in ("bounded", "branched", "pruned", "leaves", "iterations", "incumbent_updates"):
+            name = "nodes_" + key if key in ("bounded", "branched", "pruned") else key
+            assert r[name] == ref[key], (i, key)
+        assert oracle.makespan(p, r["perm"]) == r["cmax"], i
+    B.set_split(True)
+    B.run()
+    for i, (a, b) in enumerate(zip(res, B.results())):
+        assert oracle.makespan(instances[i], b["perm"]) == b["cmax"], i
+        if a["status"] == F.OK and b["status"] == F.OK:
+            assert a["cmax"] == b["cmax"], i
+    with pytest.raises(F.FspError):  # records of 32 jobs + 2 bytes: no bidirectional batch kernel
+        F.Batch([inputs.instance(31, 20, 1)], [64]).set_bidir(True)
