@@ -320,7 +320,14 @@ def learned_vs_plain(fsp, budget=LEARNED_BUDGET):
                     "identical_search": same, "cmax": a["cmax"],
                     "optimal": a["status"] == fsp.OK, "early_cut_fraction": b["early_pruned"] / max(1, b["nodes_bounded"]),
                     "train_s": t_train, "train_final_loss": loss,
-                    "us_per_iteration": phases})
+                    "us_per_iteration": phases,
+                    # where the family kernel's work goes: families (parents) whose children
+                    # all fall to their one-machine bounds, those the predicted pairs close,
+                    # and the pair evaluations left exact
+                    "families": {nm: {"parents": x["nodes_branched"], "closed_by_lb1": x["families_closed_lb1"],
+                                      "closed_by_predicted_pairs": x["families_closed_predicted"],
+                                      "exact_pair_evals": x["exact_pair_evals"]}
+                                 for nm, (x, _) in (("plain", res["plain"]), ("learned", res["learned"]))}})
         inst.close()
     return out
 

@@ -74,7 +74,8 @@ typedef struct {
     int64_t incumbent_updates; /* strict improvements of the UB            */
     double time_ms;            /* wall time of the search on the stream    */
     double select_ms;          /* device time in selection (opt->profile)  */
-    double bound_ms;           /* device time in branching + bounding      */
+    double bound_ms;           /* device time in branching + bounding (the
+                                  network's infer_ms not included)         */
     double compact_ms;         /* device time in elimination + compaction  */
     int64_t tuned_pool;        /* pool size the tuner settled on (pool_size = 0), else the pool */
     int64_t early_pruned;      /* children cut by their predicted pairs alone (order = learned) */
@@ -82,6 +83,13 @@ typedef struct {
     int64_t tuned_warps;       /* warps per CTA of the family kernel (chosen on measured
                                   throughput with pool_size = 0); 0 if the per-child
                                   kernels ran */
+    /* family kernel only (0 otherwise), summed over the search: */
+    int64_t families_closed_lb1;       /* parents whose children all reach the UB of the
+                                          iteration by their one-machine bounds (any order) */
+    int64_t families_closed_predicted; /* learned order: parents whose children not cut by
+                                          their one-machine bounds are all cut by the
+                                          predicted pairs (the 190-pair work then skipped) */
+    int64_t exact_pair_evals;          /* pairs evaluated exactly (not certified), per family */
 } fsp_stats;
 
 #define FSP_ORDER_PLAIN 0   /* every child gets its full bound */

@@ -304,8 +304,9 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
                 reinterpret_cast<uint4 *>(V.recb)[lane] =
                     reinterpret_cast<const uint4 *>(W.stack + (S - 1 - f) * stride)[lane];
             __syncwarp();
+            int fc[4] = {0, 0, 0, 0};  // not reported by the batch
             fam_bound<MT, NV, false, false, BIDIR>(V, V.recb, poff[f], n, mp, stride, ub, W.children, W.lbs,
-                                                   &best_key, nullptr, 0, nullptr);
+                                                   &best_key, 0, 0, nullptr, fc);
             __syncwarp();
         }
         __syncthreads();

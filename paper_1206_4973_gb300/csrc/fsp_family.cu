@@ -87,9 +87,13 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
     // record is copied into the other buffer while this one is processed
     unsigned long long *next_f = reinterpret_cast<unsigned long long *>(&ws.ctl->fam_next);
     int f = 0, buf = 0;
+    int fc[4] = {0, 0, 0, 0};  // this warp's family counts (SolveCtl::fam) and early cuts
     if (lane == 0) f = (int)atomicAdd(next_f, 1ull);
     f = __shfl_sync(0xffffffffu, f, 0);
     if (f < np) fam_fetch<NV>(ws, S, stride, f, lane, V.recb, V.pofs);
+    // learned order: lane j < K loads the family's j-th predicted pair one family
+    // ahead, so the load completes while the previous family is bounded
+    int pair = (LRN && f < np && lane < L.K) ? __ldg(ws.topk + (long long)f * L.K + lane) : 0;
     while (f < np) {
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         __syncwarp();
@@ -99,12 +103,18 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         if (lane == 0) fn = (int)atomicAdd(next_f, 1ull);
         fn = __shfl_sync(0xffffffffu, fn, 0);
         if (fn < np) fam_fetch<NV>(ws, S, stride, fn, lane, V.recb + (buf ^ 1) * 16 * NV, V.pofs + (buf ^ 1));
+        const int pair_next = (LRN && fn < np && lane < L.K) ? __ldg(ws.topk + (long long)fn * L.K + lane) : 0;
         fam_bound<MT, NV, LRN, HEADS, BIDIR>(V, rec_s, c0, n, mp, stride, ub_iter, ws.children, ws.lbs,
-                                      &ws.ctl->best_key, LRN ? ws.topk + (long long)f * L.K : nullptr, L.K,
-                                      reinterpret_cast<unsigned long long *>(&ws.ctl->early));
+                                             &ws.ctl->best_key, pair, L.K, nullptr, fc);
         __syncwarp();
         f = fn;
+        pair = pair_next;
         buf ^= 1;
+    }
+    if (lane == 0) {
+        for (int q = 0; q < 3; ++q)
+            if (fc[q]) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctl->fam[q]), (unsigned long long)fc[q]);
+        if (fc[3]) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctl->early), (unsigned long long)fc[3]);
     }
 }
 

@@ -232,7 +232,8 @@ __device__ __forceinline__ int32_t fam_prefix_p(int t, int lane, int d, int k, i
 // in this warp's shared memory; c0: the index of its first child; the child
 // records go to children, their bounds to lbs, and a depth n-1 child below
 // ub_iter to the atomic minimum *best_key = (bound << 32) | child index.
-// LRN: the learned order.  Children whose LB1 reaches the iteration's UB are
+// LRN: the learned order (lane j < K holds the parent's j-th predicted pair
+// in my_pair).  Children whose LB1 reaches the iteration's UB are
 // cut at once; the parent's K predicted pairs (topk_row) then give each open
 // child a lower bound from their forward scans and cut more; only if a
 // child is left do the certification and the remaining pairs run, for the
@@ -251,8 +252,8 @@ __device__ __forceinline__ int32_t fam_prefix_p(int t, int lane, int d, int k, i
 template <int MT, int NV, bool LRN, bool HEADS, bool BIDIR = false>
 __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s, long long c0, int n, int mp,
                                           int stride, int ub_iter, uint8_t *children, int32_t *lbs,
-                                          unsigned long long *best_key, const int16_t *topk_row, int K,
-                                          unsigned long long *early)
+                                          unsigned long long *best_key, int my_pair, int K,
+                                          unsigned long long *early, int (&fc)[4])
 {
     constexpr int P = MT * (MT - 1) / 2;
     constexpr int NS = (P + 31) / 32;
@@ -517,18 +518,27 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
 
         const bool leaves = r == 2;  // the children have one job left: complete schedules
         bool open = !leaves;
+        if (!leaves) {  // counted in every order: children all cut by their one-machine bounds
+            const bool any = open_any();
+            fc[0] += !any;
+            if (LRN) open = any;
+        }
         if (LRN) {
-            if (open) open = open_any();
             if (open) {  // the parent's predicted pairs
-                if (lane < K) lkl[lane] = (uint16_t)topk_row[lane];
+                if (lane < K) lkl[lane] = (uint16_t)my_pair;
                 __syncwarp();
                 forward_pairs(K);
                 open = open_any();
+                fc[1] += !open;
             }
             int cut = 0;
             for (int ci = lane; ci < r; ci += 32) cut += lbv[ci] >= ub_iter;
             cut = __reduce_add_sync(0xffffffffu, cut);
-            if (lane == 0 && cut) atomicAdd(early, (unsigned long long)cut);
+            if (early) {
+                if (lane == 0 && cut) atomicAdd(early, (unsigned long long)cut);
+            } else {
+                fc[3] += cut;  // added once per warp by the caller (one address for every family)
+            }
         }
         if (open) {
             // -- per machine: alpha_k = min_c (LB1 - C_k), beta_l = max_c SQ_l
@@ -621,6 +631,7 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
             }
             __syncwarp();
 
+            fc[2] += n2;
             exact_pairs(n2);
         }
 

@@ -1227,13 +1227,14 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 TRY(cudaEventElapsedTime(&b, pe[1], pe[2]));
                 TRY(cudaEventElapsedTime(&c, pe[2], pe[3]));
                 t_sel += a;
-                t_bb += b;
                 t_cmp += c;
-                if (P->L.learned && (P->bl || P->bf)) {
+                if (P->L.learned && (P->bl || P->bf)) {  // the network's share is not bounding
                     float d = 0;
                     TRY(cudaEventElapsedTime(&d, pe[1], pe[4]));
                     t_inf += d;
+                    b -= d;
                 }
+                t_bb += b;
             }
             if (h.status != 0) {
                 rc = h.status;
@@ -1350,6 +1351,9 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
         stats->tuned_pool = tuner.on ? tuner.best : o.pool_size;
         stats->tuned_warps = P->bf ? P->famC[fam_i].warps : 0;
         stats->early_pruned = h.cnt[6];
+        stats->families_closed_lb1 = h.fam[0];
+        stats->families_closed_predicted = h.fam[1];
+        stats->exact_pair_evals = h.fam[2];
         stats->infer_ms = t_inf;
         float ms = 0.f;
         if (timed) cudaEventElapsedTime(&ms, ev0, ev1);

@@ -18,6 +18,10 @@ struct SolveCtl {
     long long n_list;       // learned order: children left for the full bound
     long long early;        // learned order: children cut by their predicted pairs
     long long fam_next;     // family kernel: next parent to take
+    long long fam[3];       // family kernel, summed over the search: families whose children
+                            // all reach the UB by their one-machine bounds; families closed
+                            // by their predicted pairs alone (learned order); exact pair
+                            // evaluations (pairs left uncertified, per family)
 };
 
 struct SolveWs {

@@ -51,7 +51,8 @@ class fsp_stats(ctypes.Structure):
                 ("time_ms", ctypes.c_double), ("select_ms", ctypes.c_double),
                 ("bound_ms", ctypes.c_double), ("compact_ms", ctypes.c_double),
                 ("tuned_pool", ctypes.c_int64), ("early_pruned", ctypes.c_int64), ("infer_ms", ctypes.c_double),
-                ("tuned_warps", ctypes.c_int64)]
+                ("tuned_warps", ctypes.c_int64), ("families_closed_lb1", ctypes.c_int64),
+                ("families_closed_predicted", ctypes.c_int64), ("exact_pair_evals", ctypes.c_int64)]
 
 
 class fsp_options(ctypes.Structure):
@@ -384,7 +385,7 @@ def fsp_solve_workspace_bytes(inst: Instance, **kw) -> int:
 
 STATS = ("nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iterations", "incumbent_updates")
 _RESULT_FIELDS = STATS + ("time_ms", "select_ms", "bound_ms", "compact_ms", "infer_ms", "tuned_pool", "tuned_warps",
-                          "early_pruned")
+                          "early_pruned", "families_closed_lb1", "families_closed_predicted", "exact_pair_evals")
 
 
 def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_budget: int = 0,

@@ -108,3 +108,10 @@ def test_trained_network_cuts_more_than_untrained(F):
         assert a[k] == b[k] == c[k], k
     assert a["early_pruned"] > b["early_pruned"], (a["early_pruned"], b["early_pruned"])
     assert c["early_pruned"] == 0
+    # the family counts: the same searches close the same families by their
+    # one-machine bounds; only the learned order closes any by predicted
+    # pairs, and every family it closes that way skips its exact pairs
+    assert a["families_closed_lb1"] == b["families_closed_lb1"] == c["families_closed_lb1"] > 0
+    assert c["families_closed_predicted"] == 0
+    assert a["families_closed_predicted"] > b["families_closed_predicted"] >= 0
+    assert a["exact_pair_evals"] <= c["exact_pair_evals"]
