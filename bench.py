@@ -43,10 +43,10 @@ SMS, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # reports sm__inst_executed_pipe_alu.avg.peak_sustained = 0.5 warp instructions per cycle per
 # scheduler (4 schedulers x 16 lanes); the issue ceiling above is 4 x 32 lanes.
 ALU_LANES_PER_SM = 64
-# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of
-# `bench.py --profile-case` (dram__bytes_read.sum + dram__bytes_write.sum); None until a capture of
-# the current kernel is taken.
-BB_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one launch of the dominant kernel (k_branch_family on the step), from
+# one ncu capture of `bench.py --profile-case` (dram__bytes_read.sum + dram__bytes_write.sum); set to
+# None when that kernel changes, until it is captured again.
+BB_TRAFFIC_BYTES = 1080064
 
 
 def work_ops(depth, n=N_JOBS, m=N_MACH):
@@ -479,6 +479,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="the timed step, e2e, fsp_bound_pool and the roofline only (no solves, learned order, "
+                         "batch, bound variants or bidirectional runs)")
     ap.add_argument("--profile-case", action="store_true",
                     help="one B&B step and one 2^18-node bounding launch, nothing else (for ncu)")
     ap.add_argument("--profile-learned", action="store_true",
@@ -642,14 +645,15 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "bound_pool": bp,
-            "bound_variants": bound_variants(fsp),
-            "bidirectional": bidir_vs_forward(fsp),
             "phase_ms": {"select": r["select_ms"], "branch_bound": r["bound_ms"], "compact": r["compact_ms"]},
             "wall_s": t_wall,
-            "solves": solve_times(fsp),
-            "learned_order": learned_vs_plain(fsp),
-            "batch": batch_solve(fsp),
         }
+        if not args.no_extras:
+            line["bound_variants"] = bound_variants(fsp)
+            line["bidirectional"] = bidir_vs_forward(fsp)
+            line["solves"] = solve_times(fsp)
+            line["learned_order"] = learned_vs_plain(fsp)
+            line["batch"] = batch_solve(fsp)
         if world == 1 and not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(p, ub, frontier, big, bp[str(2**18)]["nodes_per_s"])
         print(json.dumps(line), flush=True)
