@@ -401,27 +401,44 @@ def batch_solve(fsp):
     t0 = time.perf_counter()
     pools = fsp.fsp_batch_tune_pools(instances, probe_budget=100_000)
     t_tune = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    warps = fsp.fsp_batch_tune_warps(instances, pools, probe_budget=100_000)
+    t_tune_w = time.perf_counter() - t0
     B = fsp.Batch(instances, pools, np.full(BATCH_COUNT, BATCH_BUDGET, np.int64))
-    B.run()
-    B.results()  # warm-up launch
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    B.run()
-    res = B.results()
-    t_batch = time.perf_counter() - t1
+
+    def timed():
+        B.run()
+        B.results()  # warm-up launch
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        B.run()
+        out = B.results()
+        return out, time.perf_counter() - t1
+
+    res, t_batch = timed()  # whole instances, 8 warps per CTA for every shape
     solved = sum(r["status"] == fsp.OK for r in res)
     nodes = sum(r["nodes_bounded"] for r in res)
     # split mode: the roots' subtrees as work items, a shared UB per instance
     B.set_split(True)
-    B.run()
-    B.results()
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    B.run()
-    res_s = B.results()
-    t_split = time.perf_counter() - t1
+    res_s, t_split = timed()
+    # the block shape tuned per shape, whole instances and split
+    B.set_warps(warps)
     B.set_split(False)
-    # bidirectional branching in the batch, whole instances and split
+    res_w, t_w = timed()
+    B.set_split(True)
+    res_ws, t_ws = timed()
+    B.set_split(False)
+    tuned = {"whole": {"batch_s": t_w, "solved_in_batch": sum(r["status"] == fsp.OK for r in res_w),
+                       "batch_nodes_per_s": sum(r["nodes_bounded"] for r in res_w) / t_w,
+                       "same_results_as_8_warps": all(
+                           {k: v for k, v in a.items() if k != "perm"} == {k: v for k, v in b.items() if k != "perm"}
+                           for a, b in zip(res, res_w))},
+             "split": {"batch_s": t_ws, "solved_in_batch": sum(r["status"] == fsp.OK for r in res_ws),
+                       "batch_nodes_per_s": sum(r["nodes_bounded"] for r in res_ws) / t_ws,
+                       "same_optima": all(a["cmax"] == b["cmax"] for a, b in zip(res, res_ws)
+                                          if a["status"] == fsp.OK and b["status"] == fsp.OK)},
+             "tune_s": t_tune_w}
+    # bidirectional branching in the batch (tuned block shapes), whole instances and split
     bidir = {}
     for mode in ("whole", "split"):
         B.set_bidir(True)
@@ -458,14 +475,14 @@ def batch_solve(fsp):
         inst.close()
     t_left = time.perf_counter() - t2
     per_shape = {}
-    for (n, m, _), r in zip(shapes, res):
-        d = per_shape.setdefault(f"{n}x{m}", {"pool": r["pool"], "solved": 0, "count": 0})
+    for (n, m, _), r, w in zip(shapes, res, warps):
+        d = per_shape.setdefault(f"{n}x{m}", {"pool": r["pool"], "warps": int(w), "solved": 0, "count": 0})
         d["count"] += 1
         d["solved"] += r["status"] == fsp.OK
     B.close()
     return {"instances": BATCH_COUNT, "solved_in_batch": solved, "batch_s": t_batch,
             "batch_nodes_bounded": nodes, "batch_nodes_per_s": nodes / t_batch, "tune_s": t_tune,
-            "split": split, "bidirectional": bidir,
+            "warps_per_cta": 8, "split": split, "tuned_block_shapes": tuned, "bidirectional": bidir,
             "node_budget_per_instance": BATCH_BUDGET, "leftovers": BATCH_COUNT - solved,
             "leftovers_finished": finished, "leftover_branching": "bidirectional", "leftover_s": t_left,
             "leftover_nodes": left_nodes,
@@ -533,8 +550,12 @@ def main():
 
     # the step through the public API: a prepared fsp_solve (options, workspace and result
     # buffers built once; every run() is one call into the library)
-    calls = {id(x): fsp.SolveCall(inst, ub0=ub, pool_size=POOL, init_nodes=x, max_iterations=1, workspace=ws,
-                                  profile=True) for x in (front_dev, front_host)}
+    calls = {id(x): fsp.SolveCall(inst, ub0=ub, pool_size=POOL, init_nodes=x, max_iterations=1, workspace=ws)
+             for x in (front_dev, front_host)}
+    # the same call with the library's phase events (select, branch + bound, compaction), which
+    # time the dominant kernel for the roofline in a second timed region of identical steps
+    prof_call = fsp.SolveCall(inst, ub0=ub, pool_size=POOL, init_nodes=front_dev, max_iterations=1, workspace=ws,
+                              profile=True)
 
     def step(init):
         return calls[id(init)].run()
@@ -569,11 +590,20 @@ def main():
             ev[i][0].record(st)
             r = step(front_dev)
             ev[i][1].record(st)
-            bound_ms.append(r["bound_ms"])
             bounded += r["nodes_bounded"]
             launches += 2 + 4 * r["iterations"]  # k_solve_init_nodes, k_init_cum; per iteration select, branch-bound, count, push
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall
+        # the same steps with the phase events: the dominant kernel's duration (roofline)
+        phases = {"select": [], "branch_bound": [], "compact": []}
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            rp = prof_call.run()
+            bound_ms.append(rp["bound_ms"])
+            phases["select"].append(rp["select_ms"])
+            phases["branch_bound"].append(rp["bound_ms"])
+            phases["compact"].append(rp["compact_ms"])
+        torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -645,7 +675,7 @@ def main():
             "clocks": clk.summary(),
             "e2e": e2e,
             "bound_pool": bp,
-            "phase_ms": {"select": r["select_ms"], "branch_bound": r["bound_ms"], "compact": r["compact_ms"]},
+            "phase_ms": {k: statistics.mean(v) for k, v in phases.items()},
             "wall_s": t_wall,
         }
         if not args.no_extras:

@@ -394,9 +394,14 @@ int fsp_pair_order(fsp_instance *inst, fsp_mlp *mlp, const uint8_t *nodes, int64
  * the next instance from a device work queue and runs the whole search of
  * fsp_solve for it (same rules, the instance's own pool size) with the
  * NEH makespan as initial UB (or the given ub0), under the instance's node
- * budget.  The queue reset and the kernel are one CUDA graph, captured at
- * creation and replayed by fsp_batch_run.  Shapes: m = 5 or 10 with
- * n <= 15, 16..31 or 48..63 jobs, and m = 20 with 16..31 jobs.
+ * budget.  Instances are grouped into classes of one shape and one block
+ * shape (warps per CTA, 8 by default, set per instance with
+ * fsp_batch_set_warps); each class is one launch of the persistent kernel
+ * with its own CTA size, shared memory, grid (its occupancy times the SMs)
+ * and work queue, and the launches of all classes are parallel branches of
+ * one CUDA graph, captured at creation and replayed by fsp_batch_run.
+ * Shapes: m = 5 or 10 with n <= 15, 16..31 or 48..63 jobs, and m = 20 with
+ * 16..31 jobs.
  * --------------------------------------------------------------------- */
 typedef struct fsp_batch fsp_batch;
 
@@ -452,6 +457,26 @@ int fsp_batch_set_bidir(fsp_batch *batch, int on);
  * written for every instance of that shape to pools_out (host, count). */
 int fsp_batch_tune_pools(int count, const int32_t *shapes, const int32_t *p_flat, int64_t probe_budget,
                          int64_t *pools_out);
+
+/* Block shape per instance: warps (host, count; 0 = the default 8, else
+ * 1..16) warps per CTA of the launch that solves it; NULL resets all to 8.
+ * Instances of one shape with one block shape form a class (one launch).
+ * The results do not depend on the block shape (whole-instance searches are
+ * the same search; split mode reaches the same optima).  Synchronises the
+ * device, rebuilds the classes' scratch and re-captures the graph.  Errors:
+ * FSP_ERR_ARG (a count outside 0..16, or a block shape whose shared memory
+ * does not fit a CTA; nothing changes), FSP_ERR_OOM, FSP_ERR_CUDA. */
+int fsp_batch_set_warps(fsp_batch *batch, const int32_t *warps);
+
+/* Block shape per shape on measured throughput: for each shape, up to 8 of
+ * its instances (pools from `pools`, probe_budget nodes each), repeated until
+ * their split-mode items fill every SM twice at 4 warps per CTA, run as one
+ * split-mode batch with 4, 8 and 16 warps per CTA (those whose shared memory
+ * fits); the block shape with the most nodes bounded per second is written
+ * for every instance of that shape to warps_out (host, count).  Not in the
+ * paper, which tunes the pool size only (Algorithm 1). */
+int fsp_batch_tune_warps(int count, const int32_t *shapes, const int32_t *p_flat, const int64_t *pools,
+                         int64_t probe_budget, int32_t *warps_out);
 
 /* Message of the last error on this thread ("" if none). */
 const char *fsp_last_error(void);

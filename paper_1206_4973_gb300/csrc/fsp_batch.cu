@@ -8,12 +8,14 @@
 
 #include "fsp_batch.cuh"
 
-template __global__ void k_batch<false>(const BatchDesc *, int, const int32_t *, BatchOut *, uint8_t *, int *, BatchWs);
-template __global__ void k_batch_split<false>(const BatchDesc *, const int32_t *, int *, BatchWs, BatchSplit);
+template __global__ void k_batch<false>(const BatchDesc *, const int *, int, const int32_t *, BatchOut *, uint8_t *,
+                                        int *, BatchWs);
+template __global__ void k_batch_split<false>(const BatchDesc *, const int *, int, const int32_t *, int *, BatchWs,
+                                              BatchSplit);
 
 // The bidirectional instantiations (fsp_batch_bidir.cu).
-typedef void (*BatchFn)(const BatchDesc *, int, const int32_t *, BatchOut *, uint8_t *, int *, BatchWs);
-typedef void (*BatchSplitFn)(const BatchDesc *, const int32_t *, int *, BatchWs, BatchSplit);
+typedef void (*BatchFn)(const BatchDesc *, const int *, int, const int32_t *, BatchOut *, uint8_t *, int *, BatchWs);
+typedef void (*BatchSplitFn)(const BatchDesc *, const int *, int, const int32_t *, int *, BatchWs, BatchSplit);
 BatchFn batch_kernel_bidir();
 BatchSplitFn batch_split_kernel_bidir();
 
@@ -72,21 +74,36 @@ __global__ void k_batch_split_finish(const BatchDesc *__restrict__ desc, int cou
 
 // ------------------------------------------------------------------ host --
 
+// The instances of one shape that run with one block shape (warps per CTA):
+// one launch of the persistent kernel with its own shared-memory size, grid,
+// work list, queue and scratch.  The launches of all classes are parallel
+// branches of the batch's graph.
+struct BatchClass {
+    int n, m, warps;
+    std::vector<int> inst;   // instance indices, in batch order
+    std::vector<int> items;  // their split-mode items, in item order
+    int *d_list = nullptr;   // the instance indices, then the item indices
+    size_t smem = 0;         // dynamic shared memory per CTA (the larger of forward and bidirectional)
+    int grid_max = 0;        // CTAs the scratch holds
+    BatchWs ws{};
+};
+
 struct fsp_batch {
-    int count, device, sm_count, grid;
+    int count, device, sm_count, optin;
     BatchDesc *d_desc;
     int32_t *d_p;
     BatchOut *d_out;
     uint8_t *d_perms;
-    int *d_queue;
-    BatchWs ws;
-    size_t smem;
+    int *d_queue = nullptr;  // one counter per class
     std::vector<BatchDesc> desc;
+    std::vector<int> warps;  // block shape per instance
+    std::vector<BatchClass> cls;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     bool split = false, bidir = false;
     BatchSplit X{};
     int *d_item = nullptr;  // item instances, then item jobs
+    std::vector<int> item_inst;
 };
 
 static bool batch_shape_ok(int n, int m, bool bidir = false)
@@ -99,43 +116,185 @@ static bool batch_shape_ok(int n, int m, bool bidir = false)
     return false;
 }
 
+static void batch_free_classes(fsp_batch *B)
+{
+    for (BatchClass &c : B->cls) {
+        cudaFree(c.d_list);
+        cudaFree(c.ws.stack);
+        cudaFree(c.ws.children);
+        cudaFree(c.ws.lbs);
+    }
+    B->cls.clear();
+    cudaFree(B->d_queue);
+    B->d_queue = nullptr;
+}
 
 static void batch_free(fsp_batch *B)
 {
     if (!B) return;
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
-    cudaFree(B->d_desc); cudaFree(B->d_p); cudaFree(B->d_out); cudaFree(B->d_perms); cudaFree(B->d_queue);
-    cudaFree(B->ws.stack); cudaFree(B->ws.children); cudaFree(B->ws.lbs);
+    batch_free_classes(B);
+    cudaFree(B->d_desc); cudaFree(B->d_p); cudaFree(B->d_out); cudaFree(B->d_perms);
     cudaFree(B->d_item); cudaFree(B->X.ub); cudaFree(B->X.key); cudaFree(B->X.cnt); cudaFree(B->X.flags);
     cudaFree(B->X.item_perm);
     delete B;
 }
 
+static const void *batch_kernel(bool split, bool bidir)
+{
+    if (split) return bidir ? (const void *)batch_split_kernel_bidir() : (const void *)&k_batch_split<false>;
+    return bidir ? (const void *)batch_kernel_bidir() : (const void *)&k_batch<false>;
+}
+
+// Dynamic shared memory a batch CTA may use: the opt-in limit less the
+// kernels' static shared memory.
+static int batch_smem_limit(int optin)
+{
+    size_t st = 0;
+    for (int k = 0; k < 4; ++k) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, batch_kernel(k & 1, k >> 1)) == cudaSuccess) st = std::max(st, a.sharedSizeBytes);
+    }
+    return optin - (int)st;
+}
+
+// Group the instances by (shape, warps) and give each class its lists, its
+// shared-memory size, the most CTAs it can run at once (the four kernels'
+// occupancy at its block shape) and its scratch.
+static int batch_build_classes(fsp_batch *B)
+{
+    batch_free_classes(B);
+    for (int i = 0; i < B->count; ++i) {
+        const BatchDesc &d = B->desc[i];
+        BatchClass *c = nullptr;
+        for (BatchClass &x : B->cls)
+            if (x.n == d.n && x.m == d.m && x.warps == B->warps[i]) c = &x;
+        if (!c) {
+            B->cls.emplace_back();
+            c = &B->cls.back();
+            c->n = d.n;
+            c->m = d.m;
+            c->warps = B->warps[i];
+        }
+        c->inst.push_back(i);
+    }
+    // the classes with the most work per instance (n x m) first: their launches go out first
+    std::stable_sort(B->cls.begin(), B->cls.end(), [](const BatchClass &a, const BatchClass &b) {
+        return a.n * a.m > b.n * b.m;
+    });
+    for (int it = 0; it < (int)B->item_inst.size(); ++it)
+        for (BatchClass &x : B->cls) {
+            const BatchDesc &d = B->desc[B->item_inst[it]];
+            if (x.n == d.n && x.m == d.m && x.warps == B->warps[B->item_inst[it]]) x.items.push_back(it);
+        }
+    size_t smem_max = 0;
+    for (BatchClass &c : B->cls) {
+        c.smem = std::max(batch_smem_nm(c.n, c.m, false, c.warps), batch_smem_nm(c.n, c.m, true, c.warps));
+        const int limit = batch_smem_limit(B->optin);
+        if ((int)c.smem > limit) {
+            fsp_set_error("fsp_batch: %dx%d instances with %d warps need %zu bytes of shared memory per CTA "
+                          "(at most %d)", c.n, c.m, c.warps, c.smem, limit);
+            return FSP_ERR_ARG;
+        }
+        smem_max = std::max(smem_max, c.smem);
+    }
+    for (int k = 0; k < 4; ++k)
+        FSP_CUDA(cudaFuncSetAttribute(batch_kernel(k & 1, k >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_max));
+    FSP_CUDA(cudaMalloc(&B->d_queue, sizeof(int) * B->cls.size()));
+    for (BatchClass &c : B->cls) {
+        int per_sm = 1 << 30;
+        for (int k = 0; k < 4; ++k) {
+            int o = 0;
+            FSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, batch_kernel(k & 1, k >> 1), c.warps * 32,
+                                                                   c.smem));
+            per_sm = std::min(per_sm, o);
+        }
+        if (per_sm < 1) {
+            fsp_set_error("fsp_batch: no CTA of %d warps fits an SM for %dx%d instances", c.warps, c.n, c.m);
+            return FSP_ERR_ARG;
+        }
+        const int work = (int)std::max(c.inst.size(), c.items.size());
+        c.grid_max = std::min(B->sm_count * per_sm, work);
+        long long pool_max = 1;
+        for (int i : c.inst) pool_max = std::max(pool_max, (long long)B->desc[i].pool);
+        c.ws.stride_max = (c.n + 2 + 15) / 16 * 16;  // wide enough for bidirectional records
+        c.ws.cap = (long long)c.n * (pool_max + c.n);
+        c.ws.ch_cap = pool_max + c.n;
+        const size_t g = (size_t)c.grid_max;
+        FSP_CUDA(cudaMalloc(&c.ws.stack, g * c.ws.cap * c.ws.stride_max));
+        FSP_CUDA(cudaMalloc(&c.ws.children, g * c.ws.ch_cap * c.ws.stride_max));
+        FSP_CUDA(cudaMalloc(&c.ws.lbs, g * c.ws.ch_cap * sizeof(int32_t)));
+        std::vector<int> list(c.inst);
+        list.insert(list.end(), c.items.begin(), c.items.end());
+        FSP_CUDA(cudaMalloc(&c.d_list, sizeof(int) * list.size()));
+        FSP_CUDA(cudaMemcpy(c.d_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice));
+    }
+    return FSP_OK;
+}
+
+// The graph: the queues cleared; (split) the instances' UBs; every class's
+// persistent kernel on a branch of its own; (split) the results.
 static int batch_capture(fsp_batch *B)
 {
     if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    const int nc = (int)B->cls.size();
     cudaStream_t st;
     FSP_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
+    std::vector<cudaStream_t> side(nc, nullptr);
+    std::vector<cudaEvent_t> done(nc, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        e = cudaStreamCreateWithFlags(&side[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[c], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    const bool capturing = e == cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int) * nc, st);
+    if (e == cudaSuccess && B->split) {
+        k_batch_split_init<<<B->count, BB, 0, st>>>(B->d_desc, B->d_p, B->d_perms, B->X);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(fork, st);
     const BatchFn kb = B->bidir ? batch_kernel_bidir() : &k_batch<false>;
     const BatchSplitFn ks = B->bidir ? batch_split_kernel_bidir() : &k_batch_split<false>;
-    if (e == cudaSuccess && !B->split) {
-        kb<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->count, B->d_p, B->d_out, B->d_perms, B->d_queue, B->ws);
-        e = cudaGetLastError();
-    } else if (e == cudaSuccess) {
-        k_batch_split_init<<<B->count, BB, 0, st>>>(B->d_desc, B->d_p, B->d_perms, B->X);
-        ks<<<B->grid, BB, B->smem, st>>>(B->d_desc, B->d_p, B->d_queue, B->ws, B->X);
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        const BatchClass &C = B->cls[c];
+        e = cudaStreamWaitEvent(side[c], fork, 0);
+        if (e != cudaSuccess) break;
+        const int len = B->split ? (int)C.items.size() : (int)C.inst.size();
+        const int grid = std::min(C.grid_max, len);
+        if (grid > 0) {
+            if (B->split)
+                ks<<<grid, C.warps * 32, C.smem, side[c]>>>(B->d_desc, C.d_list + C.inst.size(), len, B->d_p,
+                                                             B->d_queue + c, C.ws, B->X);
+            else
+                kb<<<grid, C.warps * 32, C.smem, side[c]>>>(B->d_desc, C.d_list, len, B->d_p, B->d_out, B->d_perms,
+                                                             B->d_queue + c, C.ws);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(done[c], side[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, done[c], 0);
+    }
+    if (e == cudaSuccess && B->split) {
         k_batch_split_finish<<<B->count, 64, 0, st>>>(B->d_desc, B->count, B->d_out, B->d_perms, B->X);
         e = cudaGetLastError();
     }
-    cudaGraph_t g = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(st, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
-    B->graph = g;
+    if (capturing) {
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, g, 0);
+        B->graph = g;
+    }
+    for (int c = 0; c < nc; ++c) {
+        if (side[c]) cudaStreamDestroy(side[c]);
+        if (done[c]) cudaEventDestroy(done[c]);
+    }
+    if (fork) cudaEventDestroy(fork);
     cudaStreamDestroy(st);
     if (e != cudaSuccess) return fsp_cuda_fail(e, "batch graph capture");
     return FSP_OK;
@@ -152,8 +311,6 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
     fsp_batch *B = new fsp_batch();
     B->count = count;
     long long off = 0;
-    int n_max = 2, m_max = 5, s_max = 16;
-    size_t smem_max = 0;
     for (int i = 0; i < count; ++i) {
         const int n = shapes[2 * i], m = shapes[2 * i + 1];
         if (!batch_shape_ok(n, m) || pools[i] < 1 || pools[i] > POOL_MAX) {
@@ -174,56 +331,85 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
         d.budget = budgets ? budgets[i] : 0;
         B->desc.push_back(d);
         off += (long long)n * m;
-        if (n > n_max) n_max = n;
-        if (m > m_max) m_max = m;
-        smem_max = std::max(smem_max, std::max(batch_smem_nm(n, m), batch_smem_nm(n, m, true)));
-        const int s = (n + 2 + 15) / 16 * 16;  // wide enough for bidirectional records
-        if (s > s_max) s_max = s;
     }
+    B->warps.assign(count, BB / 32);
+    // split-mode work items: the instances with the most work (n x m) first,
+    // each as the n subtrees of its root (the root itself when n <= 2)
+    std::vector<int> order(count), item_job;
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long long)B->desc[a].n * B->desc[a].m > (long long)B->desc[b].n * B->desc[b].m;
+    });
+    for (int i : order) {
+        if (B->desc[i].n <= 2) {
+            B->item_inst.push_back(i);
+            item_job.push_back(-1);
+            continue;
+        }
+        for (int j = 0; j < B->desc[i].n; ++j) { B->item_inst.push_back(i); item_job.push_back(j); }
+    }
+    const int items = (int)B->item_inst.size();
     int rc = FSP_OK;
     cudaError_t e;
 #define TRYB(call) do { e = (call); if (e != cudaSuccess) { rc = fsp_cuda_fail(e, #call); goto fail; } } while (0)
     TRYB(cudaGetDevice(&B->device));
     TRYB(cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, B->device));
-    {
-        int optin = 0;
-        TRYB(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, B->device));
-        B->smem = smem_max;
-        if ((int)B->smem > optin) {
-            fsp_set_error("fsp_batch_create: instances too large for one CTA's shared memory");
-            rc = FSP_ERR_ARG;
-            goto fail;
-        }
-        const void *kern[4] = {(const void *)&k_batch<false>, (const void *)&k_batch_split<false>,
-                               (const void *)batch_kernel_bidir(), (const void *)batch_split_kernel_bidir()};
-        for (const void *k : kern)
-            TRYB(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B->smem));
-        int per_sm = 0, per_sm_b = 0;
-        TRYB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern[0], BB, B->smem));
-        TRYB(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_b, kern[2], BB, B->smem));
-        per_sm = std::min(per_sm, per_sm_b);
-        B->grid = B->sm_count * (per_sm > 0 ? per_sm : 1);
-        if (B->grid > count) B->grid = count;
-    }
-    B->ws.stride_max = s_max;
-    B->ws.cap = (long long)n_max * (POOL_MAX + n_max);
+    TRYB(cudaDeviceGetAttribute(&B->optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, B->device));
     TRYB(cudaMalloc(&B->d_desc, sizeof(BatchDesc) * count));
     TRYB(cudaMalloc(&B->d_p, sizeof(int32_t) * off));
     TRYB(cudaMalloc(&B->d_out, sizeof(BatchOut) * count));
     TRYB(cudaMalloc(&B->d_perms, (size_t)FSP_MAX_JOBS * count));
-    TRYB(cudaMalloc(&B->d_queue, sizeof(int)));
-    TRYB(cudaMalloc(&B->ws.stack, (size_t)B->grid * B->ws.cap * s_max));
-    TRYB(cudaMalloc(&B->ws.children, (size_t)B->grid * (POOL_MAX + FSP_MAX_JOBS) * s_max));
-    TRYB(cudaMalloc(&B->ws.lbs, (size_t)B->grid * (POOL_MAX + FSP_MAX_JOBS) * sizeof(int32_t)));
     TRYB(cudaMemcpy(B->d_desc, B->desc.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice));
     TRYB(cudaMemcpy(B->d_p, p_flat, sizeof(int32_t) * off, cudaMemcpyHostToDevice));
+    TRYB(cudaMalloc(&B->d_item, sizeof(int) * 2 * (size_t)items));
+    TRYB(cudaMemcpy(B->d_item, B->item_inst.data(), sizeof(int) * items, cudaMemcpyHostToDevice));
+    TRYB(cudaMemcpy(B->d_item + items, item_job.data(), sizeof(int) * items, cudaMemcpyHostToDevice));
+    TRYB(cudaMalloc(&B->X.ub, sizeof(int) * count));
+    TRYB(cudaMalloc(&B->X.key, sizeof(unsigned long long) * count));
+    TRYB(cudaMalloc(&B->X.cnt, sizeof(long long) * 6 * count));
+    TRYB(cudaMalloc(&B->X.flags, sizeof(int) * count));
+    TRYB(cudaMalloc(&B->X.item_perm, (size_t)FSP_MAX_JOBS * items));
 #undef TRYB
+    B->X.item_inst = B->d_item;
+    B->X.item_job = B->d_item + items;
+    B->X.items = items;
+    if ((rc = batch_build_classes(B)) != FSP_OK) goto fail;
     if ((rc = batch_capture(B)) != FSP_OK) goto fail;
     *out = B;
     return FSP_OK;
 fail:
     batch_free(B);
     return rc;
+}
+
+extern "C" int fsp_batch_set_warps(fsp_batch *B, const int32_t *warps)
+{
+    if (!B) { fsp_set_error("fsp_batch_set_warps: NULL batch"); return FSP_ERR_ARG; }
+    std::vector<int> w(B->count, BB / 32);
+    if (warps)
+        for (int i = 0; i < B->count; ++i) {
+            if (warps[i] < 0 || warps[i] > BB_MAX / 32) {
+                fsp_set_error("fsp_batch_set_warps: instance %d: %d warps (0 = default, 1..%d)", i, warps[i],
+                              BB_MAX / 32);
+                return FSP_ERR_ARG;
+            }
+            w[i] = warps[i] ? warps[i] : BB / 32;
+        }
+    const int limit = batch_smem_limit(B->optin);
+    for (int i = 0; i < B->count; ++i) {
+        const size_t need = std::max(batch_smem_nm(B->desc[i].n, B->desc[i].m, false, w[i]),
+                                     batch_smem_nm(B->desc[i].n, B->desc[i].m, true, w[i]));
+        if ((int)need > limit) {
+            fsp_set_error("fsp_batch_set_warps: instance %d (%dx%d) with %d warps needs %zu bytes of shared memory "
+                          "(at most %d); nothing changed", i, B->desc[i].n, B->desc[i].m, w[i], need, limit);
+            return FSP_ERR_ARG;
+        }
+    }
+    FSP_CUDA(cudaDeviceSynchronize());  // the old scratch may still be in use by a launch
+    B->warps = w;
+    int rc = batch_build_classes(B);
+    if (rc != FSP_OK) return rc;
+    return batch_capture(B);
 }
 
 extern "C" int fsp_batch_set_bidir(fsp_batch *B, int on)
@@ -243,35 +429,6 @@ extern "C" int fsp_batch_set_bidir(fsp_batch *B, int on)
 extern "C" int fsp_batch_set_split(fsp_batch *B, int on)
 {
     if (!B) { fsp_set_error("fsp_batch_set_split: NULL batch"); return FSP_ERR_ARG; }
-    if (on && !B->d_item) {
-        // the work items, the instances with the most jobs (the longest searches) first
-        std::vector<int> order(B->count);
-        for (int i = 0; i < B->count; ++i) order[i] = i;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return (long long)B->desc[a].n * B->desc[a].m > (long long)B->desc[b].n * B->desc[b].m;
-        });
-        std::vector<int> inst, job;
-        for (int i : order) {
-            if (B->desc[i].n <= 2) {  // the root's children are complete schedules: one item, the root
-                inst.push_back(i);
-                job.push_back(-1);
-                continue;
-            }
-            for (int j = 0; j < B->desc[i].n; ++j) { inst.push_back(i); job.push_back(j); }
-        }
-        const int items = (int)inst.size();
-        FSP_CUDA(cudaMalloc(&B->d_item, sizeof(int) * 2 * (size_t)items));
-        FSP_CUDA(cudaMemcpy(B->d_item, inst.data(), sizeof(int) * items, cudaMemcpyHostToDevice));
-        FSP_CUDA(cudaMemcpy(B->d_item + items, job.data(), sizeof(int) * items, cudaMemcpyHostToDevice));
-        FSP_CUDA(cudaMalloc(&B->X.ub, sizeof(int) * B->count));
-        FSP_CUDA(cudaMalloc(&B->X.key, sizeof(unsigned long long) * B->count));
-        FSP_CUDA(cudaMalloc(&B->X.cnt, sizeof(long long) * 6 * B->count));
-        FSP_CUDA(cudaMalloc(&B->X.flags, sizeof(int) * B->count));
-        FSP_CUDA(cudaMalloc(&B->X.item_perm, (size_t)FSP_MAX_JOBS * items));
-        B->X.item_inst = B->d_item;
-        B->X.item_job = B->d_item + items;
-        B->X.items = items;
-    }
     B->split = on != 0;
     return batch_capture(B);
 }
@@ -370,6 +527,86 @@ extern "C" int fsp_batch_tune_pools(int count, const int32_t *shapes, const int3
             if (rate > best) { best = rate; best_pool = c; }
         }
         for (int j : same) { pools_out[j] = best_pool; done[j] = 1; }
+    }
+    return FSP_OK;
+}
+
+// Block shape per shape on measured throughput: for each shape, up to 8 of
+// its instances (with their pools and a node budget each), repeated until
+// their split-mode items fill every SM twice over at the smallest block
+// shape, run as one split-mode batch with each candidate number of warps per
+// CTA that fits; the most nodes bounded per second wins.  Filling the GPU is
+// what makes the comparison fair: a smaller CTA bounds an instance more
+// slowly but more of them share an SM.
+extern "C" int fsp_batch_tune_warps(int count, const int32_t *shapes, const int32_t *p_flat, const int64_t *pools,
+                                    int64_t probe_budget, int32_t *warps_out)
+{
+    if (count < 1 || !shapes || !p_flat || !pools || !warps_out) {
+        fsp_set_error("fsp_batch_tune_warps: invalid argument");
+        return FSP_ERR_ARG;
+    }
+    const int cands[] = {4, 8, 16};
+    int dev = 0, sms = 1, optin = 0;
+    FSP_CUDA(cudaGetDevice(&dev));
+    FSP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int limit = batch_smem_limit(optin);
+    std::vector<long long> off(count + 1, 0);
+    for (int i = 0; i < count; ++i) off[i + 1] = off[i] + (long long)shapes[2 * i] * shapes[2 * i + 1];
+    std::vector<int> done(count, 0);
+    for (int i = 0; i < count; ++i) {
+        if (done[i]) continue;
+        const int n = shapes[2 * i], m = shapes[2 * i + 1];
+        std::vector<int> same;
+        for (int j = i; j < count; ++j)
+            if (shapes[2 * j] == n && shapes[2 * j + 1] == m) same.push_back(j);
+        const int probe = (int)(same.size() < 8 ? same.size() : 8);
+        const int need_items = 2 * sms * 4, per_copy = probe * (n > 2 ? n : 1);
+        const int reps = (need_items + per_copy - 1) / per_copy;
+        std::vector<int32_t> sh, pf;
+        std::vector<int64_t> pl, budgets;
+        for (int r = 0; r < reps; ++r)
+            for (int q = 0; q < probe; ++q) {
+                const int j = same[q];
+                sh.push_back(n);
+                sh.push_back(m);
+                pf.insert(pf.end(), p_flat + off[j], p_flat + off[j + 1]);
+                pl.push_back(pools[j]);
+                budgets.push_back(probe_budget);
+            }
+        const int pc = probe * reps;
+        double best = -1.0;
+        int best_w = BB / 32;
+        for (int w : cands) {
+            const size_t need = std::max(batch_smem_nm(n, m, false, w), batch_smem_nm(n, m, true, w));
+            if ((int)need > limit) continue;
+            fsp_batch *B = nullptr;
+            int rc = fsp_batch_create(pc, sh.data(), pf.data(), pl.data(), budgets.data(), nullptr, &B);
+            if (rc != FSP_OK) return rc;
+            std::vector<int32_t> ws(pc, w);
+            rc = fsp_batch_set_warps(B, ws.data());
+            if (rc == FSP_OK) rc = fsp_batch_set_split(B, 1);
+            if (rc != FSP_OK) { fsp_batch_destroy(B); return rc; }
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, 0);
+            rc = fsp_batch_run(B, 0);
+            cudaEventRecord(e1, 0);
+            std::vector<fsp_batch_result> r(pc);
+            if (rc == FSP_OK) rc = fsp_batch_results(B, r.data(), nullptr, 0);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            fsp_batch_destroy(B);
+            if (rc != FSP_OK) return rc;
+            long long nodes = 0;
+            for (auto &x : r) nodes += x.nodes_bounded;
+            const double rate = ms > 0 ? nodes / (double)ms : 0.0;
+            if (rate > best) { best = rate; best_w = w; }
+        }
+        for (int j : same) { warps_out[j] = best_w; done[j] = 1; }
     }
     return FSP_OK;
 }

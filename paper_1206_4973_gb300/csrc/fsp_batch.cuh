@@ -16,7 +16,8 @@
 
 #include "fsp_family.cuh"
 
-#define BB 256        // threads per CTA
+#define BB 256        // threads per CTA of the helper kernels and the default batch CTA
+#define BB_MAX 512    // most threads of a batch CTA (16 warps; the block shape is chosen per shape)
 
 // Shapes of the batch kernel: machines MT x record vectors NV x mask words NW
 // (n <= 15, <= 31, <= 63 jobs; m = 5, 10, 20).
@@ -38,10 +39,11 @@ struct BatchOut {  // one result (device; mirrored by fsp_batch_result)
     long long bounded, branched, pruned, leaves, iterations, updates;
 };
 
-struct BatchWs {  // per-CTA scratch in global memory
+struct BatchWs {  // per-CTA scratch in global memory (one slice per CTA of a class's launch)
     uint8_t *stack, *children;
     int32_t *lbs;
-    long long cap;  // records per stack
+    long long cap;     // records per stack
+    long long ch_cap;  // children per iteration (the class's largest pool + n)
     int stride_max;
 };
 
@@ -68,13 +70,14 @@ __device__ __forceinline__ int b_block_incl_scan(int v, int *warp_tot)
     if (lane == 31) warp_tot[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        int t = lane < BB / 32 ? warp_tot[lane] : 0;
+        const int nw = (int)(blockDim.x >> 5);
+        int t = lane < nw ? warp_tot[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(0xffffffffu, t, o);
             if (lane >= o) t += u;
         }
-        if (lane < BB / 32) warp_tot[lane] = t;
+        if (lane < nw) warp_tot[lane] = t;
     }
     __syncthreads();
     const int add = wid > 0 ? warp_tot[wid - 1] : 0;
@@ -86,7 +89,7 @@ __device__ __forceinline__ int b_block_sum(int v, int *warp_tot)
 {
     const int incl = b_block_incl_scan(v, warp_tot);
     __shared__ int s_total;
-    if (threadIdx.x == BB - 1) s_total = incl;
+    if (threadIdx.x == blockDim.x - 1) s_total = incl;
     __syncthreads();
     const int t = s_total;
     __syncthreads();
@@ -110,18 +113,19 @@ __device__ __forceinline__ bool b_precedes(int i, int32_t ai, int32_t bi, int32_
 }
 
 struct BatchShared {  // static shared state of a CTA
-    int warp_tot[BB / 32];
+    int warp_tot[BB_MAX / 32];
     uint8_t inc[FSP_MAX_JOBS + 1], seq[FSP_MAX_JOBS + 1], ord[FSP_MAX_JOBS + 1];
     int32_t tot[FSP_MAX_JOBS + 1];
     unsigned long long best_key;
 };
 
-// Shared memory of a batch CTA for an n x m instance: the family layout
-// (fsp_family.cuh) for the CTA's warps, then the parents' first-child offsets.
-__host__ __device__ inline size_t batch_smem_nm(int n, int m, bool bidir = false)
+// Shared memory of a batch CTA of `warps` warps for an n x m instance: the
+// family layout (fsp_family.cuh) for those warps, then the parents'
+// first-child offsets.
+__host__ __device__ inline size_t batch_smem_nm(int n, int m, bool bidir = false, int warps = BB / 32)
 {
     const int mp = (m % 2 == 0) ? m + 1 : m, nv = (n + (bidir ? 2 : 1) + 15) / 16;
-    return fsp_align16(family_smem_layout_nm(n, m, mp, m, nv, BB / 32).bytes) + (size_t)(POOL_MAX / 2 + 4) * 4;
+    return fsp_align16(family_smem_layout_nm(n, m, mp, m, nv, warps).bytes) + (size_t)(POOL_MAX / 2 + 4) * 4;
 }
 
 // NEH upper bound: jobs by decreasing total time, each inserted at the
@@ -130,17 +134,17 @@ __host__ __device__ inline size_t batch_smem_nm(int n, int m, bool bidir = false
 template <int MT>
 __device__ int b_neh(const int32_t *__restrict__ p, int n, BatchShared &sh)
 {
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, NT = (int)blockDim.x;
     uint8_t *seq = sh.seq, *ord = sh.ord;
     int32_t *tot = sh.tot;
     unsigned long long &best_key = sh.best_key;
-    for (int j = tid; j < n; j += BB) {
+    for (int j = tid; j < n; j += NT) {
         int32_t s = 0;
         for (int k = 0; k < MT; ++k) s += p[j * MT + k];
         tot[j] = s;
     }
     __syncthreads();
-    for (int j = tid; j < n; j += BB) {
+    for (int j = tid; j < n; j += NT) {
         int rank = 0;
         for (int i = 0; i < n; ++i) rank += (tot[i] > tot[j]) || (tot[i] == tot[j] && i < j);
         ord[rank] = (uint8_t)j;
@@ -150,7 +154,7 @@ __device__ int b_neh(const int32_t *__restrict__ p, int n, BatchShared &sh)
         const int job = ord[len];
         if (tid == 0) best_key = ~0ull;
         __syncthreads();
-        for (int pos = tid; pos <= len; pos += BB) {
+        for (int pos = tid; pos <= len; pos += NT) {
             int32_t C[MT];
 #pragma unroll
             for (int k = 0; k < MT; ++k) C[k] = 0;
@@ -185,10 +189,10 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
                         const BatchWs &W, unsigned char *smem, BatchShared &sh, const BatchSplit &X, int inst,
                         int item, int job, bool tables_ready)
 {
-    const int n = D.n, tid = threadIdx.x;
+    const int n = D.n, tid = threadIdx.x, NT = (int)blockDim.x, NWP = NT >> 5;
     const int P = MT * (MT - 1) / 2, mp = (MT % 2 == 0) ? MT + 1 : MT;
     const int stride = (n + (BIDIR ? 2 : 1) + 15) / 16 * 16;
-    const FamSmem L = family_smem_layout_nm(n, MT, mp, MT, NV, BB / 32);
+    const FamSmem L = family_smem_layout_nm(n, MT, mp, MT, NV, NWP);
     const FamView V = fam_view(smem, L, tid >> 5);
     int2 *pq_s = V.pq;
     int *poff = reinterpret_cast<int *>(smem + fsp_align16(L.bytes));
@@ -198,13 +202,13 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
 
     // tables: {p, tail} rows and the Johnson entries of every pair
     if (!SPLIT || !tables_ready) {
-    for (int i = tid; i < n * MT; i += BB) {
+    for (int i = tid; i < n * MT; i += NT) {
         const int j = i / MT, k = i - j * MT;
         int32_t q = 0;
         for (int h = k + 1; h < MT; ++h) q += p[j * MT + h];
         pq_s[j * mp + k] = make_int2(p[i], q);
     }
-    for (int e = tid; e < P * n; e += BB) {
+    for (int e = tid; e < P * n; e += NT) {
         const int kl = e / n, j = e - kl * n;
         int k = 0, rem = kl;
         while (rem >= MT - 1 - k) { rem -= MT - 1 - k; ++k; }
@@ -231,7 +235,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         ub = *(volatile int *)&X.ub[inst];
     } else if (ub <= 0) {
         ub = b_neh<MT>(p, n, sh);
-        for (int i = tid; i < n; i += BB) inc[i] = seq[i];
+        for (int i = tid; i < n; i += NT) inc[i] = seq[i];
     }
     __syncthreads();
 
@@ -240,10 +244,10 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
     int status = FSP_OK;
     long long S = 1;
     if (SPLIT && job >= 0) {  // the root's child that schedules `job` first (the rest in increasing order)
-        for (int i = tid; i < stride; i += BB)
+        for (int i = tid; i < stride; i += NT)
             W.stack[i] = (uint8_t)(i == 0 ? job : i < n ? (i - 1 < job ? i - 1 : i) : i == n ? 1 : 0);
     } else {
-        for (int i = tid; i < stride; i += BB) W.stack[i] = (uint8_t)(i < n ? i : 0);
+        for (int i = tid; i < stride; i += NT) W.stack[i] = (uint8_t)(i < n ? i : 0);
     }
     bool improved = false;
     __shared__ int s_ub;
@@ -268,7 +272,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         // selection: deepest parents while their children fit (at least one)
         const long long cand = S < pool ? S : pool;
         long long running = 0, np = 0;
-        for (long long base = 0; base < cand; base += (long long)BB * SEL_Q) {
+        for (long long base = 0; base < cand; base += (long long)NT * SEL_Q) {
             int r[SEL_Q], tsum = 0;
 #pragma unroll
             for (int q = 0; q < SEL_Q; ++q) {
@@ -291,7 +295,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
             const int ct = b_block_sum(taken, warp_tot), cts = b_block_sum(tsum_taken, warp_tot);
             np += ct;
             running += cts;
-            if (ct < BB * SEL_Q) break;
+            if (ct < NT * SEL_Q) break;
         }
         const long long nch = running;
         if (tid == 0) poff[np] = (int)nch;
@@ -299,7 +303,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         if (tid == 0) best_key = ~0ull;
         __syncthreads();
         // branching + bounding: each warp bounds a parent's children together
-        for (long long f = warp; f < np; f += BB / 32) {
+        for (long long f = warp; f < np; f += NWP) {
             if (lane < NV)
                 reinterpret_cast<uint4 *>(V.recb)[lane] =
                     reinterpret_cast<const uint4 *>(W.stack + (S - 1 - f) * stride)[lane];
@@ -314,7 +318,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         const int ub_new = (bk != ~0ull && (int)(bk >> 32) < ub) ? (int)(bk >> 32) : ub;
         if (ub_new < ub) {
             const long long idx = (long long)(bk & 0xffffffffull);
-            for (int i = tid; i < n; i += BB) inc[i] = W.children[idx * stride + i];
+            for (int i = tid; i < n; i += NT) inc[i] = W.children[idx * stride + i];
             updates++;
             if (SPLIT) {
                 improved = true;
@@ -331,7 +335,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
             const uint8_t *ch = W.children + c * stride;
             return (int)ch[n] + (BIDIR ? (int)ch[n + 1] : 0);
         };
-        for (long long c = tid; c < nch; c += BB) {
+        for (long long c = tid; c < nch; c += NT) {
             const bool leaf = depth(c) == n - 1;
             my_l += leaf;
             my_s += !leaf && W.lbs[c] < ub;
@@ -339,7 +343,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         const int total = b_block_sum(my_s, warp_tot), nleaf = b_block_sum(my_l, warp_tot);
         const long long base_s = S - np;
         long long done = 0;
-        for (long long c0 = 0; c0 < nch; c0 += BB) {
+        for (long long c0 = 0; c0 < nch; c0 += NT) {
             const long long c = c0 + tid;
             const bool surv = c < nch && depth(c) != n - 1 && W.lbs[c] < ub;
             const int incl = b_block_incl_scan(surv ? 1 : 0, warp_tot);
@@ -372,7 +376,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
             if (status == FSP_ERR_CAPACITY) atomicOr(&X.flags[inst], 2);
         }
         if (improved)
-            for (int i = tid; i < n; i += BB) X.item_perm[(size_t)item * FSP_MAX_JOBS + i] = inc[i];
+            for (int i = tid; i < n; i += NT) X.item_perm[(size_t)item * FSP_MAX_JOBS + i] = inc[i];
         __syncthreads();
         return;
     }
@@ -386,28 +390,33 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
         out->iterations = iters;
         out->updates = updates;
     }
-    for (int i = tid; i < n; i += BB) perm_out[i] = inc[i];
+    for (int i = tid; i < n; i += NT) perm_out[i] = inc[i];
     __syncthreads();
 }
 
+// The persistent kernels.  A launch serves one class of instances (one shape
+// and block shape): the queue hands out positions 0..len-1 of `list`, which
+// holds the class's instance indices (whole instances) or item indices (split
+// mode); W is the class's scratch, one slice per CTA.
 template <bool BIDIR>
-__global__ void __launch_bounds__(BB) k_batch(const BatchDesc *__restrict__ desc, int count,
-                                              const int32_t *__restrict__ p_flat, BatchOut *out, uint8_t *perms,
-                                              int *queue, BatchWs W)
+__global__ void __launch_bounds__(BB_MAX) k_batch(const BatchDesc *__restrict__ desc, const int *__restrict__ list,
+                                                  int len, const int32_t *__restrict__ p_flat, BatchOut *out,
+                                                  uint8_t *perms, int *queue, BatchWs W)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_inst;
     __shared__ BatchShared sh;
     BatchWs w = W;
     w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
-    w.children = W.children + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS) * W.stride_max;
-    w.lbs = W.lbs + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS);
+    w.children = W.children + (size_t)blockIdx.x * W.ch_cap * W.stride_max;
+    w.lbs = W.lbs + (size_t)blockIdx.x * W.ch_cap;
     for (;;) {
         if (threadIdx.x == 0) s_inst = atomicAdd(queue, 1);
         __syncthreads();
-        const int i = s_inst;
+        const int q = s_inst;
         __syncthreads();
-        if (i >= count) break;
+        if (q >= len) break;
+        const int i = list[q];
         const BatchDesc D = desc[i];
         const int32_t *p = p_flat + D.p_off;
         const int nv = (D.n + (BIDIR ? 2 : 1) + 15) / 16, nw = D.n <= 32 ? 1 : 2;
@@ -425,26 +434,28 @@ __global__ void __launch_bounds__(BB) k_batch(const BatchDesc *__restrict__ desc
 
 // Split mode: the persistent kernel over the work items; a CTA keeps the
 // tables of the instance it last worked on (the items of an instance are
-// consecutive in the queue).
+// consecutive in the list).
 template <bool BIDIR>
-__global__ void __launch_bounds__(BB) k_batch_split(const BatchDesc *__restrict__ desc,
-                                                    const int32_t *__restrict__ p_flat, int *queue, BatchWs W,
-                                                    BatchSplit X)
+__global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restrict__ desc,
+                                                        const int *__restrict__ list, int len,
+                                                        const int32_t *__restrict__ p_flat, int *queue, BatchWs W,
+                                                        BatchSplit X)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     __shared__ BatchShared sh;
     BatchWs w = W;
     w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
-    w.children = W.children + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS) * W.stride_max;
-    w.lbs = W.lbs + (size_t)blockIdx.x * (POOL_MAX + FSP_MAX_JOBS);
+    w.children = W.children + (size_t)blockIdx.x * W.ch_cap * W.stride_max;
+    w.lbs = W.lbs + (size_t)blockIdx.x * W.ch_cap;
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
-        const int item = s_item;
+        const int q = s_item;
         __syncthreads();
-        if (item >= X.items) break;
+        if (q >= len) break;
+        const int item = list[q];
         const int i = X.item_inst[item], job = X.item_job[item];
         const BatchDesc D = desc[i];
         const int32_t *p = p_flat + D.p_off;
@@ -461,4 +472,3 @@ __global__ void __launch_bounds__(BB) k_batch_split(const BatchDesc *__restrict_
         cur = -1;
     }
 }
-

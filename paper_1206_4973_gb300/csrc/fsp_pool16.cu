@@ -88,8 +88,8 @@ __device__ __forceinline__ int p16_rs_dev(int m)
 }
 
 struct Pool16Smem {
-    size_t rows_off, ej_off, klm_off, img_bytes, tab_off, tab_bytes, bytes;
-    int warps;
+    size_t rows_off, ej_off, klm_off, img_bytes, tab_off, tab_bytes, red_off, bytes;
+    int warps, slices;
 };
 
 static inline int p16_rs(int m)
@@ -98,7 +98,7 @@ static inline int p16_rs(int m)
     return (m + 2 * H) | 1;
 }
 
-static inline Pool16Smem pool16_layout(const fsp_instance *I, int warps)
+static inline Pool16Smem pool16_layout(const fsp_instance *I, int warps, int slices = 1)
 {
     Pool16Smem L;
     size_t o = 0;
@@ -109,8 +109,11 @@ static inline Pool16Smem pool16_layout(const fsp_instance *I, int warps)
     L.tab_off = o;
     L.tab_bytes = fsp_align16((size_t)(I->n + 2 * I->m) * P16_TS * 4);
     o += L.tab_bytes * warps;
+    L.red_off = o;
+    if (slices > 1) o += (size_t)warps * 32 * 4;
     L.bytes = o;
     L.warps = warps;
+    L.slices = slices;
     return L;
 }
 
@@ -256,6 +259,11 @@ __device__ __forceinline__ void p16_prologue(const FspRec<NV> &r, int d, int d2,
     }
 }
 
+// S > 1 (small pools, which leave SMs idle at one warp per 32 nodes): a team
+// of S consecutive warps takes each group of 32 nodes, every warp computes the
+// group's tables itself and scans NPASS / S of the passes over the pairs, and
+// the team combines its maxima through shared memory (a named barrier per
+// team; S divides NPASS and the warps per CTA).
 template <int MT, int NV, bool BIDIR>
 __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst I, const uint8_t *__restrict__ img,
                                                                       const uint8_t *__restrict__ nodes,
@@ -272,8 +280,11 @@ __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst 
     const uint16_t *klm_s = reinterpret_cast<const uint16_t *>(smem + L.klm_off);
     const int n = I.n;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int S = L.slices, team = warp / S, slice = warp - team * S, TEAMS = W / S;
+    const int pass0 = slice * (NPASS / S), pass1 = pass0 + NPASS / S;
     uint32_t *tw = reinterpret_cast<uint32_t *>(smem + L.tab_off + warp * L.tab_bytes);
     uint16_t *th = reinterpret_cast<uint16_t *>(tw);
+    int32_t *raise_s = reinterpret_cast<int32_t *>(smem + L.red_off);  // [W][32]: each warp's raises
 
     // stage the image: 16-byte asynchronous copies, all in flight at once
     for (int c = threadIdx.x; c < (int)(L.img_bytes >> 4); c += blockDim.x) {
@@ -285,7 +296,7 @@ __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst 
     __syncthreads();
 
     const long long groups = (count + 31) >> 5;
-    for (long long g = (long long)blockIdx.x * W + warp; g < groups; g += (long long)gridDim.x * W) {
+    for (long long g = (long long)blockIdx.x * TEAMS + team; g < groups; g += (long long)gridDim.x * TEAMS) {
         // -- lane v: node g*32 + v, its one-machine quantities into the tables
         const long long node = (g << 5) + lane;
         FspRec<NV> r;
@@ -315,7 +326,7 @@ __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst 
 #pragma unroll
         for (int q = 0; q < 16; ++q) acc[q] = 0u;
 #pragma unroll 1
-        for (int pass = 0; pass < NPASS; ++pass) {
+        for (int pass = pass0; pass < pass1; ++pass) {
             const int kl_raw = pass * 32 + lane;
             const bool live = kl_raw < P;
             const int kl = live ? kl_raw : P - 1;
@@ -358,8 +369,15 @@ __global__ void __launch_bounds__(P16_MAX_WARPS * 32, 1) k_bound_pool16(DevInst 
             }
         }
         const uint32_t v = p16_max(acc[0], __shfl_xor_sync(0xffffffffu, acc[0], 1));
-        const int32_t raise = (int32_t)((lane & 1) ? (v >> 16) : (v & 0xFFFFu));
-        if (node < count) {
+        int32_t raise = (int32_t)((lane & 1) ? (v >> 16) : (v & 0xFFFFu));
+        if (S > 1) {  // the team's maximum over its slices of the pairs
+            raise_s[warp * 32 + lane] = raise;
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(S * 32) : "memory");
+            if (slice == 0)
+                for (int w = 1; w < S; ++w) raise = max(raise, raise_s[(warp + w) * 32 + lane]);
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + team), "r"(S * 32) : "memory");  // raise_s reused next
+        }
+        if (node < count && slice == 0) {
             int32_t lb = lb1 + raise;
             if (bad) {
                 lb = FSP_LB_INVALID;
@@ -414,7 +432,10 @@ int pool16_build(fsp_instance *I)
 // Launch on a pool of count nodes; FSP_ERR_ARG (nothing launched) when the
 // instance is not eligible or its tables do not fit.  warps = 0: the default
 // CTA shape: 8 warps, fewer when the pool has fewer than 8 groups of 32 nodes
-// per SM, so that a small pool still spreads over every SM.
+// per SM, so that a small pool still spreads over every SM; and when even one
+// warp per group leaves most of the GPU's 16 warps per SM idle, teams of S
+// warps per group (the largest divisor S of the passes over the pairs that
+// keeps groups x S within SMs x 16).  FSP_POOL16_SLICES sets S (tests).
 int pool16_bound(fsp_instance *I, const uint8_t *nodes, long long count, int32_t *lb_out, cudaStream_t st,
                  int warps)
 {
@@ -432,20 +453,36 @@ int pool16_bound_ex(fsp_instance *I, const uint8_t *nodes, long long count, cons
     Pool16Fn fn = pick_pool16(fsp_mt(I->m), stride / 16, bidir);
     if (!fn) return FSP_ERR_ARG;
     const long long groups = (count + 31) / 32;
-    if (warps <= 0) {
+    const int npass = (I->P + 31) / 32;
+    int slices = 1;
+    const char *es = getenv("FSP_POOL16_SLICES");
+    if (es) {
+        slices = atoi(es);
+        if (slices < 1 || npass % slices != 0) slices = 1;
+    } else if (warps <= 0) {
+        for (int sl = npass; sl > 1; --sl)
+            if (npass % sl == 0 && groups * sl <= (long long)I->sm_count * 16) { slices = sl; break; }
+    }
+    if (slices > 1) {
+        warps = slices * (8 / slices > 1 ? 8 / slices : 1);
+    } else if (warps <= 0) {
         const long long per_sm = (groups + I->sm_count - 1) / I->sm_count;
         warps = per_sm >= 16 ? 8 : per_sm >= 2 ? (int)((per_sm + 1) / 2) : 1;
     }
     if (warps > P16_MAX_WARPS) warps = P16_MAX_WARPS;
-    Pool16Smem L = pool16_layout(I, warps);
-    while (warps > 1 && (int)L.bytes > I->smem_optin) L = pool16_layout(I, --warps);
+    Pool16Smem L = pool16_layout(I, warps, slices);
+    while (warps > slices && (int)L.bytes > I->smem_optin) {
+        warps -= slices;
+        L = pool16_layout(I, warps, slices);
+    }
     if ((int)L.bytes > I->smem_optin) return FSP_ERR_ARG;
     int rc = fsp_allow_smem(I, (const void *)fn, L.bytes);
     if (rc != FSP_OK) return rc;
     int per_sm = 1;
     if ((rc = fsp_blocks_per_sm(I, (const void *)fn, warps * 32, L.bytes, &per_sm)) != FSP_OK) return rc;
     long long grid = (long long)I->sm_count * per_sm;
-    const long long need = (groups + warps - 1) / warps;
+    const long long teams = warps / slices;
+    const long long need = (groups + teams - 1) / teams;
     if (need < grid) grid = need;
     fn<<<(unsigned)grid, warps * 32, L.bytes, st>>>(dev_view(I), I->d_p16, nodes, count, dcount, stride, lb_out, L);
     FSP_CUDA(cudaGetLastError());

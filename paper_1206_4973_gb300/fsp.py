@@ -31,7 +31,8 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_node_stride_bidir", "f
            "fsp_mlp_create", "fsp_mlp_destroy", "fsp_mlp_num_params", "fsp_mlp_get_params",
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
            "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
-           "fsp_batch_tune_pools", "fsp_batch_set_split", "fsp_batch_set_bidir", "fsp_set_bound", "fsp_instance_host_objects",
+           "fsp_batch_tune_pools", "fsp_batch_set_split", "fsp_batch_set_bidir", "fsp_batch_set_warps",
+           "fsp_batch_tune_warps", "fsp_set_bound", "fsp_instance_host_objects",
            "fsp_last_error")
 BOUND_BASE, BOUND_HEADS = 0, 1
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
@@ -131,6 +132,8 @@ def load(path: str | None = None):
         "fsp_batch_tune_pools": (ctypes.c_int, [ctypes.c_int, vp, vp, i64, vp]),
         "fsp_batch_set_split": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_batch_set_bidir": (ctypes.c_int, [vp, ctypes.c_int]),
+        "fsp_batch_set_warps": (ctypes.c_int, [vp, vp]),
+        "fsp_batch_tune_warps": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, i64, vp]),
         "fsp_set_bound": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_instance_host_objects": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64),
                                                      ctypes.POINTER(ctypes.c_int64)]),
@@ -611,10 +614,20 @@ def fsp_batch_tune_pools(instances, probe_budget: int = 200000):
     return out
 
 
+def fsp_batch_tune_warps(instances, pools, probe_budget: int = 200000):
+    """Block shape (warps per CTA) per shape on measured throughput; returns one per instance."""
+    shapes, flat = _flatten(instances)
+    pools = np.ascontiguousarray(pools, dtype=np.int64)
+    out = np.zeros(len(instances), np.int32)
+    _check(load().fsp_batch_tune_warps(len(instances), shapes.ctypes.data, flat.ctypes.data, pools.ctypes.data,
+                                       int(probe_budget), out.ctypes.data))
+    return out
+
+
 class Batch:
     """Instances of mixed shape solved in one persistent launch (a CUDA graph)."""
 
-    def __init__(self, instances, pools, budgets=None, ub0=None, split=False):
+    def __init__(self, instances, pools, budgets=None, ub0=None, split=False, warps=None):
         shapes, flat = _flatten(instances)
         self.count = len(instances)
         self.n = shapes[:, 0].copy()
@@ -626,8 +639,20 @@ class Batch:
                                        None if bud is None else bud.ctypes.data,
                                        None if ub is None else ub.ctypes.data, ctypes.byref(h)))
         self.handle = h
+        if warps is not None:
+            self.set_warps(warps)
         if split:
             self.set_split(True)
+
+    def set_warps(self, warps):
+        """Warps per CTA for each instance (fsp_batch_set_warps; None = 8 for all)."""
+        if warps is None:
+            _check(load().fsp_batch_set_warps(self.handle, None))
+            return
+        w = np.ascontiguousarray(warps, dtype=np.int32)
+        if w.shape != (self.count,):
+            raise ValueError("one block shape per instance")
+        _check(load().fsp_batch_set_warps(self.handle, w.ctypes.data))
 
     def set_split(self, on: bool):
         """Work items = the subtrees of the roots (fsp_batch_set_split)."""

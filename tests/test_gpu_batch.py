@@ -161,3 +161,60 @@ def test_bidirectional_batch_matches_oracle(F):
             assert a["cmax"] == b["cmax"], i
     with pytest.raises(F.FspError):  # records of 32 jobs + 2 bytes: no bidirectional batch kernel
         F.Batch([inputs.instance(31, 20, 1)], [64]).set_bidir(True)
+
+
+def test_block_shapes_per_instance_give_the_same_searches(F):
+    """Every instance with its own block shape (1 to 16 warps per CTA, the
+    instances of one shape split over several block shapes, so several
+    launches run side by side): the whole-instance searches are the oracle's,
+    counter for counter, as with the default 8 warps; split mode reaches the
+    same optima with every block shape."""
+    shapes = inputs.batch_shapes(24, first_seed=300)
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    pools = np.array([(64, 256, 1024)[i % 3] for i in range(24)], np.int64)
+    budgets = np.full(24, 20000, np.int64)
+    # 16 warps of 50 x 10 tables exceed a CTA's shared memory: at most 12 there
+    warps = np.array([min((1, 2, 4, 8, 12, 16)[i % 6], 12 if shapes[i][:2] == (50, 10) else 16)
+                      for i in range(24)], np.int32)
+    B = F.Batch(instances, pools, budgets, warps=warps)
+    B.run()
+    res = B.results()
+    check(F, instances, res, pools, budgets)
+    B.set_warps(None)  # back to 8 warps for all: the same results
+    B.run()
+    for a, b in zip(B.results(), res):
+        assert {k: v for k, v in a.items() if k != "perm"} == {k: v for k, v in b.items() if k != "perm"}
+        assert list(a["perm"]) == list(b["perm"])
+    small = [inputs.instance(n, m, s) for n, m, s in [(9, 5, 1), (10, 10, 2), (12, 5, 4), (11, 10, 6), (13, 5, 9)]]
+    sp = np.array([256, 512, 64, 2048, 128], np.int64)
+    S = F.Batch(small, sp, split=True, warps=np.array([4, 16, 2, 8, 12], np.int32))
+    S.run()
+    for p, r in zip(small, S.results()):
+        assert r["status"] == F.OK and r["cmax"] == oracle.solve(p, ub0=oracle.neh(p)[0], pool=1024)["cmax"]
+        assert oracle.makespan(p, r["perm"]) == r["cmax"]
+    S.set_bidir(True)
+    S.run()
+    for p, r in zip(small, S.results()):
+        assert r["status"] == F.OK and oracle.makespan(p, r["perm"]) == r["cmax"]
+
+
+def test_block_shape_rejected_when_it_does_not_fit(F):
+    B = F.Batch([inputs.instance(12, 5, 1), inputs.instance(50, 10, 2)], [64, 64], budgets=[20000, 20000])
+    with pytest.raises(F.FspError):
+        B.set_warps(np.array([8, 17], np.int32))  # more than 16 warps
+    with pytest.raises(F.FspError):
+        B.set_warps(np.array([8, 16], np.int32))  # 50 x 10 tables of 16 warps exceed a CTA's shared memory
+    B.run()  # unchanged and still usable
+    assert all(r["status"] in (F.OK, F.INCOMPLETE) for r in B.results())
+
+
+def test_block_shape_tuning_per_shape(F):
+    shapes = inputs.batch_shapes(16, first_seed=100)
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    pools = np.full(16, 512, np.int64)
+    w = F.fsp_batch_tune_warps(instances, pools, probe_budget=5000)
+    assert set(w.tolist()) <= {4, 8, 16}
+    for i in range(16):
+        for j in range(16):
+            if shapes[i][:2] == shapes[j][:2]:
+                assert w[i] == w[j]

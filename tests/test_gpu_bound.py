@@ -165,6 +165,36 @@ def test_packed_kernel_cta_shapes(F, warps, monkeypatch):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("n,m,slices", [(20, 20, 1), (20, 20, 2), (20, 20, 3), (20, 20, 6), (15, 10, 2),
+                                          (31, 10, 2), (12, 5, 1)])
+def test_packed_kernel_pair_slices(F, n, m, slices, monkeypatch):
+    """Teams of warps that split a group's passes over the machine pairs (the
+    small-pool shape) give the same bounds as one warp per group, forward and
+    bidirectional, on ragged pools of every size class: fewer nodes than one
+    group, a few groups, and more groups than the teams resident at once."""
+    import torch
+    p = inputs.instance(n, m, 7)
+    inst = F.fsp_create_instance(p)
+    monkeypatch.setenv("FSP_POOL16_SLICES", str(slices))
+    for count in (17, 300, 20011):
+        _, _, rec = inputs.pool_workload(n, m, 7, count)
+        want = oracle.bound_pool(p, rec)
+        got = F.fsp_bound_pool(inst, torch.from_numpy(rec).cuda()).cpu().numpy()
+        assert np.array_equal(got, want), (count, np.nonzero(got != want)[0][:10])
+    # bidirectional records: a suffix on every other node
+    rng = np.random.default_rng(5)
+    st2 = F.fsp_node_stride_bidir(n)
+    rec2 = np.zeros((3001, st2), np.uint8)
+    for t in range(rec2.shape[0]):
+        rec2[t, :n] = rng.permutation(n)
+        d1 = int(rng.integers(0, n - 1))
+        d2 = int(rng.integers(0, n - d1)) if t % 2 else 0
+        rec2[t, n], rec2[t, n + 1] = d1, d2
+    want2 = oracle.bound_pool2(p, rec2)
+    got2 = F.fsp_bound_pool_bidir(inst, torch.from_numpy(rec2).cuda()).cpu().numpy()
+    assert np.array_equal(got2, want2), np.nonzero(got2 != want2)[0][:10]
+
+
 def test_packed_kernel_extreme_times(F):
     """Instances at the edge of the packed kernel's 16-bit range
     ((n + m) * max p <= 16383) and just past it (the 32-bit kernels take
