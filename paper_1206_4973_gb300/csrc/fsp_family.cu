@@ -60,15 +60,14 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
 {
     constexpr int P = MT * (MT - 1) / 2;
     const SolveCtl *ctl = ws.ctl;
-    const int np = (int)ctl->n_parents;
     const int W = blockDim.x >> 5;
-    if (blockIdx.x * W >= np) return;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = I.n, stride = I.stride, mp = I.mp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const FamView V = fam_view(smem, L, warp);
 
-    // stage the instance tables
+    // stage the instance tables (read-only: this may run while the selection
+    // ahead of this kernel is still running)
     for (int i = threadIdx.x; i < n * P; i += blockDim.x) V.we[i] = __ldg(I.we + i);
     for (int i = threadIdx.x; i < P * V.rks8; i += blockDim.x) {
         const int kl = i / V.rks8, j = i - kl * V.rks8;
@@ -79,6 +78,9 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         V.pq[j * mp + k] = make_int2(__ldg(I.p + i), __ldg(I.q + i));
     }
     fam_tables_finish<MT>(V, n, mp);
+    pdl_wait();  // the selection's control block and stack from here on
+    const int np = (int)ctl->n_parents;
+    if (blockIdx.x * W >= np) return;
 
     const long long S = ctl->s_pop + np;  // the stack before the pops (np >= 1 here)
     const long long top = ws.cum[S - 1];  // children of the whole stack
@@ -111,6 +113,7 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         pair = pair_next;
         buf ^= 1;
     }
+    pdl_launch_dependents();  // no parent left: the elimination may be scheduled
     if (lane == 0) {
         for (int q = 0; q < 3; ++q)
             if (fc[q]) atomicAdd(reinterpret_cast<unsigned long long *>(&ws.ctl->fam[q]), (unsigned long long)fc[q]);

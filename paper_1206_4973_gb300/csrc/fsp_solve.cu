@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(SOLVE_B, 8) k_solve_init_nodes(SolveWs ws, con
     // bytes keeps each thread's 16-byte reads of its own record conflict-free
     constexpr int SS = 16 * (NV | 1);
     __shared__ __align__(16) uint8_t recs[SOLVE_B * SS];
+    pdl_launch_dependents();
     const long long t = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
     if (!wide) {
         const long long first = (long long)blockIdx.x * SOLVE_B;
@@ -339,6 +340,8 @@ __device__ __forceinline__ long long block_sum_ll(long long v, long long *red)
 __global__ void __launch_bounds__(SOLVE_B) k_init_cum(SolveWs ws, int n, int stride, long long count, int scanned)
 {
     __shared__ long long red[SOLVE_B / 32];
+    pdl_launch_dependents();
+    pdl_wait();
     long long before = 0;
     if (scanned) {
         before = ws.iblk[blockIdx.x];
@@ -426,6 +429,8 @@ __device__ __forceinline__ int block_incl_scan(int v, int *warp_tot)
 __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stride, long long pool,
                                                     long long budget, long long max_it, int write_poff)
 {
+    pdl_launch_dependents();  // the bounding kernel stages its tables meanwhile
+    pdl_wait();
     SolveCtl *ctl = ws.ctl;
     const long long S = ctl->stack_size;
     // nothing to do: an error (a malformed start record), an empty stack, or
@@ -574,6 +579,8 @@ __global__ void __launch_bounds__(SOLVE_B, 8) k_count(SolveWs ws, int n, int str
 {
     __shared__ long long red[2][SOLVE_B / 32];
     __shared__ int s_last;
+    pdl_launch_dependents();
+    pdl_wait();
     SolveCtl *ctl = ws.ctl;
     const long long nch = ctl->n_children;
     const int ubn = solve_ub_new(ctl);
@@ -677,6 +684,7 @@ __global__ void __launch_bounds__(SOLVE_B, 8) k_count(SolveWs ws, int n, int str
 __global__ void __launch_bounds__(SOLVE_B, 8) k_push(SolveWs ws, int n, int stride)
 {
     __shared__ int wcnt[SOLVE_B / 32], wr[SOLVE_B / 32];
+    pdl_wait();
     const SolveCtl *ctl = ws.ctl;
     if (ctl->n_parents == 0) return;  // an iteration that did nothing changes nothing
     const long long nch = ctl->n_children;
@@ -927,6 +935,28 @@ static double wall_seconds()
 }
 
 // Options, workspace layout and kernels of one search.
+// Launch with programmatic stream serialization (the kernel may start while
+// the one ahead of it on the stream finishes; it calls pdl_wait() before it
+// reads what that one writes).  FSP_PDL=0 launches in plain stream order.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                              Args... args)
+{
+    const char *e = getenv("FSP_PDL");
+    const bool on = !(e && e[0] == '0');
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = on ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 struct SolvePlan {
     fsp_options o;
     SolveLayout L;
@@ -1156,7 +1186,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if (wide) k_solve_init_nodes_wide<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
             const int scanned = gi > INIT_SCAN_BLOCKS;
             if (scanned) k_init_scan<<<1, 1024, 0, st>>>(ws, gi);
-            k_init_cum<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count, scanned);
+            TRY(launch_pdl(k_init_cum, gi, SOLVE_B, 0, st, ws, I->n, I->stride, (long long)o.init_count, scanned));
         } else {
             k_solve_init<<<1, 128, 0, st>>>(ws, I->n, rs, ub0);
         }
@@ -1179,8 +1209,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
             idle = false;
             if (prof) LTRY(cudaEventRecord(pe[0], st));
-            k_select<<<1, SELECT_B, 0, st>>>(ws, I->n, rs, pool, o.node_budget, o.max_iterations,
-                                             P->bf == nullptr);
+            LTRY(launch_pdl(k_select, 1, SELECT_B, 0, st, ws, I->n, rs, pool, (long long)o.node_budget,
+                            (long long)o.max_iterations, (int)(P->bf == nullptr)));
             if (prof) LTRY(cudaEventRecord(pe[1], st));
             if (P->bidir && !P->bf) {  // children, their bounds, then the exact values of the complete ones
                 const long long mc = pool + I->n;
@@ -1221,15 +1251,15 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
                 DevInst Df = D;
                 Df.stride = rs;  // bidirectional records are wider
-                P->bf<<<grid_f, FL.warps * 32, FL.bytes, st>>>(Df, ws, FL);
+                LTRY(launch_pdl(P->bf, (unsigned)grid_f, FL.warps * 32, FL.bytes, st, Df, ws, FL));
             } else if (bb2) {
                 bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             } else {
                 bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
             }
             if (prof) LTRY(cudaEventRecord(pe[2], st));
-            k_count<<<grid, SOLVE_B, 0, st>>>(ws, I->n, rs);
-            k_push<<<grid, SOLVE_B, 0, st>>>(ws, I->n, rs);
+            LTRY(launch_pdl(k_count, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
+            LTRY(launch_pdl(k_push, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
             if (prof) LTRY(cudaEventRecord(pe[3], st));
             LTRY(cudaGetLastError());
 #undef LTRY

@@ -4,6 +4,17 @@
 
 #include "fsp_bound.cuh"
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched with the
+// programmatic stream serialization attribute may start while the kernel
+// ahead of it on the stream is still running.  pdl_wait() returns once that
+// kernel has completed and its memory operations are visible (at once for a
+// kernel launched without the attribute); the code before it touches nothing
+// the kernel ahead writes.  pdl_launch_dependents() lets the kernel behind
+// this one be scheduled before this one completes (it then waits in its own
+// pdl_wait()).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 struct SolveCtl {
     long long stack_size;   // records on the stack
     long long s_pop;        // stack size after this iteration's pops

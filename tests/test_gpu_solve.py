@@ -301,3 +301,36 @@ def test_bench_step_matches_oracle(F):
     k = got["stack_left"]
     assert k == ref["stack_left"]
     assert canon(out[:k].cpu().numpy(), n) == canon(ref["stack"], n)
+
+
+@pytest.mark.parametrize("pdl", ["0", "1"])
+def test_bench_step_and_search_in_both_launch_orders(F, pdl, monkeypatch):
+    """The step kernels launched with programmatic stream serialization (the
+    default: a kernel may start while the one ahead finishes and waits for
+    its results in place) or in plain stream order (FSP_PDL=0): the bench
+    step as bench.py times it (no phase events) equals the oracle's, stack
+    included, and a 20 x 20 search of many iterations launched ahead gives
+    the same trace and stack either way."""
+    import torch
+    monkeypatch.setenv("FSP_PDL", pdl)
+    n, pool = 20, 2**18
+    p, ub_perm, rec = frontier_20x20(2**18)
+    ub = oracle.makespan(p, ub_perm)
+    ref = oracle.solve(p, ub0=ub, pool=pool, init_nodes=rec, max_iterations=1, trace_cap=1, export_stack=True)
+    inst = F.fsp_create_instance(p)
+    out = torch.zeros((len(rec) + pool, inst.stride), dtype=torch.uint8, device="cuda")
+    got = F.fsp_solve(inst, ub0=ub, pool_size=pool, init_nodes=torch.from_numpy(rec).cuda(), max_iterations=1,
+                      trace_cap=1, out_nodes=out)
+    same(got, ref)
+    k = got["stack_left"]
+    assert canon(out[:k].cpu().numpy(), n) == canon(ref["stack"], n)
+    q = inputs.instance(20, 20, 6)
+    qi = F.fsp_create_instance(q)
+    u, perm = F.fsp_neh(qi)
+    a = F.fsp_solve(qi, ub0=u, ub0_perm=perm, pool_size=8192, node_budget=3_000_000, trace_cap=4096)
+    monkeypatch.setenv("FSP_PDL", "1" if pdl == "0" else "0")
+    b = F.fsp_solve(qi, ub0=u, ub0_perm=perm, pool_size=8192, node_budget=3_000_000, trace_cap=4096)
+    for key in ("status", "cmax", "nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iterations",
+                "incumbent_updates", "stack_left"):
+        assert a[key] == b[key], key
+    assert np.array_equal(a["trace"], b["trace"])
