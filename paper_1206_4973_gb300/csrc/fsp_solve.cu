@@ -171,17 +171,25 @@ __device__ __forceinline__ bool init_node_fast(FspRec<NV> &rec, bool same, uint8
     bool ok = d <= n - 2, sorted = true;
     M seen = 0, rem = 0;
     int prev = -1;
+    // word by word; the words past the n-th byte are skipped (n is the same
+    // for every thread, so the exit is uniform)
 #pragma unroll
-    for (int i = 0; i < 16 * NV; ++i) {
-        if (i < n) {
-            const int j = (int)((rec.w[i >> 2] >> ((i & 3) * 8)) & 0xFFu);
-            ok &= j < n;
-            const M bit = j < n ? (M)1 << j : (M)0;
-            seen |= bit;
-            if (i >= d) {
-                rem |= bit;
-                sorted &= j > prev;
-                prev = j;
+    for (int q = 0; q < 4 * NV; ++q) {
+        if (4 * q >= n) break;
+        const uint32_t w = rec.w[q];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = 4 * q + b;
+            if (i < n) {
+                const int j = (int)((w >> (8 * b)) & 0xFFu);
+                ok &= j < n;
+                const M bit = j < n ? (M)1 << j : (M)0;
+                seen |= bit;
+                if (i >= d) {
+                    rem |= bit;
+                    sorted &= j > prev;
+                    prev = j;
+                }
             }
         }
     }
@@ -191,13 +199,20 @@ __device__ __forceinline__ bool init_node_fast(FspRec<NV> &rec, bool same, uint8
         return true;
     }
 #pragma unroll
-    for (int i = 0; i < 16 * NV; ++i) {  // positions d..n-1: the remaining jobs in increasing order
-        if (i >= d && i < n) {
-            const int j = init_low(rem);
-            rem &= rem - (M)1;
-            const int sh = (i & 3) * 8;
-            rec.w[i >> 2] = (rec.w[i >> 2] & ~(0xFFu << sh)) | ((uint32_t)j << sh);
+    for (int q = 0; q < 4 * NV; ++q) {  // positions d..n-1: the remaining jobs in increasing order
+        if (4 * q >= n) break;
+        if (4 * q + 3 < d) continue;
+        uint32_t w = rec.w[q];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = 4 * q + b;
+            if (i >= d && i < n) {
+                const int j = init_low(rem);
+                rem &= rem - (M)1;
+                w = (w & ~(0xFFu << (8 * b))) | ((uint32_t)j << (8 * b));
+            }
         }
+        rec.w[q] = w;
     }
     fsp_store_rec(rec, dst);
     return true;
