@@ -471,7 +471,7 @@ int fsp_batch_set_warps(fsp_batch *batch, const int32_t *warps);
 /* Block shape per shape on measured throughput: for each shape, up to 8 of
  * its instances (pools from `pools`, probe_budget nodes each), repeated until
  * their split-mode items fill every SM twice at 4 warps per CTA, run as one
- * split-mode batch with 4, 8 and 16 warps per CTA (those whose shared memory
+ * split-mode batch with 4, 8, 12 and 16 warps per CTA (those whose shared memory
  * fits); the block shape with the most nodes bounded per second is written
  * for every instance of that shape to warps_out (host, count).  Not in the
  * paper, which tunes the pool size only (Algorithm 1). */

@@ -35,8 +35,7 @@ struct SolveLayout {
     long long pool_max, max_children, cap, trace_cap, max_parents;
     int max_blocks, topk;
     bool learned;
-    size_t off_ctl, off_stack, off_cum, off_iblk, off_children, off_lbs, off_poff, off_blk, off_aft, off_inc, off_trace,
-        bytes;
+    size_t off_ctl, off_stack, off_cum, off_iblk, off_children, off_lbs, off_poff, off_blk, off_inc, off_trace, bytes;
     size_t off_list, off_px, off_pscore, off_topk;
 };
 
@@ -94,7 +93,6 @@ static int solve_layout(const fsp_instance *I, const fsp_options *o, SolveLayout
     L->off_lbs = off; off = align256(off + (size_t)L->max_children * 4);
     L->off_poff = off; off = align256(off + (size_t)(L->max_children + 2) * 4);
     L->off_blk = off; off = align256(off + (size_t)L->max_blocks * 12);
-    L->off_aft = off; off = align256(off + (size_t)L->max_blocks * 16);
     L->off_trace = off; off = align256(off + (size_t)L->trace_cap * 32);
     L->learned = o->order == FSP_ORDER_LEARNED;
     L->topk = o->topk > 0 ? o->topk : 4;
@@ -456,7 +454,6 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
             ctl->n_parents = 0;
             ctl->n_children = 0;
             ctl->s_pop = S;
-            ctl->count_done = 0;
             ctl->n_list = 0;
             ctl->early = 0;
             ctl->fam_next = 0;
@@ -487,7 +484,6 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
         ctl->n_list = 0;
         ctl->early = 0;
         ctl->fam_next = 0;
-        ctl->count_done = 0;
         ctl->best_key = ~0ull;
         ctl->ub_iter = ctl->ub;
         if (S - np + running > ws.cap) {  // could overflow: keep the stack intact
@@ -584,23 +580,18 @@ __device__ __forceinline__ int solve_ub_new(const SolveCtl *ctl)
     return b < ubi ? b : ubi;
 }
 
-// Elimination (Sec. II-A), step 1: survivors (not complete schedules,
-// bound below the new UB), leaves and survivors' children per block of 256
-// children; the last block to finish (an atomic count, cleared by k_select)
-// sums them over the blocks after each block (the survivors are pushed in
-// reverse pool order) and applies the iteration to the control block:
-// counters, UB, stack size, trace, incumbent.
+// Elimination (Sec. II-A), step 1: survivors (not complete schedules, bound
+// below the new UB) and leaves per block of 256 children.  Both elimination
+// kernels are held to 32 registers: 8 blocks of 256 per SM, one wave for a
+// pool of 2^18 children.
 __global__ void __launch_bounds__(SOLVE_B, 8) k_count(SolveWs ws, int n, int stride)
 {
-    __shared__ long long red[2][SOLVE_B / 32];
-    __shared__ int s_last;
     pdl_launch_dependents();
     pdl_wait();
-    SolveCtl *ctl = ws.ctl;
+    const SolveCtl *ctl = ws.ctl;
     const long long nch = ctl->n_children;
     const int ubn = solve_ub_new(ctl);
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const long long c = (long long)blockIdx.x * SOLVE_B + tid;
+    const long long c = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
     bool leaf = false, surv = false;
     int dch = 0;
     if (c < nch) {
@@ -608,112 +599,65 @@ __global__ void __launch_bounds__(SOLVE_B, 8) k_count(SolveWs ws, int n, int str
         leaf = dch == n - 1;
         surv = !leaf && ws.lbs[c] < ubn;
     }
+    __shared__ long long red[SOLVE_B / 32];
     const int cs = __syncthreads_count(surv);
     const int cl = __syncthreads_count(leaf);
-    int cr = surv ? n - dch : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cr += __shfl_xor_sync(0xffffffffu, cr, o);
-    if (lane == 0) red[0][wid] = cr;
-    __syncthreads();
-    if (tid == 0) {
-        long long r = 0;
-        for (int w = 0; w < SOLVE_B / 32; ++w) r += red[0][w];
+    const long long cr = block_sum_ll(surv ? n - dch : 0, red);
+    if (threadIdx.x == 0) {
         ws.blk[3 * blockIdx.x] = cs;
         ws.blk[3 * blockIdx.x + 1] = cl;
-        ws.blk[3 * blockIdx.x + 2] = (int)r;
-        __threadfence();
-        s_last = atomicAdd(&ctl->count_done, 1) == (int)gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (ctl->n_parents == 0) return;  // an iteration that did nothing changes nothing
-    // the last block: suffix sums over the blocks; thread t takes the t-th
-    // run of `per` consecutive blocks counted from the end of the pool
-    const int nb = (int)gridDim.x, per = (nb + SOLVE_B - 1) / SOLVE_B;
-    long long tsv = 0, tsr = 0, leaves = 0;
-    for (int j = tid * per; j < (tid + 1) * per && j < nb; ++j) {
-        const int b = nb - 1 - j;
-        tsv += __ldcg(ws.blk + 3 * b);
-        leaves += __ldcg(ws.blk + 3 * b + 1);
-        tsr += __ldcg(ws.blk + 3 * b + 2);
-    }
-    long long is = tsv, ir = tsr;  // inclusive scan over the threads
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long us = __shfl_up_sync(0xffffffffu, is, o), ur = __shfl_up_sync(0xffffffffu, ir, o);
-        if (lane >= o) { is += us; ir += ur; }
-    }
-    if (lane == 31) { red[0][wid] = is; red[1][wid] = ir; }
-    __syncthreads();
-    long long cs_ = is - tsv, cr_ = ir - tsr, carry_s = 0;  // before this thread's run
-    for (int w = 0; w < SOLVE_B / 32; ++w) {
-        if (w < wid) { cs_ += red[0][w]; cr_ += red[1][w]; }
-        carry_s += red[0][w];
-    }
-    for (int j = tid * per; j < (tid + 1) * per && j < nb; ++j) {
-        const int b = nb - 1 - j;
-        ws.aft[2 * b] = cs_;
-        ws.aft[2 * b + 1] = cr_;
-        cs_ += __ldcg(ws.blk + 3 * b);
-        cr_ += __ldcg(ws.blk + 3 * b + 2);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) leaves += __shfl_xor_sync(0xffffffffu, leaves, o);
-    if (lane == 0) red[0][wid] = leaves;
-    __syncthreads();
-    const long long total = carry_s;
-    const int ubi = ctl->ub_iter;
-    const bool improved = ubn < ubi;
-    if (improved) {
-        const long long idx = (long long)(ctl->best_key & 0xffffffffull);
-        for (int i = tid; i < n; i += SOLVE_B) ws.inc[i] = ws.children[idx * stride + i];
-    }
-    if (tid == 0) {
-        long long lv = 0;
-        for (int w = 0; w < SOLVE_B / 32; ++w) lv += red[0][w];
-        const long long it = ctl->cnt[4];
-        const long long s_pop = ctl->s_pop;
-        ctl->cnt[0] += nch;
-        ctl->cnt[1] += ctl->n_parents;
-        ctl->cnt[2] += nch - lv - total;
-        ctl->cnt[3] += lv;
-        ctl->cnt[4] = it + 1;
-        if (improved) ctl->cnt[5] += 1;
-        ctl->cnt[6] += ctl->early;
-        ctl->ub = ubn;
-        ctl->stack_size = s_pop + total;
-        if (it < ws.trace_cap) {
-            ws.trace[4 * it + 0] = ctl->n_parents;
-            ws.trace[4 * it + 1] = nch;
-            ws.trace[4 * it + 2] = total;
-            ws.trace[4 * it + 3] = ubn;
-        }
+        ws.blk[3 * blockIdx.x + 2] = (int)cr;
     }
 }
 
 // Elimination, step 2: stable compaction onto the stack in reverse pool
 // order (the pool's first survivor on top), with each survivor's running
-// children count; block b's survivors go below those of the blocks after it.
+// children count; block 0 applies the iteration to the control block.
 __global__ void __launch_bounds__(SOLVE_B, 8) k_push(SolveWs ws, int n, int stride)
 {
+    __shared__ long long red[5][SOLVE_B / 32];
     __shared__ int wcnt[SOLVE_B / 32], wr[SOLVE_B / 32];
     pdl_wait();
-    const SolveCtl *ctl = ws.ctl;
+    SolveCtl *ctl = ws.ctl;
     if (ctl->n_parents == 0) return;  // an iteration that did nothing changes nothing
     const long long nch = ctl->n_children;
-    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if ((long long)b * SOLVE_B >= nch) return;
     const int ubn = solve_ub_new(ctl);
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    // this thread's child first (its loads overlap the block sums below)
     const long long c = (long long)b * SOLVE_B + tid;
-    bool surv = false;
-    int rc = 0;
+    int dch = n - 1;
+    int32_t lbc = 0;
     if (c < nch) {
-        const int dch = solve_depth(ws, ws.children + c * stride, n);
-        surv = dch != n - 1 && ws.lbs[c] < ubn;
-        rc = surv ? n - dch : 0;
+        dch = solve_depth(ws, ws.children + c * stride, n);
+        lbc = ws.lbs[c];
     }
+    // survivors and leaves per iteration stay below 2^27 (pool <= 2^26): int;
+    // survivors' children (up to 255 each) need 64 bits
+    int before = 0, total = 0, leaves = 0;
+    long long before_r = 0, total_r = 0;
+#pragma unroll 4
+    for (int i = tid; i < (int)gridDim.x; i += SOLVE_B) {
+        const int s = ws.blk[3 * i];
+        const long long sr = ws.blk[3 * i + 2];
+        total += s;
+        total_r += sr;
+        leaves += ws.blk[3 * i + 1];
+        if (i < b) { before += s; before_r += sr; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        before += __shfl_xor_sync(0xffffffffu, before, o);
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        leaves += __shfl_xor_sync(0xffffffffu, leaves, o);
+        before_r += __shfl_xor_sync(0xffffffffu, before_r, o);
+        total_r += __shfl_xor_sync(0xffffffffu, total_r, o);
+    }
+    if (lane == 0) {
+        red[0][wid] = before; red[1][wid] = total; red[2][wid] = leaves;
+        red[3][wid] = before_r; red[4][wid] = total_r;
+    }
+    const bool surv = c < nch && dch != n - 1 && lbc < ubn;
+    const int rc = surv ? n - dch : 0;
     const unsigned bal = __ballot_sync(0xffffffffu, surv);
     int rincl = rc;  // survivors' children up to this one, in the warp
 #pragma unroll
@@ -724,23 +668,53 @@ __global__ void __launch_bounds__(SOLVE_B, 8) k_push(SolveWs ws, int n, int stri
     if (lane == 0) wcnt[wid] = __popc(bal);
     if (lane == 31) wr[wid] = rincl;
     __syncthreads();
-    if (!surv) return;
-    int sv = 0, rt = 0, woff = 0, wroff = 0;
-#pragma unroll
+    before = total = leaves = before_r = total_r = 0;
+    int woff = 0, wroff = 0;
     for (int w = 0; w < SOLVE_B / 32; ++w) {
-        sv += wcnt[w];
-        rt += wr[w];
+        before += red[0][w];
+        total += red[1][w];
+        leaves += red[2][w];
+        before_r += red[3][w];
+        total_r += red[4][w];
         if (w < wid) { woff += wcnt[w]; wroff += wr[w]; }
     }
     const long long s_pop = ctl->s_pop;
-    const int q = woff + __popc(bal & ((1u << lane) - 1u));  // survivors before this one in the block
-    const long long pos = s_pop + ws.aft[2 * b] + (sv - 1 - q);
-    const uint4 *src = reinterpret_cast<const uint4 *>(ws.children + c * stride);
-    uint4 *dst = reinterpret_cast<uint4 *>(ws.stack + pos * stride);
-    for (int v = 0; v < (stride >> 4); ++v) dst[v] = src[v];
-    // the survivors at or below pos are this one and those after it in pool order
-    const long long base = s_pop > 0 ? ws.cum[s_pop - 1] : 0;
-    ws.cum[pos] = base + ws.aft[2 * b + 1] + (rt - (wroff + rincl - rc));
+    if (surv) {
+        const long long q = before + woff + __popc(bal & ((1u << lane) - 1u));
+        const long long pos = s_pop + total - 1 - q;
+        const uint4 *src = reinterpret_cast<const uint4 *>(ws.children + c * stride);
+        uint4 *dst = reinterpret_cast<uint4 *>(ws.stack + pos * stride);
+        for (int v = 0; v < (stride >> 4); ++v) dst[v] = src[v];
+        // the survivors at or below pos are this one and those after it in pool order
+        const long long base = s_pop > 0 ? ws.cum[s_pop - 1] : 0;
+        ws.cum[pos] = base + total_r - (before_r + wroff + rincl - rc);
+    }
+    if (b == 0) {
+        const int ubi = ctl->ub_iter;
+        const bool improved = ubn < ubi;
+        if (improved) {
+            const long long idx = (long long)(ctl->best_key & 0xffffffffull);
+            for (int i = tid; i < n; i += SOLVE_B) ws.inc[i] = ws.children[idx * stride + i];
+        }
+        if (tid == 0) {
+            const long long it = ctl->cnt[4];
+            ctl->cnt[0] += nch;
+            ctl->cnt[1] += ctl->n_parents;
+            ctl->cnt[2] += nch - leaves - total;
+            ctl->cnt[3] += leaves;
+            ctl->cnt[4] = it + 1;
+            if (improved) ctl->cnt[5] += 1;
+            ctl->cnt[6] += ctl->early;
+            ctl->ub = ubn;
+            ctl->stack_size = s_pop + total;
+            if (it < ws.trace_cap) {
+                ws.trace[4 * it + 0] = ctl->n_parents;
+                ws.trace[4 * it + 1] = nch;
+                ws.trace[4 * it + 2] = total;
+                ws.trace[4 * it + 3] = ubn;
+            }
+        }
+    }
 }
 
 // Branching + bounding, fast path: NPT children per thread (fsp_bound2.cuh).
@@ -1123,7 +1097,6 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     ws.lbs = (int32_t *)(base + L.off_lbs);
     ws.poff = (int *)(base + L.off_poff);
     ws.blk = (int *)(base + L.off_blk);
-    ws.aft = (long long *)(base + L.off_aft);
     ws.cum = (long long *)(base + L.off_cum);
     ws.iblk = (long long *)(base + L.off_iblk);
     ws.inc = base + L.off_inc;

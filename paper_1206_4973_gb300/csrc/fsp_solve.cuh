@@ -24,7 +24,7 @@ struct SolveCtl {
     int ub;                 // current upper bound
     int ub_iter;            // upper bound at the start of the iteration
     int status;             // FSP_ERR_* raised on the device, 0 if none
-    int count_done;         // k_count: blocks finished this iteration (cleared by k_select)
+    int pad0;
     long long cnt[7];       // bounded, branched, pruned, leaves, iterations, updates, early cuts
     long long n_list;       // learned order: children left for the full bound
     long long early;        // learned order: children cut by their predicted pairs
@@ -45,7 +45,6 @@ struct SolveWs {
     int32_t *lbs;
     int *poff;              // first child of each popped parent; poff[np] = children
     int *blk;               // per block of 256 children: survivors, leaves, survivors' children
-    long long *aft;         // per block: survivors and their children in the blocks after it
     uint8_t *inc;
     long long *trace;
     long long trace_cap;

@@ -213,7 +213,7 @@ def test_block_shape_tuning_per_shape(F):
     instances = [inputs.instance(n, m, s) for n, m, s in shapes]
     pools = np.full(16, 512, np.int64)
     w = F.fsp_batch_tune_warps(instances, pools, probe_budget=5000)
-    assert set(w.tolist()) <= {4, 8, 16}
+    assert set(w.tolist()) <= {4, 8, 12, 16}
     for i in range(16):
         for j in range(16):
             if shapes[i][:2] == shapes[j][:2]:
