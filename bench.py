@@ -40,8 +40,9 @@ UNIT = "subproblems/s"
 L2_FLUSH_BYTES = 512 << 20
 SMS, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 # The ALU pipe (logic, min/max, the add-max instructions) retires 64 lanes per clock per SM: ncu
-# reports sm__inst_executed_pipe_alu.avg.peak_sustained = 0.5 warp instructions per cycle per
-# scheduler (4 schedulers x 16 lanes); the issue ceiling above is 4 x 32 lanes.
+# reports sm__inst_executed_pipe_alu.avg.peak_sustained = 2 warp instructions per cycle per SM
+# against sm__inst_executed.avg.peak_sustained = 4 (the issue ceiling above, 4 x 32 lanes), in a
+# capture of `bench.py --profile-case`.
 ALU_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one launch of the dominant kernel (k_branch_family on the step), from
 # one ncu capture of `bench.py --profile-case` (dram__bytes_read.sum + dram__bytes_write.sum); set to

@@ -164,6 +164,12 @@ typedef struct {
                                is its completion.  Starts from the root (init_nodes must be
                                NULL), plain order, base bound, no node logging; out_nodes
                                receives bidirectional records. */
+    int warps;              /* block shape of the search's bounding kernel where it bounds
+                               each parent's children together: warps per CTA, 1..16; 0 =
+                               the most whose tables fit (with pool_size = 0, chosen among
+                               4, 8, 12 and that most on measured throughput).  The search
+                               does not depend on it.  FSP_ERR_ARG if its tables do not fit
+                               a CTA; ignored by the per-child kernels of other shapes. */
 } fsp_options;
 
 #define FSP_BRANCH_FORWARD 0

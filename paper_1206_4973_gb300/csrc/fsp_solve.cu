@@ -964,6 +964,22 @@ struct SolvePlan {
     int rs;              // bytes per stack record
 };
 
+// A block shape fixed by the caller (opt->warps): the one candidate, so the
+// block tuner has nothing to choose.
+static int family_fixed_warps(const fsp_instance *I, int mt, int nv, int most, int warps, SolvePlan *P)
+{
+    if (warps == 0) return FSP_OK;
+    if (warps < 0 || warps > most) {
+        fsp_set_error("fsp_solve: warps = %d; this shape's bounding kernel takes 1..%d", warps, most);
+        return FSP_ERR_ARG;
+    }
+    const int K = P->famL.K;
+    P->famC[0] = family_smem_layout(I, mt, nv, warps);
+    P->famC[0].K = K;
+    P->nfam = 1;
+    return FSP_OK;
+}
+
 static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fsp_options *opt, SolvePlan *P)
 {
     if (!I || !cmax || !perm) { fsp_set_error("fsp_solve: NULL argument"); return FSP_ERR_ARG; }
@@ -999,6 +1015,7 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
             for (int c = 0; c < 3; ++c)
                 if (cand[c] < w) P->famC[P->nfam++] = family_smem_layout(I, mt, nv, cand[c]);
             P->famC[P->nfam++] = P->famL;
+            if ((rc = family_fixed_warps(I, mt, nv, w, o.warps, P)) != FSP_OK) return rc;
             if ((rc = fsp_allow_smem(I, (const void *)P->bf, P->famL.bytes)) != FSP_OK) return rc;
         }
         if (o.workspace && ((uintptr_t)o.workspace & 255) != 0) {
@@ -1040,6 +1057,7 @@ static int solve_prepare(fsp_instance *I, int32_t *cmax, int32_t *perm, const fs
                     P->famC[P->nfam++].K = P->famL.K;
                 }
             P->famC[P->nfam++] = P->famL;
+            if ((rc = family_fixed_warps(I, shp.mt, shp.nv, w, o.warps, P)) != FSP_OK) return rc;
             if ((rc = fsp_allow_smem(I, (const void *)P->bf, P->famL.bytes)) != FSP_OK) return rc;
         }
     }

@@ -70,7 +70,7 @@ class fsp_options(ctypes.Structure):
                 ("order", ctypes.c_int), ("topk", ctypes.c_int), ("model", ctypes.c_void_p),
                 ("log_nodes", ctypes.c_void_p), ("log_cap", ctypes.c_int64),
                 ("log_count", ctypes.POINTER(ctypes.c_int64)), ("log_lbs", ctypes.c_void_p),
-                ("branching", ctypes.c_int)]
+                ("branching", ctypes.c_int), ("warps", ctypes.c_int)]
 ORDER_PLAIN, ORDER_LEARNED = 0, 1
 BRANCH_FORWARD, BRANCH_BIDIR = 0, 1
 
@@ -313,7 +313,7 @@ _default_options = None  # fsp_default_options' struct, as bytes
 def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, trace_cap=0,
              schedule=None, stream=None, init_nodes=None, init_count=None, max_iterations=0,
              out_nodes=None, profile=False, tune_window=0, schedule_out=None, model=None, topk=0,
-             log_nodes=None, log_lbs=None, branching=0):
+             log_nodes=None, log_lbs=None, branching=0, warps=0):
     global _default_options
     if _default_options is None:
         d = fsp_options()
@@ -323,6 +323,7 @@ def _options(pool_size=1024, node_budget=0, stack_capacity=0, ub0_perm=None, tra
     o.pool_size = int(pool_size)
     o.tune_window = int(tune_window)
     o.branching = int(branching)
+    o.warps = int(warps)
     if model is not None:
         o.order = ORDER_LEARNED
         o.model = model.handle
@@ -395,7 +396,8 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
               stack_capacity: int = 0, ub0_perm=None, trace_cap: int = 0, schedule=None, stream=None,
               workspace=None, init_nodes=None, init_count=None, max_iterations: int = 0,
               out_nodes=None, profile: bool = False, tune_window: int = 0, schedule_cap: int = 0,
-              model=None, topk: int = 0, log_nodes=None, log_lbs=None, branching: int = BRANCH_FORWARD):
+              model=None, topk: int = 0, log_nodes=None, log_lbs=None, branching: int = BRANCH_FORWARD,
+              warps: int = 0):
     """Exact B&B on the device.  The scratch is a torch uint8 tensor (allocated
     here when `workspace` is None).  init_nodes (host array or device tensor of
     records) starts the search from that stack; out_nodes (host array or
@@ -408,7 +410,7 @@ def fsp_solve(inst: Instance, ub0: int = UB_INF, pool_size: int = 1024, node_bud
     o, keep, trace, out_count = _options(pool_size, node_budget, stack_capacity, ub0_perm, trace_cap,
                                          schedule, stream, init_nodes, init_count, max_iterations,
                                          out_nodes, profile, tune_window, sched_out, model, topk, log_nodes,
-                                         log_lbs, branching)
+                                         log_lbs, branching, warps)
     nbytes = _check(int(load().fsp_solve_workspace_bytes(inst.handle, ctypes.byref(o))))
     if workspace is None:
         workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")

@@ -154,3 +154,25 @@ def test_small_pools_one_warp_per_node(F, n, m, seed, count):
         keep = np.ones(count, bool)
         keep[[2, 3]] = False
         assert np.array_equal(got[keep], oracle.bound_pool(p, rec[keep], bound=F.BOUND_HEADS))
+
+
+def test_fixed_block_shape_gives_the_same_search(F):
+    """fsp_options.warps fixes the bounding kernel's block shape (warps per
+    CTA): every shape gives the search of the default shape, counter for
+    counter, trace and incumbent; a shape outside 1..16 or too large for the
+    tables is refused."""
+    p = inputs.instance(20, 20, 6)
+    inst = F.fsp_create_instance(p)
+    u, perm = F.fsp_neh(inst)
+    kw = dict(ub0=u, ub0_perm=perm, pool_size=8192, node_budget=1_000_000, trace_cap=4096)
+    ref = F.fsp_solve(inst, **kw)
+    for w in (1, 2, 5, 8, 16):
+        got = F.fsp_solve(inst, warps=w, **kw)
+        for k in ("status", "cmax", "nodes_bounded", "nodes_branched", "nodes_pruned", "leaves", "iterations",
+                  "incumbent_updates", "stack_left"):
+            assert got[k] == ref[k], (w, k)
+        assert np.array_equal(got["trace"], ref["trace"]), w
+        assert list(got["perm"]) == list(ref["perm"])
+    for w in (-1, 17):
+        with pytest.raises(F.FspError):
+            F.fsp_solve(inst, warps=w, **kw)
