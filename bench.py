@@ -481,10 +481,21 @@ def batch_solve(fsp):
         d["count"] += 1
         d["solved"] += r["status"] == fsp.OK
     B.close()
-    return {"instances": BATCH_COUNT, "solved_in_batch": solved, "batch_s": t_batch,
-            "batch_nodes_bounded": nodes, "batch_nodes_per_s": nodes / t_batch, "tune_s": t_tune,
-            "warps_per_cta": 8, "split": split, "tuned_block_shapes": tuned, "bidirectional": bidir,
+    # the headline: the recommended configuration (block shape tuned per shape, the roots'
+    # subtrees shared between CTAs, bidirectional branching); every other mode is listed beside it
+    head = bidir["split"]
+    return {"instances": BATCH_COUNT, "mode": "tuned block shapes, split, bidirectional",
+            "solved_in_batch": head["solved_in_batch"], "batch_s": head["batch_s"],
+            "batch_nodes_bounded": head["batch_nodes_bounded"], "batch_nodes_per_s": head["batch_nodes_per_s"],
+            "same_optima_as_forward": head["same_optima_as_forward"],
+            "tune_s": t_tune, "tune_block_shapes_s": t_tune_w,
+            "forward": {"whole_8_warps": {"batch_s": t_batch, "solved_in_batch": solved,
+                                          "batch_nodes_bounded": nodes, "batch_nodes_per_s": nodes / t_batch},
+                        "split_8_warps": split,
+                        "whole_tuned": tuned["whole"], "split_tuned": tuned["split"]},
+            "bidirectional_whole_tuned": bidir["whole"],
             "node_budget_per_instance": BATCH_BUDGET, "leftovers": BATCH_COUNT - solved,
+            "leftovers_from": "forward whole, 8 warps",
             "leftovers_finished": finished, "leftover_branching": "bidirectional", "leftover_s": t_left,
             "leftover_nodes": left_nodes,
             "leftover_budget_each": LEFTOVER_BUDGET, "per_shape": per_shape}
