@@ -47,7 +47,7 @@ ALU_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one launch of the dominant kernel (k_branch_family on the step), from
 # one ncu capture of `bench.py --profile-case` (dram__bytes_read.sum + dram__bytes_write.sum); set to
 # None when that kernel changes, until it is captured again.
-BB_TRAFFIC_BYTES = 1080576
+BB_TRAFFIC_BYTES = 1080320
 
 
 def work_ops(depth, n=N_JOBS, m=N_MACH):

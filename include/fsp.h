@@ -165,7 +165,7 @@ typedef struct {
                                NULL), plain order, base bound, no node logging; out_nodes
                                receives bidirectional records. */
     int warps;              /* block shape of the search's bounding kernel where it bounds
-                               each parent's children together: warps per CTA, 1..16; 0 =
+                               each parent's children together: warps per CTA, 1..20; 0 =
                                the most whose tables fit (with pool_size = 0, chosen among
                                4, 8, 12 and that most on measured throughput).  The search
                                does not depend on it.  FSP_ERR_ARG if its tables do not fit

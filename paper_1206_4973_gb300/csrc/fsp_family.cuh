@@ -8,7 +8,7 @@
 
 #include "fsp_solve.cuh"
 
-#define FAM_MAX_WARPS 16  // warps per CTA at most (one parent per warp at a time)
+#define FAM_MAX_WARPS 20  // warps per CTA at most (one parent per warp at a time)
 #define FAM_MIN_WARPS 4   // below this the per-child kernel is used
 #define FAM_TS 33         // row stride of the per-warp scan table (32 pairs + 1)
 
