@@ -465,19 +465,19 @@ int fsp_batch_tune_pools(int count, const int32_t *shapes, const int32_t *p_flat
                          int64_t *pools_out);
 
 /* Block shape per instance: warps (host, count; 0 = the default 8, else
- * 1..16) warps per CTA of the launch that solves it; NULL resets all to 8.
+ * 1..20) warps per CTA of the launch that solves it; NULL resets all to 8.
  * Instances of one shape with one block shape form a class (one launch).
  * The results do not depend on the block shape (whole-instance searches are
  * the same search; split mode reaches the same optima).  Synchronises the
  * device, rebuilds the classes' scratch and re-captures the graph.  Errors:
- * FSP_ERR_ARG (a count outside 0..16, or a block shape whose shared memory
+ * FSP_ERR_ARG (a count outside 0..20, or a block shape whose shared memory
  * does not fit a CTA; nothing changes), FSP_ERR_OOM, FSP_ERR_CUDA. */
 int fsp_batch_set_warps(fsp_batch *batch, const int32_t *warps);
 
 /* Block shape per shape on measured throughput: for each shape, up to 8 of
  * its instances (pools from `pools`, probe_budget nodes each), repeated until
  * their split-mode items fill every SM twice at 4 warps per CTA, run as one
- * split-mode batch with 4, 8, 12 and 16 warps per CTA (those whose shared memory
+ * split-mode batch with 4, 8, 12, 16 and 20 warps per CTA (those whose shared memory
  * fits); the block shape with the most nodes bounded per second is written
  * for every instance of that shape to warps_out (host, count).  Not in the
  * paper, which tunes the pool size only (Algorithm 1). */

@@ -545,7 +545,7 @@ extern "C" int fsp_batch_tune_warps(int count, const int32_t *shapes, const int3
         fsp_set_error("fsp_batch_tune_warps: invalid argument");
         return FSP_ERR_ARG;
     }
-    const int cands[] = {4, 8, 12, 16};
+    const int cands[] = {4, 8, 12, 16, 20};
     int dev = 0, sms = 1, optin = 0;
     FSP_CUDA(cudaGetDevice(&dev));
     FSP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

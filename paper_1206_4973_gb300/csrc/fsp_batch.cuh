@@ -17,7 +17,7 @@
 #include "fsp_family.cuh"
 
 #define BB 256        // threads per CTA of the helper kernels and the default batch CTA
-#define BB_MAX 512    // most threads of a batch CTA (16 warps; the block shape is chosen per shape)
+#define BB_MAX 640    // most threads of a batch CTA (20 warps; the block shape is chosen per shape)
 
 // Shapes of the batch kernel: machines MT x record vectors NV x mask words NW
 // (n <= 15, <= 31, <= 63 jobs; m = 5, 10, 20).

@@ -164,7 +164,7 @@ def test_bidirectional_batch_matches_oracle(F):
 
 
 def test_block_shapes_per_instance_give_the_same_searches(F):
-    """Every instance with its own block shape (1 to 16 warps per CTA, the
+    """Every instance with its own block shape (1 to 20 warps per CTA, the
     instances of one shape split over several block shapes, so several
     launches run side by side): the whole-instance searches are the oracle's,
     counter for counter, as with the default 8 warps; split mode reaches the
@@ -174,7 +174,7 @@ def test_block_shapes_per_instance_give_the_same_searches(F):
     pools = np.array([(64, 256, 1024)[i % 3] for i in range(24)], np.int64)
     budgets = np.full(24, 20000, np.int64)
     # 16 warps of 50 x 10 tables exceed a CTA's shared memory: at most 12 there
-    warps = np.array([min((1, 2, 4, 8, 12, 16)[i % 6], 12 if shapes[i][:2] == (50, 10) else 16)
+    warps = np.array([min((1, 2, 4, 8, 12, 16, 20)[i % 7], 12 if shapes[i][:2] == (50, 10) else 20)
                       for i in range(24)], np.int32)
     B = F.Batch(instances, pools, budgets, warps=warps)
     B.run()
@@ -201,7 +201,7 @@ def test_block_shapes_per_instance_give_the_same_searches(F):
 def test_block_shape_rejected_when_it_does_not_fit(F):
     B = F.Batch([inputs.instance(12, 5, 1), inputs.instance(50, 10, 2)], [64, 64], budgets=[20000, 20000])
     with pytest.raises(F.FspError):
-        B.set_warps(np.array([8, 17], np.int32))  # more than 16 warps
+        B.set_warps(np.array([8, 21], np.int32))  # more than 20 warps
     with pytest.raises(F.FspError):
         B.set_warps(np.array([8, 16], np.int32))  # 50 x 10 tables of 16 warps exceed a CTA's shared memory
     B.run()  # unchanged and still usable
@@ -213,7 +213,7 @@ def test_block_shape_tuning_per_shape(F):
     instances = [inputs.instance(n, m, s) for n, m, s in shapes]
     pools = np.full(16, 512, np.int64)
     w = F.fsp_batch_tune_warps(instances, pools, probe_budget=5000)
-    assert set(w.tolist()) <= {4, 8, 12, 16}
+    assert set(w.tolist()) <= {4, 8, 12, 16, 20}
     for i in range(16):
         for j in range(16):
             if shapes[i][:2] == shapes[j][:2]:
