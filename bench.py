@@ -451,11 +451,19 @@ def batch_solve(fsp):
         B.run()
         rb = B.results()
         tb = time.perf_counter() - t1
+        cs = B.class_stats()  # the CTAs of this launch, per class, from the global timer
         bidir[mode] = {"batch_s": tb, "solved_in_batch": sum(r["status"] == fsp.OK for r in rb),
                        "batch_nodes_bounded": sum(r["nodes_bounded"] for r in rb),
                        "batch_nodes_per_s": sum(r["nodes_bounded"] for r in rb) / tb,
                        "same_optima_as_forward": all(a["cmax"] == b["cmax"] for a, b in zip(res, rb)
-                                                     if a["status"] == fsp.OK and b["status"] == fsp.OK)}
+                                                     if a["status"] == fsp.OK and b["status"] == fsp.OK),
+                       "cta_utilization": (sum(c["ctas"] * c["busy_mean_ms"] for c in cs)
+                                           / max(1e-9, sum(c["ctas"] for c in cs) * cs[0]["launch_span_ms"])),
+                       "classes": [{"shape": f"{c['n']}x{c['m']}", "warps": c["warps"], "ctas": c["ctas"],
+                                    "items": c["items"], "busy_mean_ms": round(c["busy_mean_ms"], 2),
+                                    "busy_max_ms": round(c["busy_max_ms"], 2),
+                                    "last_end_ms": round(c["last_end_ms"], 2)} for c in cs],
+                       "launch_span_ms": round(cs[0]["launch_span_ms"], 2)}
     B.set_bidir(False)
     B.set_split(False)
     split = {"batch_s": t_split, "solved_in_batch": sum(r["status"] == fsp.OK for r in res_s),
@@ -488,6 +496,8 @@ def batch_solve(fsp):
             "solved_in_batch": head["solved_in_batch"], "batch_s": head["batch_s"],
             "batch_nodes_bounded": head["batch_nodes_bounded"], "batch_nodes_per_s": head["batch_nodes_per_s"],
             "same_optima_as_forward": head["same_optima_as_forward"],
+            "cta_utilization": head["cta_utilization"], "launch_span_ms": head["launch_span_ms"],
+            "classes": head["classes"],
             "tune_s": t_tune, "tune_block_shapes_s": t_tune_w,
             "forward": {"whole_8_warps": {"batch_s": t_batch, "solved_in_batch": solved,
                                           "batch_nodes_bounded": nodes, "batch_nodes_per_s": nodes / t_batch},

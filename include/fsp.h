@@ -474,6 +474,26 @@ int fsp_batch_tune_pools(int count, const int32_t *shapes, const int32_t *p_flat
  * does not fit a CTA; nothing changes), FSP_ERR_OOM, FSP_ERR_CUDA. */
 int fsp_batch_set_warps(fsp_batch *batch, const int32_t *warps);
 
+/* Load balance of the last completed fsp_batch_run: one entry per class
+ * (instances of one shape run with one block shape, in launch order), from
+ * the global timer each persistent CTA reads when it starts and when it
+ * leaves (no work left in its queue).  Times in ms from the earliest CTA
+ * start of the whole launch; launch_span_ms is the time from that start to
+ * the last CTA's exit, the same for every class.  Synchronises the device.
+ * out (host, cap entries) may be NULL when cap = 0; *count receives the
+ * number of classes.  Errors: FSP_ERR_ARG, FSP_ERR_CUDA. */
+typedef struct {
+    int32_t n, m, warps;   /* the class: shape and warps per CTA */
+    int32_t ctas;          /* CTAs of its launch */
+    int32_t instances;     /* its instances */
+    int32_t items;         /* its work items (instances, or split-mode subtrees) */
+    double busy_mean_ms, busy_min_ms, busy_max_ms;  /* CTA lifetimes */
+    double first_start_ms, last_end_ms;             /* its first CTA start, its last CTA exit */
+    double launch_span_ms;
+} fsp_batch_class_info;
+
+int fsp_batch_class_stats(fsp_batch *batch, fsp_batch_class_info *out, int cap, int *count);
+
 /* Block shape per shape on measured throughput: for each shape, up to 8 of
  * its instances (pools from `pools`, probe_budget nodes each), repeated until
  * their split-mode items fill every SM twice at 4 warps per CTA, run as one

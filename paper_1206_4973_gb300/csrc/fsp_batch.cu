@@ -85,6 +85,7 @@ struct BatchClass {
     int *d_list = nullptr;   // the instance indices, then the item indices
     size_t smem = 0;         // dynamic shared memory per CTA (the larger of forward and bidirectional)
     int grid_max = 0;        // CTAs the scratch holds
+    int grid = 0;            // CTAs of the captured launch
     BatchWs ws{};
 };
 
@@ -123,6 +124,7 @@ static void batch_free_classes(fsp_batch *B)
         cudaFree(c.ws.stack);
         cudaFree(c.ws.children);
         cudaFree(c.ws.lbs);
+        cudaFree(c.ws.cta_ns);
     }
     B->cls.clear();
     cudaFree(B->d_queue);
@@ -226,6 +228,7 @@ static int batch_build_classes(fsp_batch *B)
         FSP_CUDA(cudaMalloc(&c.ws.stack, g * c.ws.cap * c.ws.stride_max));
         FSP_CUDA(cudaMalloc(&c.ws.children, g * c.ws.ch_cap * c.ws.stride_max));
         FSP_CUDA(cudaMalloc(&c.ws.lbs, g * c.ws.ch_cap * sizeof(int32_t)));
+        FSP_CUDA(cudaMalloc(&c.ws.cta_ns, g * 2 * sizeof(unsigned long long)));
         std::vector<int> list(c.inst);
         list.insert(list.end(), c.items.begin(), c.items.end());
         FSP_CUDA(cudaMalloc(&c.d_list, sizeof(int) * list.size()));
@@ -262,11 +265,12 @@ static int batch_capture(fsp_batch *B)
     const BatchFn kb = B->bidir ? batch_kernel_bidir() : &k_batch<false>;
     const BatchSplitFn ks = B->bidir ? batch_split_kernel_bidir() : &k_batch_split<false>;
     for (int c = 0; c < nc && e == cudaSuccess; ++c) {
-        const BatchClass &C = B->cls[c];
+        BatchClass &C = B->cls[c];
         e = cudaStreamWaitEvent(side[c], fork, 0);
         if (e != cudaSuccess) break;
         const int len = B->split ? (int)C.items.size() : (int)C.inst.size();
         const int grid = std::min(C.grid_max, len);
+        C.grid = grid;
         if (grid > 0) {
             if (B->split)
                 ks<<<grid, C.warps * 32, C.smem, side[c]>>>(B->d_desc, C.d_list + C.inst.size(), len, B->d_p,
@@ -431,6 +435,52 @@ extern "C" int fsp_batch_set_split(fsp_batch *B, int on)
     if (!B) { fsp_set_error("fsp_batch_set_split: NULL batch"); return FSP_ERR_ARG; }
     B->split = on != 0;
     return batch_capture(B);
+}
+
+extern "C" int fsp_batch_class_stats(fsp_batch *B, fsp_batch_class_info *out, int cap, int *count)
+{
+    if (!B || !count || (cap > 0 && !out)) { fsp_set_error("fsp_batch_class_stats: NULL argument"); return FSP_ERR_ARG; }
+    *count = (int)B->cls.size();
+    FSP_CUDA(cudaDeviceSynchronize());
+    unsigned long long t0 = ~0ull, t1 = 0;
+    std::vector<std::vector<unsigned long long>> ns(B->cls.size());
+    for (size_t c = 0; c < B->cls.size(); ++c) {
+        const BatchClass &C = B->cls[c];
+        ns[c].resize(2 * (size_t)C.grid);
+        if (C.grid > 0)
+            FSP_CUDA(cudaMemcpy(ns[c].data(), C.ws.cta_ns, ns[c].size() * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost));
+        for (int k = 0; k < C.grid; ++k) {
+            t0 = std::min(t0, ns[c][2 * k]);
+            t1 = std::max(t1, ns[c][2 * k + 1]);
+        }
+    }
+    for (size_t c = 0; c < B->cls.size() && (int)c < cap; ++c) {
+        const BatchClass &C = B->cls[c];
+        fsp_batch_class_info &o = out[c];
+        o.n = C.n;
+        o.m = C.m;
+        o.warps = C.warps;
+        o.ctas = C.grid;
+        o.instances = (int32_t)C.inst.size();
+        o.items = B->split ? (int32_t)C.items.size() : (int32_t)C.inst.size();
+        double sum = 0.0, lo = 1e300, hi = 0.0, first = 1e300, last = 0.0;
+        for (int k = 0; k < C.grid; ++k) {
+            const double a = (double)(ns[c][2 * k] - t0) * 1e-6, b = (double)(ns[c][2 * k + 1] - t0) * 1e-6;
+            sum += b - a;
+            lo = std::min(lo, b - a);
+            hi = std::max(hi, b - a);
+            first = std::min(first, a);
+            last = std::max(last, b);
+        }
+        o.busy_mean_ms = C.grid > 0 ? sum / C.grid : 0.0;
+        o.busy_min_ms = C.grid > 0 ? lo : 0.0;
+        o.busy_max_ms = hi;
+        o.first_start_ms = C.grid > 0 ? first : 0.0;
+        o.last_end_ms = last;
+        o.launch_span_ms = t1 > t0 ? (double)(t1 - t0) * 1e-6 : 0.0;
+    }
+    return FSP_OK;
 }
 
 extern "C" void fsp_batch_destroy(fsp_batch *B)

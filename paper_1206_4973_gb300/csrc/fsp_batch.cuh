@@ -42,10 +42,18 @@ struct BatchOut {  // one result (device; mirrored by fsp_batch_result)
 struct BatchWs {  // per-CTA scratch in global memory (one slice per CTA of a class's launch)
     uint8_t *stack, *children;
     int32_t *lbs;
+    unsigned long long *cta_ns;  // per CTA: the global timer (ns) when it started and when it left
     long long cap;     // records per stack
     long long ch_cap;  // children per iteration (the class's largest pool + n)
     int stride_max;
 };
+
+__device__ __forceinline__ unsigned long long b_globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Split mode: the work items are (instance, first job) pairs, the subtrees of
 // the root; every CTA working on an instance shares its UB and counters.
@@ -410,6 +418,7 @@ __global__ void __launch_bounds__(BB_MAX) k_batch(const BatchDesc *__restrict__ 
     w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
     w.children = W.children + (size_t)blockIdx.x * W.ch_cap * W.stride_max;
     w.lbs = W.lbs + (size_t)blockIdx.x * W.ch_cap;
+    if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x] = b_globaltimer();
     for (;;) {
         if (threadIdx.x == 0) s_inst = atomicAdd(queue, 1);
         __syncthreads();
@@ -430,6 +439,7 @@ __global__ void __launch_bounds__(BB_MAX) k_batch(const BatchDesc *__restrict__ 
 #undef B_CASE
         if (threadIdx.x == 0) out[i].status = FSP_ERR_ARG;  // shape without a kernel (checked on the host)
     }
+    if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x + 1] = b_globaltimer();
 }
 
 // Split mode: the persistent kernel over the work items; a CTA keeps the
@@ -448,6 +458,7 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
     w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
     w.children = W.children + (size_t)blockIdx.x * W.ch_cap * W.stride_max;
     w.lbs = W.lbs + (size_t)blockIdx.x * W.ch_cap;
+    if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x] = b_globaltimer();
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
@@ -471,4 +482,5 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
 #undef B_CASE
         cur = -1;
     }
+    if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x + 1] = b_globaltimer();
 }

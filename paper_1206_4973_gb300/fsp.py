@@ -32,7 +32,7 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_node_stride_bidir", "f
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
            "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
            "fsp_batch_tune_pools", "fsp_batch_set_split", "fsp_batch_set_bidir", "fsp_batch_set_warps",
-           "fsp_batch_tune_warps", "fsp_set_bound", "fsp_instance_host_objects",
+           "fsp_batch_tune_warps", "fsp_batch_class_stats", "fsp_set_bound", "fsp_instance_host_objects",
            "fsp_last_error")
 BOUND_BASE, BOUND_HEADS = 0, 1
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
@@ -134,6 +134,7 @@ def load(path: str | None = None):
         "fsp_batch_set_bidir": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_batch_set_warps": (ctypes.c_int, [vp, vp]),
         "fsp_batch_tune_warps": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, i64, vp]),
+        "fsp_batch_class_stats": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
         "fsp_set_bound": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_instance_host_objects": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64),
                                                      ctypes.POINTER(ctypes.c_int64)]),
@@ -601,6 +602,14 @@ class fsp_batch_result(ctypes.Structure):
                 ("iterations", ctypes.c_int64), ("incumbent_updates", ctypes.c_int64), ("pool", ctypes.c_int64)]
 
 
+class fsp_batch_class_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("warps", ctypes.c_int32), ("ctas", ctypes.c_int32),
+                ("instances", ctypes.c_int32), ("items", ctypes.c_int32), ("busy_mean_ms", ctypes.c_double),
+                ("busy_min_ms", ctypes.c_double), ("busy_max_ms", ctypes.c_double),
+                ("first_start_ms", ctypes.c_double), ("last_end_ms", ctypes.c_double),
+                ("launch_span_ms", ctypes.c_double)]
+
+
 def _flatten(instances):
     shapes = np.array([[p.shape[0], p.shape[1]] for p in instances], dtype=np.int32)
     flat = np.concatenate([np.ascontiguousarray(p, dtype=np.int32).ravel() for p in instances]).astype(np.int32)
@@ -677,6 +686,14 @@ class Batch:
 
     def run(self, stream=None):
         _check(load().fsp_batch_run(self.handle, _stream(stream)))
+
+    def class_stats(self):
+        """Per class (shape, warps) of the last run: CTAs, items and CTA lifetimes (fsp_batch_class_stats)."""
+        count = ctypes.c_int(0)
+        _check(load().fsp_batch_class_stats(self.handle, None, 0, ctypes.byref(count)))
+        arr = (fsp_batch_class_info * max(1, count.value))()
+        _check(load().fsp_batch_class_stats(self.handle, ctypes.addressof(arr), count.value, ctypes.byref(count)))
+        return [{k: getattr(arr[i], k) for k, _ in fsp_batch_class_info._fields_} for i in range(count.value)]
 
     def results(self, stream=None):
         res = (fsp_batch_result * self.count)()

@@ -65,8 +65,9 @@ def test_struct_layouts_match_the_header(tmp_path):
     """The binding's ctypes structs have the header's sizes and offsets."""
     import subprocess
     src = tmp_path / "layout.c"
-    fields = {"fsp_options": [f for f, _ in fsp.fsp_options._fields_],
-              "fsp_stats": [f for f, _ in fsp.fsp_stats._fields_]}
+    classes = {"fsp_options": fsp.fsp_options, "fsp_stats": fsp.fsp_stats,
+               "fsp_batch_result": fsp.fsp_batch_result, "fsp_batch_class_info": fsp.fsp_batch_class_info}
+    fields = {st: [f for f, _ in cls._fields_] for st, cls in classes.items()}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fsp.h"', "int main(void){"]
     for st, fl in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
@@ -78,7 +79,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                          check=True).stdout.split("\n") if l)
-    for st, cls in (("fsp_options", fsp.fsp_options), ("fsp_stats", fsp.fsp_stats)):
+    for st, cls in classes.items():
         assert int(out[st]) == ctypes.sizeof(cls), st
         for f in fields[st]:
             assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, f"{st}.{f}"

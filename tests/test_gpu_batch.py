@@ -218,3 +218,28 @@ def test_block_shape_tuning_per_shape(F):
         for j in range(16):
             if shapes[i][:2] == shapes[j][:2]:
                 assert w[i] == w[j]
+
+
+def test_class_stats_describe_the_last_launch(F):
+    """fsp_batch_class_stats: one entry per (shape, warps) class, the CTAs of
+    its launch and their lifetimes from the global timer, consistent with one
+    another and with the launch span; split mode lists the subtrees as items."""
+    shapes = [(12, 5, 1), (12, 5, 2), (15, 10, 3), (15, 10, 4), (20, 5, 5)]
+    instances = [inputs.instance(n, m, s) for n, m, s in shapes]
+    B = F.Batch(instances, np.full(5, 256, np.int64), np.full(5, 20000, np.int64),
+                warps=np.array([8, 8, 4, 16, 8], np.int32))
+    B.run()
+    B.results()
+    st = B.class_stats()
+    assert sorted((c["n"], c["m"], c["warps"]) for c in st) == [(12, 5, 8), (15, 10, 4), (15, 10, 16), (20, 5, 8)]
+    for c in st:
+        assert 1 <= c["ctas"] <= c["items"] == c["instances"]
+        assert 0.0 <= c["busy_min_ms"] <= c["busy_mean_ms"] <= c["busy_max_ms"] <= c["launch_span_ms"] + 1e-6
+        assert c["first_start_ms"] <= c["last_end_ms"] <= c["launch_span_ms"] + 1e-6
+    B.set_split(True)
+    B.run()
+    B.results()
+    st = B.class_stats()
+    for c in st:
+        assert c["items"] == c["instances"] * c["n"]
+        assert 1 <= c["ctas"] <= c["items"]
