@@ -74,6 +74,9 @@ __global__ void k_batch_split_finish(const BatchDesc *__restrict__ desc, int cou
 
 // ------------------------------------------------------------------ host --
 
+#define DQ_SLOTS 1024      // donated nodes waiting at a time, per class
+#define DQ_IDS 16384       // donated nodes per class and launch at most (their item ids)
+
 // The instances of one shape that run with one block shape (warps per CTA):
 // one launch of the persistent kernel with its own shared-memory size, grid,
 // work list, queue and scratch.  The launches of all classes are parallel
@@ -95,7 +98,7 @@ struct fsp_batch {
     int32_t *d_p;
     BatchOut *d_out;
     uint8_t *d_perms;
-    int *d_queue = nullptr;  // one counter per class
+    int *d_queue = nullptr;  // one counter per class, then 8 donation counters per class
     std::vector<BatchDesc> desc;
     std::vector<int> warps;  // block shape per instance
     std::vector<BatchClass> cls;
@@ -125,6 +128,9 @@ static void batch_free_classes(fsp_batch *B)
         cudaFree(c.ws.children);
         cudaFree(c.ws.lbs);
         cudaFree(c.ws.cta_ns);
+        cudaFree(c.ws.slot_inst);
+        cudaFree(c.ws.slot_id);
+        cudaFree(c.ws.slot_rec);
     }
     B->cls.clear();
     cudaFree(B->d_queue);
@@ -204,7 +210,12 @@ static int batch_build_classes(fsp_batch *B)
     for (int k = 0; k < 4; ++k)
         FSP_CUDA(cudaFuncSetAttribute(batch_kernel(k & 1, k >> 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_max));
-    FSP_CUDA(cudaMalloc(&B->d_queue, sizeof(int) * B->cls.size()));
+    const size_t nc = B->cls.size();
+    FSP_CUDA(cudaMalloc(&B->d_queue, sizeof(int) * nc * 9));
+    // split-mode schedules of the donated nodes follow the items' (ids items.. in class order)
+    cudaFree(B->X.item_perm);
+    B->X.item_perm = nullptr;
+    FSP_CUDA(cudaMalloc(&B->X.item_perm, (size_t)FSP_MAX_JOBS * ((size_t)B->X.items + nc * DQ_IDS)));
     for (BatchClass &c : B->cls) {
         int per_sm = 1 << 30;
         for (int k = 0; k < 4; ++k) {
@@ -229,6 +240,14 @@ static int batch_build_classes(fsp_batch *B)
         FSP_CUDA(cudaMalloc(&c.ws.children, g * c.ws.ch_cap * c.ws.stride_max));
         FSP_CUDA(cudaMalloc(&c.ws.lbs, g * c.ws.ch_cap * sizeof(int32_t)));
         FSP_CUDA(cudaMalloc(&c.ws.cta_ns, g * 2 * sizeof(unsigned long long)));
+        const size_t ci = (size_t)(&c - &B->cls[0]);
+        c.ws.dq = B->d_queue + nc + 8 * ci;
+        c.ws.slots = DQ_SLOTS;
+        c.ws.ids_base = B->X.items + (int)ci * DQ_IDS;
+        c.ws.ids_cap = DQ_IDS;
+        FSP_CUDA(cudaMalloc(&c.ws.slot_inst, sizeof(int) * DQ_SLOTS));
+        FSP_CUDA(cudaMalloc(&c.ws.slot_id, sizeof(int) * DQ_SLOTS));
+        FSP_CUDA(cudaMalloc(&c.ws.slot_rec, (size_t)DQ_SLOTS * c.ws.stride_max));
         std::vector<int> list(c.inst);
         list.insert(list.end(), c.items.begin(), c.items.end());
         FSP_CUDA(cudaMalloc(&c.d_list, sizeof(int) * list.size()));
@@ -256,7 +275,7 @@ static int batch_capture(fsp_batch *B)
     }
     if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     const bool capturing = e == cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int) * nc, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int) * nc * 9, st);
     if (e == cudaSuccess && B->split) {
         k_batch_split_init<<<B->count, BB, 0, st>>>(B->d_desc, B->d_p, B->d_perms, B->X);
         e = cudaGetLastError();
@@ -372,7 +391,6 @@ extern "C" int fsp_batch_create(int count, const int32_t *shapes, const int32_t 
     TRYB(cudaMalloc(&B->X.key, sizeof(unsigned long long) * count));
     TRYB(cudaMalloc(&B->X.cnt, sizeof(long long) * 6 * count));
     TRYB(cudaMalloc(&B->X.flags, sizeof(int) * count));
-    TRYB(cudaMalloc(&B->X.item_perm, (size_t)FSP_MAX_JOBS * items));
 #undef TRYB
     B->X.item_inst = B->d_item;
     B->X.item_job = B->d_item + items;

@@ -43,10 +43,42 @@ struct BatchWs {  // per-CTA scratch in global memory (one slice per CTA of a cl
     uint8_t *stack, *children;
     int32_t *lbs;
     unsigned long long *cta_ns;  // per CTA: the global timer (ns) when it started and when it left
+    // split mode, donations between the CTAs of one launch: dq = {lock, slots in use, donated
+    // items so far, CTAs waiting for work, items in progress}; each slot holds a donated node
+    // (instance, item id, record); donated item ids run from ids_base to ids_base + ids_cap
+    int *dq;
+    int *slot_inst, *slot_id;
+    uint8_t *slot_rec;
+    int slots, ids_base, ids_cap;
     long long cap;     // records per stack
     long long ch_cap;  // children per iteration (the class's largest pool + n)
     int stride_max;
 };
+
+#define DQ_LOCK_SPINS (1 << 16)
+#define DQ_WAIT_SPINS (1 << 26)  // about a minute of 1 us sleeps: a waiting CTA then just leaves
+#define DQ_IDLE_CAP 32           // CTAs of one launch that may wait for donations at a time
+#define DQ_GIVE_MAX 4            // nodes a CTA donates per iteration at most
+
+// Thread 0 only: the donation lock, taken within a bounded number of tries
+// (false: not taken; the caller skips this donation or look).
+__device__ __forceinline__ bool dq_lock(int *dq)
+{
+    for (int spin = 0; spin < DQ_LOCK_SPINS; ++spin) {
+        if (atomicCAS(dq, 0, 1) == 0) {
+            __threadfence();
+            return true;
+        }
+        __nanosleep(32);
+    }
+    return false;
+}
+
+__device__ __forceinline__ void dq_unlock(int *dq)
+{
+    __threadfence();
+    atomicExch(dq, 0);
+}
 
 __device__ __forceinline__ unsigned long long b_globaltimer()
 {
@@ -195,7 +227,7 @@ __device__ int b_neh(const int32_t *__restrict__ p, int n, BatchShared &sh)
 template <int MT, int NV, int NW, bool SPLIT, bool BIDIR>
 __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, BatchOut *out, uint8_t *perm_out,
                         const BatchWs &W, unsigned char *smem, BatchShared &sh, const BatchSplit &X, int inst,
-                        int item, int job, bool tables_ready)
+                        int item, int job, bool tables_ready, const uint8_t *start_rec = nullptr)
 {
     const int n = D.n, tid = threadIdx.x, NT = (int)blockDim.x, NWP = NT >> 5;
     const int P = MT * (MT - 1) / 2, mp = (MT % 2 == 0) ? MT + 1 : MT;
@@ -250,35 +282,58 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
     // the search
     long long bounded = 0, branched = 0, pruned = 0, leaves = 0, iters = 0, updates = 0;
     int status = FSP_OK;
-    long long S = 1;
-    if (SPLIT && job >= 0) {  // the root's child that schedules `job` first (the rest in increasing order)
+    long long S = 1, bot = 0;  // the stack holds records bot..S-1 (bot rises as bottom nodes are donated)
+    if (SPLIT && start_rec) {  // a node another CTA donated
+        for (int i = tid; i < stride; i += NT) W.stack[i] = start_rec[i];
+    } else if (SPLIT && job >= 0) {  // the root's child that schedules `job` first (the rest in increasing order)
         for (int i = tid; i < stride; i += NT)
             W.stack[i] = (uint8_t)(i == 0 ? job : i < n ? (i - 1 < job ? i - 1 : i) : i == n ? 1 : 0);
     } else {
         for (int i = tid; i < stride; i += NT) W.stack[i] = (uint8_t)(i < n ? i : 0);
     }
     bool improved = false;
-    __shared__ int s_ub;
+    __shared__ int s_ub, s_give;
     __syncthreads();
     const int pool = D.pool;
     const int warp = tid >> 5, lane = tid & 31;
-    while (S > 0) {
+    while (S > bot) {
         if (SPLIT) {  // the instance's UB and node count, as the other CTAs left them
             if (tid == 0) {
                 s_ub = min(ub, *(volatile int *)&X.ub[inst]);
                 if (D.budget > 0 && *(volatile long long *)&X.cnt[6 * inst] >= D.budget) s_ub = -1;
+                // CTAs waiting for work take the bottom nodes (the shallowest: the largest
+                // subtrees left), while this CTA keeps at least one node
+                s_give = 0;
+                const int idle = *(volatile int *)&W.dq[3];
+                if (s_ub >= 0 && idle > 0 && S - bot >= 2 && dq_lock(W.dq)) {
+                    int give = min(min(idle, DQ_GIVE_MAX), (int)(S - bot - 1));
+                    for (; s_give < give; ++s_give) {
+                        const int top = *(volatile int *)&W.dq[1], seq = *(volatile int *)&W.dq[2];
+                        if (top >= W.slots || seq >= W.ids_cap) break;
+                        W.slot_inst[top] = inst;
+                        W.slot_id[top] = W.ids_base + seq;
+                        const uint4 *src = reinterpret_cast<const uint4 *>(W.stack + (bot + s_give) * stride);
+                        uint4 *dst = reinterpret_cast<uint4 *>(W.slot_rec + (size_t)top * W.stride_max);
+                        for (int v = 0; v < stride / 16; ++v) dst[v] = src[v];
+                        *(volatile int *)&W.dq[1] = top + 1;
+                        *(volatile int *)&W.dq[2] = seq + 1;
+                    }
+                    dq_unlock(W.dq);
+                }
             }
             __syncthreads();
             const int u = s_ub;
+            bot += s_give;
             __syncthreads();
             if (u < 0) { status = FSP_INCOMPLETE; break; }
+            if (S == bot) break;
             ub = u;
         } else if (D.budget > 0 && bounded >= D.budget) {
             status = FSP_INCOMPLETE;
             break;
         }
         // selection: deepest parents while their children fit (at least one)
-        const long long cand = S < pool ? S : pool;
+        const long long cand = S - bot < pool ? S - bot : pool;
         long long running = 0, np = 0;
         for (long long base = 0; base < cand; base += (long long)NT * SEL_Q) {
             int r[SEL_Q], tsum = 0;
@@ -442,9 +497,14 @@ __global__ void __launch_bounds__(BB_MAX) k_batch(const BatchDesc *__restrict__ 
     if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x + 1] = b_globaltimer();
 }
 
-// Split mode: the persistent kernel over the work items; a CTA keeps the
-// tables of the instance it last worked on (the items of an instance are
-// consecutive in the list).
+// Split mode: the persistent kernel over the work items, then over the nodes
+// the other CTAs donate; a CTA keeps the tables of the instance it last
+// worked on (the items of an instance are consecutive in the list).  A CTA
+// with no item left waits for a donation (at most DQ_IDLE_CAP wait at a
+// time, each wait bounded) and leaves once no item is in progress and no
+// donated node is left, or when its wait runs out: leaving early loses no
+// work, since every CTA that donates takes the donated nodes back before it
+// leaves if nobody else has.
 template <bool BIDIR>
 __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restrict__ desc,
                                                         const int *__restrict__ list, int len,
@@ -452,7 +512,8 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
                                                         BatchSplit X)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_item;
+    __shared__ int s_item, s_inst, s_job;
+    __shared__ __align__(16) uint8_t s_rec[FSP_MAX_JOBS + 17];
     __shared__ BatchShared sh;
     BatchWs w = W;
     w.stack = W.stack + (size_t)blockIdx.x * W.cap * W.stride_max;
@@ -461,26 +522,61 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
     if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x] = b_globaltimer();
     int cur = -1;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        if (threadIdx.x == 0) {
+            s_item = -1;
+            const int q = atomicAdd(queue, 1);
+            if (q < len) {
+                atomicAdd(&W.dq[4], 1);  // an item in progress
+                s_item = list[q];
+                s_inst = X.item_inst[s_item];
+                s_job = X.item_job[s_item];
+            } else if (atomicAdd(&W.dq[3], 1) < DQ_IDLE_CAP) {  // wait for a donated node
+                for (int spin = 0; spin < DQ_WAIT_SPINS; ++spin) {
+                    if (*(volatile int *)&W.dq[1] > 0 && dq_lock(W.dq)) {
+                        const int top = *(volatile int *)&W.dq[1];
+                        if (top > 0) {
+                            const int sl = top - 1;
+                            *(volatile int *)&W.dq[1] = sl;
+                            atomicAdd(&W.dq[4], 1);
+                            s_item = __ldcg(W.slot_id + sl);
+                            s_inst = __ldcg(W.slot_inst + sl);
+                            s_job = -2;
+                            const uint4 *src = reinterpret_cast<const uint4 *>(W.slot_rec + (size_t)sl * W.stride_max);
+                            for (int v = 0; v < W.stride_max / 16; ++v)
+                                reinterpret_cast<uint4 *>(s_rec)[v] = __ldcg(src + v);
+                        }
+                        dq_unlock(W.dq);
+                        if (s_item >= 0) break;
+                    }
+                    if (*(volatile int *)&W.dq[4] == 0 && *(volatile int *)&W.dq[1] == 0) break;  // no work left
+                    __nanosleep(256);
+                }
+                atomicSub(&W.dq[3], 1);
+            } else {
+                atomicSub(&W.dq[3], 1);
+            }
+        }
         __syncthreads();
-        const int q = s_item;
-        __syncthreads();
-        if (q >= len) break;
-        const int item = list[q];
-        const int i = X.item_inst[item], job = X.item_job[item];
+        const int item = s_item;
+        if (item < 0) break;
+        const int i = s_inst, job = s_job;
         const BatchDesc D = desc[i];
         const int32_t *p = p_flat + D.p_off;
         const int nv = (D.n + (BIDIR ? 2 : 1) + 15) / 16, nw = D.n <= 32 ? 1 : 2;
         const bool ready = cur == i;
         cur = i;
-#define B_CASE(MT_, NV_, NW_)                                                                          \
-    if (D.m == MT_ && nv == NV_ && nw == NW_) {                                                        \
-        b_solve<MT_, NV_, NW_, true, BIDIR>(p, D, nullptr, nullptr, w, smem, sh, X, i, item, job, ready); \
-        continue;                                                                                      \
+        const uint8_t *start = job == -2 ? s_rec : nullptr;
+        bool done = false;
+#define B_CASE(MT_, NV_, NW_)                                                                                  \
+    if (!done && D.m == MT_ && nv == NV_ && nw == NW_) {                                                       \
+        b_solve<MT_, NV_, NW_, true, BIDIR>(p, D, nullptr, nullptr, w, smem, sh, X, i, item, job, ready, start); \
+        done = true;                                                                                           \
     }
         FSP_SHAPES_BATCH(B_CASE)
 #undef B_CASE
-        cur = -1;
+        if (!done) cur = -1;
+        __syncthreads();
+        if (threadIdx.x == 0) atomicSub(&W.dq[4], 1);  // the item is done
     }
     if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x + 1] = b_globaltimer();
 }
