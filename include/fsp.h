@@ -438,7 +438,9 @@ int fsp_batch_results(fsp_batch *batch, fsp_batch_result *res, int32_t *perms, v
  * queue holds the subtrees of the roots instead of whole instances -- for
  * each instance (the ones with the most jobs first) the n subtrees whose
  * schedules start with job 0, 1, ..., n-1 -- so idle CTAs take parts of the
- * instances still being searched instead of waiting for them.  The CTAs
+ * instances still being searched instead of waiting for them; once the
+ * queue is empty, a CTA still searching hands the bottom nodes of its stack
+ * (its largest subtrees) to CTAs waiting for work, each wait bounded.  The CTAs
  * working on an instance share its UB (an atomic minimum, read before every
  * iteration) and its node count: the node budget then caps the instance's
  * total.  Results: the optimum (status FSP_OK) and a schedule attaining
@@ -487,6 +489,7 @@ typedef struct {
     int32_t ctas;          /* CTAs of its launch */
     int32_t instances;     /* its instances */
     int32_t items;         /* its work items (instances, or split-mode subtrees) */
+    int32_t donated;       /* split mode: nodes its CTAs handed to CTAs waiting for work */
     double busy_mean_ms, busy_min_ms, busy_max_ms;  /* CTA lifetimes */
     double first_start_ms, last_end_ms;             /* its first CTA start, its last CTA exit */
     double launch_span_ms;

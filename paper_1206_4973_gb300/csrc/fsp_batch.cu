@@ -482,6 +482,9 @@ extern "C" int fsp_batch_class_stats(fsp_batch *B, fsp_batch_class_info *out, in
         o.ctas = C.grid;
         o.instances = (int32_t)C.inst.size();
         o.items = B->split ? (int32_t)C.items.size() : (int32_t)C.inst.size();
+        int dq[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        FSP_CUDA(cudaMemcpy(dq, C.ws.dq, sizeof dq, cudaMemcpyDeviceToHost));
+        o.donated = B->split ? dq[2] : 0;
         double sum = 0.0, lo = 1e300, hi = 0.0, first = 1e300, last = 0.0;
         for (int k = 0; k < C.grid; ++k) {
             const double a = (double)(ns[c][2 * k] - t0) * 1e-6, b = (double)(ns[c][2 * k + 1] - t0) * 1e-6;

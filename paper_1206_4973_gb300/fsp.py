@@ -604,7 +604,8 @@ class fsp_batch_result(ctypes.Structure):
 
 class fsp_batch_class_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("m", ctypes.c_int32), ("warps", ctypes.c_int32), ("ctas", ctypes.c_int32),
-                ("instances", ctypes.c_int32), ("items", ctypes.c_int32), ("busy_mean_ms", ctypes.c_double),
+                ("instances", ctypes.c_int32), ("items", ctypes.c_int32), ("donated", ctypes.c_int32),
+                ("busy_mean_ms", ctypes.c_double),
                 ("busy_min_ms", ctypes.c_double), ("busy_max_ms", ctypes.c_double),
                 ("first_start_ms", ctypes.c_double), ("last_end_ms", ctypes.c_double),
                 ("launch_span_ms", ctypes.c_double)]

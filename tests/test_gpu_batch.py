@@ -243,3 +243,30 @@ def test_class_stats_describe_the_last_launch(F):
     for c in st:
         assert c["items"] == c["instances"] * c["n"]
         assert 1 <= c["ctas"] <= c["items"]
+        assert c["donated"] >= 0
+
+
+def test_donated_nodes_keep_the_optima(F):
+    """Split mode with one hard instance among easy ones: once the item queue
+    is empty the CTAs still searching hand nodes to the waiting ones; the
+    optima stay the oracle's (whole-instance batch and oracle.solve), every
+    returned schedule attains its makespan, and nodes were donated."""
+    hard = inputs.instance(15, 10, 101)
+    easy = [inputs.instance(9, 5, s) for s in range(8)]
+    instances = [hard] + easy
+    pools = np.full(len(instances), 512, np.int64)
+    whole = F.Batch(instances, pools)
+    whole.run()
+    ref = whole.results()
+    for bidir in (False, True):
+        S = F.Batch(instances, pools, split=True)
+        if bidir:
+            S.set_bidir(True)
+        S.run()
+        got = S.results()
+        for p, a, b in zip(instances, got, ref):
+            assert a["status"] == F.OK and a["cmax"] == b["cmax"]
+            assert oracle.makespan(p, a["perm"]) == a["cmax"]
+        assert sum(c["donated"] for c in S.class_stats()) > 0
+    for p, r in zip(easy, ref[1:]):
+        assert r["cmax"] == oracle.bruteforce(p)[0]
