@@ -76,6 +76,8 @@ __global__ void k_batch_split_finish(const BatchDesc *__restrict__ desc, int cou
 
 #define DQ_SLOTS 1024      // donated nodes waiting at a time, per class
 #define DQ_IDS 16384       // donated nodes per class and launch at most (their item ids)
+#define DQ_IDLE_CAP 4      // CTAs of one class that may wait for donations at a time: waiting CTAs hold
+                           // SM slots the other classes' CTAs need (measured: 2-8 best, 16 and more slower)
 
 // The instances of one shape that run with one block shape (warps per CTA):
 // one launch of the persistent kernel with its own shared-memory size, grid,
@@ -245,6 +247,7 @@ static int batch_build_classes(fsp_batch *B)
         c.ws.slots = DQ_SLOTS;
         c.ws.ids_base = B->X.items + (int)ci * DQ_IDS;
         c.ws.ids_cap = DQ_IDS;
+        c.ws.idle_cap = DQ_IDLE_CAP;
         FSP_CUDA(cudaMalloc(&c.ws.slot_inst, sizeof(int) * DQ_SLOTS));
         FSP_CUDA(cudaMalloc(&c.ws.slot_id, sizeof(int) * DQ_SLOTS));
         FSP_CUDA(cudaMalloc(&c.ws.slot_rec, (size_t)DQ_SLOTS * c.ws.stride_max));

@@ -50,6 +50,7 @@ struct BatchWs {  // per-CTA scratch in global memory (one slice per CTA of a cl
     int *slot_inst, *slot_id;
     uint8_t *slot_rec;
     int slots, ids_base, ids_cap;
+    int idle_cap;      // CTAs of the launch that may wait for donations at a time
     long long cap;     // records per stack
     long long ch_cap;  // children per iteration (the class's largest pool + n)
     int stride_max;
@@ -57,7 +58,6 @@ struct BatchWs {  // per-CTA scratch in global memory (one slice per CTA of a cl
 
 #define DQ_LOCK_SPINS (1 << 16)
 #define DQ_WAIT_SPINS (1 << 26)  // about a minute of 1 us sleeps: a waiting CTA then just leaves
-#define DQ_IDLE_CAP 32           // CTAs of one launch that may wait for donations at a time
 #define DQ_GIVE_MAX 4            // nodes a CTA donates per iteration at most
 
 // Thread 0 only: the donation lock, taken within a bounded number of tries
@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(BB_MAX) k_batch(const BatchDesc *__restrict__ 
 // Split mode: the persistent kernel over the work items, then over the nodes
 // the other CTAs donate; a CTA keeps the tables of the instance it last
 // worked on (the items of an instance are consecutive in the list).  A CTA
-// with no item left waits for a donation (at most DQ_IDLE_CAP wait at a
+// with no item left waits for a donation (at most W.idle_cap wait at a
 // time, each wait bounded) and leaves once no item is in progress and no
 // donated node is left, or when its wait runs out: leaving early loses no
 // work, since every CTA that donates takes the donated nodes back before it
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
                 s_item = list[q];
                 s_inst = X.item_inst[s_item];
                 s_job = X.item_job[s_item];
-            } else if (atomicAdd(&W.dq[3], 1) < DQ_IDLE_CAP) {  // wait for a donated node
+            } else if (atomicAdd(&W.dq[3], 1) < W.idle_cap) {  // wait for a donated node
                 for (int spin = 0; spin < DQ_WAIT_SPINS; ++spin) {
                     if (*(volatile int *)&W.dq[1] > 0 && dq_lock(W.dq)) {
                         const int top = *(volatile int *)&W.dq[1];
