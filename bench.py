@@ -398,6 +398,7 @@ def batch_solve(fsp):
     import torch
     from paper_1206_4973_gb300 import inputs
     shapes = inputs.batch_shapes(BATCH_COUNT, first_seed=100)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     instances = [inputs.instance(n, m, sd) for n, m, sd in shapes]
     t0 = time.perf_counter()
     pools = fsp.fsp_batch_tune_pools(instances, probe_budget=100_000)
@@ -457,8 +458,12 @@ def batch_solve(fsp):
                        "batch_nodes_per_s": sum(r["nodes_bounded"] for r in rb) / tb,
                        "same_optima_as_forward": all(a["cmax"] == b["cmax"] for a, b in zip(res, rb)
                                                      if a["status"] == fsp.OK and b["status"] == fsp.OK),
-                       "cta_utilization": (sum(c["ctas"] * c["busy_mean_ms"] for c in cs)
-                                           / max(1e-9, sum(c["ctas"] for c in cs) * cs[0]["launch_span_ms"])),
+                       # CTA lifetimes summed over the SMs' time: the mean number of live batch CTAs
+                       # per SM over the launch (each class's grid is one CTA per SM at these block
+                       # shapes, and a 20-warp CTA's registers fill an SM, so about 1 is the ceiling)
+                       "live_ctas_per_sm": (sum(c["ctas"] * c["busy_mean_ms"] for c in cs)
+                                            / max(1e-9, sms * cs[0]["launch_span_ms"])),
+                       "ctas_per_sm_per_class": max(c["ctas"] for c in cs) / sms,
                        "classes": [{"shape": f"{c['n']}x{c['m']}", "warps": c["warps"], "ctas": c["ctas"],
                                     "items": c["items"], "busy_mean_ms": round(c["busy_mean_ms"], 2),
                                     "busy_max_ms": round(c["busy_max_ms"], 2),
@@ -496,7 +501,8 @@ def batch_solve(fsp):
             "solved_in_batch": head["solved_in_batch"], "batch_s": head["batch_s"],
             "batch_nodes_bounded": head["batch_nodes_bounded"], "batch_nodes_per_s": head["batch_nodes_per_s"],
             "same_optima_as_forward": head["same_optima_as_forward"],
-            "cta_utilization": head["cta_utilization"], "launch_span_ms": head["launch_span_ms"],
+            "live_ctas_per_sm": head["live_ctas_per_sm"], "ctas_per_sm_per_class": head["ctas_per_sm_per_class"],
+            "launch_span_ms": head["launch_span_ms"],
             "classes": head["classes"],
             "tune_s": t_tune, "tune_block_shapes_s": t_tune_w,
             "forward": {"whole_8_warps": {"batch_s": t_batch, "solved_in_batch": solved,
