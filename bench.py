@@ -704,7 +704,9 @@ def main():
             "e2e": e2e,
             "bound_pool": bp,
             "phase_ms": {k: statistics.mean(v) for k, v in phases.items()},
-            "wall_s": t_wall,
+            "wall_s": t_wall,  # host clock over the K steps, the L2 flush before each and host waits
+            "wall_s_covers": "the K timed steps plus the 512 MiB L2 flush before each (about 0.14 ms) and "
+                             "host-side waits; ms_per_step is the device time of the steps alone",
         }
         if not args.no_extras:
             line["bound_variants"] = bound_variants(fsp)
