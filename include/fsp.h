@@ -413,7 +413,9 @@ typedef struct fsp_batch fsp_batch;
 
 typedef struct {
     int32_t cmax;              /* best makespan found (the optimum when status = FSP_OK) */
-    int32_t status;            /* FSP_OK, FSP_INCOMPLETE (budget) or FSP_ERR_CAPACITY */
+    int32_t status;            /* FSP_OK, FSP_INCOMPLETE (budget), FSP_ERR_CAPACITY, or
+                                  FSP_ERR_TIMEOUT (split mode: a wait on the donations ran
+                                  out, so the result may miss a subtree) */
     int64_t nodes_bounded, nodes_branched, nodes_pruned, leaves, iterations, incumbent_updates;
     int64_t pool;              /* pool size used */
 } fsp_batch_result;
@@ -440,7 +442,11 @@ int fsp_batch_results(fsp_batch *batch, fsp_batch_result *res, int32_t *perms, v
  * schedules start with job 0, 1, ..., n-1 -- so idle CTAs take parts of the
  * instances still being searched instead of waiting for them; once the
  * queue is empty, a CTA still searching hands the bottom nodes of its stack
- * (its largest subtrees) to CTAs waiting for work, each wait bounded.  The CTAs
+ * (its largest subtrees) to CTAs waiting for work.  A CTA that finishes an
+ * item first takes the donated nodes still waiting, so every donated node is
+ * searched; every wait on the donations (for the lock, for a node) ends after
+ * 1 s, and an instance whose donated nodes could not be taken in that time
+ * gets status FSP_ERR_TIMEOUT (the kernel returns; the context stays usable).  The CTAs
  * working on an instance share its UB (an atomic minimum, read before every
  * iteration) and its node count: the node budget then caps the instance's
  * total.  Results: the optimum (status FSP_OK) and a schedule attaining
@@ -449,6 +455,14 @@ int fsp_batch_results(fsp_batch *batch, fsp_batch_result *res, int32_t *perms, v
  * they differ from the whole-instance search's.  Re-captures the graph.
  * Errors: FSP_ERR_ARG, FSP_ERR_OOM, FSP_ERR_CUDA. */
 int fsp_batch_set_split(fsp_batch *batch, int on);
+
+/* Test hook for the wait limit of split mode (on != 0; off with on = 0): every
+ * launch starts with each class's donation lock taken and one donated node
+ * marked waiting, and nothing releases them, so every wait on the donations
+ * runs out (1 s each) and every instance whose items finish gets status
+ * FSP_ERR_TIMEOUT.  No fault, trap or endless wait.  Not in the paper.
+ * Re-captures the graph.  Errors: FSP_ERR_ARG, FSP_ERR_CUDA. */
+int fsp_batch_set_test_hold(fsp_batch *batch, int on);
 
 /* Bidirectional branching (on != 0; FSP_BRANCH_BIDIR of fsp_options) for
  * every instance of the batch, in either mode; off again with on = 0.

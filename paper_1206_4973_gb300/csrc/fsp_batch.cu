@@ -58,7 +58,10 @@ __global__ void k_batch_split_finish(const BatchDesc *__restrict__ desc, int cou
     if (threadIdx.x == 0) {
         BatchOut o;
         o.cmax = X.ub[i];
-        o.status = (X.flags[i] & 2) ? FSP_ERR_CAPACITY : (X.flags[i] & 1) ? FSP_INCOMPLETE : FSP_OK;
+        o.status = (X.flags[i] & 4)   ? FSP_ERR_TIMEOUT
+                   : (X.flags[i] & 2) ? FSP_ERR_CAPACITY
+                   : (X.flags[i] & 1) ? FSP_INCOMPLETE
+                                      : FSP_OK;
         o.ub0 = 0;
         o.pad = 0;
         o.bounded = X.cnt[6 * i];
@@ -107,6 +110,7 @@ struct fsp_batch {
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     bool split = false, bidir = false;
+    bool hold = false;  // test hook: donation locks taken and a node marked waiting at every launch
     BatchSplit X{};
     int *d_item = nullptr;  // item instances, then item jobs
     std::vector<int> item_inst;
@@ -279,6 +283,10 @@ static int batch_capture(fsp_batch *B)
     if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     const bool capturing = e == cudaSuccess;
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue, 0, sizeof(int) * nc * 9, st);
+    for (int c = 0; c < nc && e == cudaSuccess && B->hold; ++c) {  // lock = 1, one node waiting = 1
+        e = cudaMemsetAsync(B->d_queue + nc + 8 * c, 1, 1, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B->d_queue + nc + 8 * c + 1, 1, 1, st);
+    }
     if (e == cudaSuccess && B->split) {
         k_batch_split_init<<<B->count, BB, 0, st>>>(B->d_desc, B->d_p, B->d_perms, B->X);
         e = cudaGetLastError();
@@ -455,6 +463,13 @@ extern "C" int fsp_batch_set_split(fsp_batch *B, int on)
 {
     if (!B) { fsp_set_error("fsp_batch_set_split: NULL batch"); return FSP_ERR_ARG; }
     B->split = on != 0;
+    return batch_capture(B);
+}
+
+extern "C" int fsp_batch_set_test_hold(fsp_batch *B, int on)
+{
+    if (!B) { fsp_set_error("fsp_batch_set_test_hold: NULL batch"); return FSP_ERR_ARG; }
+    B->hold = on != 0;
     return batch_capture(B);
 }
 

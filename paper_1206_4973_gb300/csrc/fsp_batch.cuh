@@ -43,8 +43,9 @@ struct BatchWs {  // per-CTA scratch in global memory (one slice per CTA of a cl
     uint8_t *stack, *children;
     int32_t *lbs;
     unsigned long long *cta_ns;  // per CTA: the global timer (ns) when it started and when it left
-    // split mode, donations between the CTAs of one launch: dq = {lock, slots in use, donated
-    // items so far, CTAs waiting for work, items in progress}; each slot holds a donated node
+    // split mode, donations between the CTAs of one launch: dq = {lock, slots in use (the
+    // donated nodes waiting), donated items so far, CTAs waiting for work, items in progress
+    // (donated nodes included)}; each slot holds a donated node
     // (instance, item id, record); donated item ids run from ids_base to ids_base + ids_cap
     int *dq;
     int *slot_inst, *slot_id;
@@ -56,15 +57,16 @@ struct BatchWs {  // per-CTA scratch in global memory (one slice per CTA of a cl
     int stride_max;
 };
 
-#define DQ_LOCK_SPINS (1 << 16)
-#define DQ_WAIT_SPINS (1 << 26)  // about a minute of 1 us sleeps: a waiting CTA then just leaves
-#define DQ_GIVE_MAX 4            // nodes a CTA donates per iteration at most
+#define DQ_GIVE_TRIES 64                // a donor tries the lock this often, then donates later
+#define DQ_TAKE_TRIES 1024              // a CTA taking a donated node: tries per look
+#define DQ_WAIT_NS 1000000000ull        // every wait on the donations ends after 1 s of global time
+#define DQ_GIVE_MAX 4                   // nodes a CTA donates per iteration at most
 
-// Thread 0 only: the donation lock, taken within a bounded number of tries
-// (false: not taken; the caller skips this donation or look).
-__device__ __forceinline__ bool dq_lock(int *dq)
+// Thread 0 only: the donation lock, taken within `tries` tries (false: not
+// taken; the caller skips this donation or looks again).
+__device__ __forceinline__ bool dq_lock(int *dq, int tries)
 {
-    for (int spin = 0; spin < DQ_LOCK_SPINS; ++spin) {
+    for (int spin = 0; spin < tries; ++spin) {
         if (atomicCAS(dq, 0, 1) == 0) {
             __threadfence();
             return true;
@@ -95,7 +97,8 @@ struct BatchSplit {
     int *ub;                  // per instance: best makespan so far (atomicMin)
     unsigned long long *key;  // per instance: (best makespan << 32) | item that found it, ~0 = none
     long long *cnt;           // per instance: bounded, branched, pruned, leaves, iterations, updates
-    int *flags;               // per instance: 1 = a node budget stopped an item, 2 = a stack filled up
+    int *flags;               // per instance: 1 = a node budget stopped an item, 2 = a stack filled up,
+                              // 4 = a wait on the donations ran out with nodes waiting
     uint8_t *item_perm;       // per item: the best schedule it found (FSP_MAX_JOBS bytes)
 };
 
@@ -305,7 +308,7 @@ __device__ void b_solve(const int32_t *__restrict__ p, const BatchDesc &D, Batch
                 // subtrees left), while this CTA keeps at least one node
                 s_give = 0;
                 const int idle = *(volatile int *)&W.dq[3];
-                if (s_ub >= 0 && idle > 0 && S - bot >= 2 && dq_lock(W.dq)) {
+                if (s_ub >= 0 && idle > 0 && S - bot >= 2 && dq_lock(W.dq, DQ_GIVE_TRIES)) {
                     int give = min(min(idle, DQ_GIVE_MAX), (int)(S - bot - 1));
                     for (; s_give < give; ++s_give) {
                         const int top = *(volatile int *)&W.dq[1], seq = *(volatile int *)&W.dq[2];
@@ -497,14 +500,40 @@ __global__ void __launch_bounds__(BB_MAX) k_batch(const BatchDesc *__restrict__ 
     if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x + 1] = b_globaltimer();
 }
 
+// Thread 0 only: takes the donated node on top of the donation stack (under
+// the lock, within DQ_TAKE_TRIES tries) as the CTA's next item and counts it
+// in progress; returns whether the stack was looked at under the lock (taken,
+// or found empty).
+__device__ __forceinline__ bool dq_take(const BatchWs &W, int &item, int &inst, int &job, uint8_t *rec)
+{
+    if (!dq_lock(W.dq, DQ_TAKE_TRIES)) return false;
+    const int top = *(volatile int *)&W.dq[1];
+    if (top > 0) {
+        const int sl = top - 1;
+        *(volatile int *)&W.dq[1] = sl;
+        atomicAdd(&W.dq[4], 1);
+        item = __ldcg(W.slot_id + sl);
+        inst = __ldcg(W.slot_inst + sl);
+        job = -2;
+        const uint4 *src = reinterpret_cast<const uint4 *>(W.slot_rec + (size_t)sl * W.stride_max);
+        for (int v = 0; v < W.stride_max / 16; ++v) reinterpret_cast<uint4 *>(rec)[v] = __ldcg(src + v);
+    }
+    dq_unlock(W.dq);
+    return true;
+}
+
 // Split mode: the persistent kernel over the work items, then over the nodes
 // the other CTAs donate; a CTA keeps the tables of the instance it last
-// worked on (the items of an instance are consecutive in the list).  A CTA
-// with no item left waits for a donation (at most W.idle_cap wait at a
-// time, each wait bounded) and leaves once no item is in progress and no
-// donated node is left, or when its wait runs out: leaving early loses no
-// work, since every CTA that donates takes the donated nodes back before it
-// leaves if nobody else has.
+// worked on (the items of an instance are consecutive in the list).
+// No donated node is left behind: a CTA that finishes an item first takes
+// the donated nodes still waiting (whoever donated them), one by one, and
+// counts the item done only when it has seen the donation stack empty, so a
+// donor is among the CTAs that look after its own donations.  If the lock
+// stays taken for DQ_WAIT_NS while nodes wait, the instance is flagged (its
+// status becomes FSP_ERR_TIMEOUT: its result may miss a subtree).  With no
+// item left, a CTA waits for a donation (at most W.idle_cap at a time, each
+// for at most DQ_WAIT_NS) and leaves once no item is in progress and no
+// donated node waits; leaving early costs a helper, never a node.
 template <bool BIDIR>
 __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restrict__ desc,
                                                         const int *__restrict__ list, int len,
@@ -521,8 +550,9 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
     w.lbs = W.lbs + (size_t)blockIdx.x * W.ch_cap;
     if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x] = b_globaltimer();
     int cur = -1;
+    bool next = false;  // thread 0: the end of the last item took a donated node
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !next) {
             s_item = -1;
             const int q = atomicAdd(queue, 1);
             if (q < len) {
@@ -531,23 +561,10 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
                 s_inst = X.item_inst[s_item];
                 s_job = X.item_job[s_item];
             } else if (atomicAdd(&W.dq[3], 1) < W.idle_cap) {  // wait for a donated node
-                for (int spin = 0; spin < DQ_WAIT_SPINS; ++spin) {
-                    if (*(volatile int *)&W.dq[1] > 0 && dq_lock(W.dq)) {
-                        const int top = *(volatile int *)&W.dq[1];
-                        if (top > 0) {
-                            const int sl = top - 1;
-                            *(volatile int *)&W.dq[1] = sl;
-                            atomicAdd(&W.dq[4], 1);
-                            s_item = __ldcg(W.slot_id + sl);
-                            s_inst = __ldcg(W.slot_inst + sl);
-                            s_job = -2;
-                            const uint4 *src = reinterpret_cast<const uint4 *>(W.slot_rec + (size_t)sl * W.stride_max);
-                            for (int v = 0; v < W.stride_max / 16; ++v)
-                                reinterpret_cast<uint4 *>(s_rec)[v] = __ldcg(src + v);
-                        }
-                        dq_unlock(W.dq);
-                        if (s_item >= 0) break;
-                    }
+                const unsigned long long t0 = b_globaltimer();
+                while (b_globaltimer() - t0 < DQ_WAIT_NS) {
+                    if (*(volatile int *)&W.dq[1] > 0 && dq_take(W, s_item, s_inst, s_job, s_rec) && s_item >= 0)
+                        break;
                     if (*(volatile int *)&W.dq[4] == 0 && *(volatile int *)&W.dq[1] == 0) break;  // no work left
                     __nanosleep(256);
                 }
@@ -576,7 +593,25 @@ __global__ void __launch_bounds__(BB_MAX) k_batch_split(const BatchDesc *__restr
 #undef B_CASE
         if (!done) cur = -1;
         __syncthreads();
-        if (threadIdx.x == 0) atomicSub(&W.dq[4], 1);  // the item is done
+        if (threadIdx.x == 0) {
+            // the donated nodes still waiting come first (the next item, if one
+            // is taken, is counted in progress before this one is counted done)
+            next = false;
+            s_item = -1;
+            const unsigned long long t0 = b_globaltimer();
+            while (*(volatile int *)&W.dq[1] > 0) {
+                if (dq_take(W, s_item, s_inst, s_job, s_rec)) {
+                    next = s_item >= 0;
+                    break;
+                }
+                if (b_globaltimer() - t0 >= DQ_WAIT_NS) {
+                    atomicOr(&X.flags[i], 4);
+                    break;
+                }
+            }
+            atomicSub(&W.dq[4], 1);  // the item is done
+        }
+        __syncthreads();
     }
     if (threadIdx.x == 0) W.cta_ns[2 * blockIdx.x + 1] = b_globaltimer();
 }

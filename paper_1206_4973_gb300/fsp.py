@@ -32,7 +32,7 @@ EXPORTS = ("fsp_default_options", "fsp_node_stride", "fsp_node_stride_bidir", "f
            "fsp_mlp_set_params", "fsp_mlp_forward", "fsp_mlp_loss_grad", "fsp_mlp_train_step",
            "fsp_pair_order", "fsp_batch_create", "fsp_batch_destroy", "fsp_batch_run", "fsp_batch_results",
            "fsp_batch_tune_pools", "fsp_batch_set_split", "fsp_batch_set_bidir", "fsp_batch_set_warps",
-           "fsp_batch_tune_warps", "fsp_batch_class_stats", "fsp_set_bound", "fsp_instance_host_objects",
+           "fsp_batch_set_test_hold", "fsp_batch_tune_warps", "fsp_batch_class_stats", "fsp_set_bound", "fsp_instance_host_objects",
            "fsp_last_error")
 BOUND_BASE, BOUND_HEADS = 0, 1
 SCORE_FN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_int64, ctypes.c_void_p)
@@ -132,6 +132,7 @@ def load(path: str | None = None):
         "fsp_batch_tune_pools": (ctypes.c_int, [ctypes.c_int, vp, vp, i64, vp]),
         "fsp_batch_set_split": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_batch_set_bidir": (ctypes.c_int, [vp, ctypes.c_int]),
+        "fsp_batch_set_test_hold": (ctypes.c_int, [vp, ctypes.c_int]),
         "fsp_batch_set_warps": (ctypes.c_int, [vp, vp]),
         "fsp_batch_tune_warps": (ctypes.c_int, [ctypes.c_int, vp, vp, vp, i64, vp]),
         "fsp_batch_class_stats": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
@@ -673,6 +674,11 @@ class Batch:
     def set_bidir(self, on: bool):
         """Bidirectional branching for every instance (fsp_batch_set_bidir)."""
         _check(load().fsp_batch_set_bidir(self.handle, 1 if on else 0))
+
+    def set_test_hold(self, on: bool):
+        """Test hook: every wait on the split mode's donations runs out
+        (fsp_batch_set_test_hold)."""
+        _check(load().fsp_batch_set_test_hold(self.handle, 1 if on else 0))
 
     def close(self):
         if self.handle:

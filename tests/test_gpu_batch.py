@@ -270,3 +270,29 @@ def test_donated_nodes_keep_the_optima(F):
         assert sum(c["donated"] for c in S.class_stats()) > 0
     for p, r in zip(easy, ref[1:]):
         assert r["cmax"] == oracle.bruteforce(p)[0]
+
+
+def test_split_wait_limit_reports_timeout_and_recovers(F):
+    """The wait limit of split mode's donations, made to run out on the host's
+    side (fsp_batch_set_test_hold: each launch starts with the donation lock
+    taken and a donated node marked waiting, and nothing releases them).  Every
+    wait ends after 1 s, the kernel returns, and every instance reports
+    FSP_ERR_TIMEOUT; with the hook off, the same batch on the same context then
+    returns the optima of brute force."""
+    import time
+    instances = [inputs.instance(7, 5, s) for s in range(3)]
+    pools = np.full(len(instances), 256, np.int64)
+    S = F.Batch(instances, pools, split=True)
+    S.set_test_hold(True)
+    t0 = time.perf_counter()
+    S.run()
+    got = S.results()
+    assert time.perf_counter() - t0 < 30
+    assert [r["status"] for r in got] == [F.ERR_TIMEOUT] * len(instances)
+    S.set_test_hold(False)
+    S.run()
+    got = S.results()
+    for p, r in zip(instances, got):
+        assert r["status"] == F.OK and r["cmax"] == oracle.bruteforce(p)[0]
+        assert oracle.makespan(p, r["perm"]) == r["cmax"]
+    S.close()
