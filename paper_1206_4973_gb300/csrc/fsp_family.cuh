@@ -300,20 +300,19 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 else Q2 = min(Q2, v.y);
             }
             // release times: lane k takes prefix position t - k at step t,
-            // after lane k-1 has finished that position on machine k-1 (the
-            // p values are read two steps ahead of their use)
+            // after lane k-1 has finished that position on machine k-1.  Its
+            // p values are staged first in its own column of the scan table
+            // (free until the pair scans; row i = prefix position i, stride
+            // 32, so the lanes' reads of different rows fall in distinct banks)
             int32_t Ck = 0;
             if (d > 0) {
-                int32_t p0 = fam_prefix_p(0, lane, d, k, mp, rec_s, pq_s);
-                int32_t p1 = fam_prefix_p(1, lane, d, k, mp, rec_s, pq_s);
+                for (int i = 0; i < d; ++i) T[32 * i + lane] = pq_s[rec_s[i] * mp + k].x;
+#pragma unroll 4
                 for (int t = 0; t < d + MT - 1; ++t) {
-                    const int32_t p2 = fam_prefix_p(t + 2, lane, d, k, mp, rec_s, pq_s);
                     int32_t up = __shfl_up_sync(0xffffffffu, Ck, 1);
                     if (lane == 0) up = 0;
                     const int i = t - lane;
-                    if (lane < MT && i >= 0 && i < d) Ck = max(Ck, up) + p0;
-                    p0 = p1;
-                    p1 = p2;
+                    if (lane < MT && i >= 0 && i < d) Ck = max(Ck, up) + T[32 * i + lane];
                 }
             }
             if (lane < MT) {
@@ -323,12 +322,15 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
             if (BIDIR) {
                 // delivery times of the suffix: lane k takes the suffix job t - (MT-1-k)
                 // from the last at step t, after lane k+1 has finished it on machine k+1
+                // (the suffix's p values staged in the lane's column like the prefix's)
                 int32_t Dk = 0;
+                for (int si = 0; si < d2; ++si) T[32 * si + lane] = pq_s[rec_s[n - 1 - si] * mp + k].x;
+#pragma unroll 4
                 for (int t = 0; t < d2 + MT - 1; ++t) {
                     int32_t down = __shfl_down_sync(0xffffffffu, Dk, 1);
                     if (lane == MT - 1) down = 0;
                     const int si = t - (MT - 1 - lane);
-                    if (lane < MT && si >= 0 && si < d2) Dk = max(Dk, down) + pq_s[rec_s[n - 1 - si] * mp + k].x;
+                    if (lane < MT && si >= 0 && si < d2) Dk = max(Dk, down) + T[32 * si + lane];
                 }
                 if (lane < MT) pd[lane] = Dk;
             }
