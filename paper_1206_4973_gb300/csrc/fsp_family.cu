@@ -109,41 +109,6 @@ __global__ void __launch_bounds__(FAM_MAX_WARPS * 32, 1) k_branch_family(DevInst
         fam_bound<MT, NV, LRN, HEADS, BIDIR>(V, rec_s, c0, n, mp, stride, ub_iter, ws.children, ws.lbs,
                                              &ws.ctl->best_key, pair, L.K, nullptr, fc);
         __syncwarp();
-        // the elimination's counts per block of 256 children (survivors below
-        // the iteration's UB, leaves, survivors' children), added to ws.blk
-        // (cleared by the selection); k_count keeps them when no leaf of the
-        // iteration lowered the UB.  The family's r children share a depth,
-        // r - 1 remaining jobs each, and are leaves when r == 2.
-        {
-            const int r = n - rec_s[n] - (BIDIR ? rec_s[n + 1] : 0);
-            const bool lf = r == 2;
-            const long long b0 = c0 >> 8;
-            int s0 = 0, s1 = 0;
-            for (int ci = lane; ci < r; ci += 32) {
-                const bool sv = !lf && V.lbv[ci] < ub_iter;
-                if (((c0 + ci) >> 8) == b0) s0 += sv;
-                else s1 += sv;
-            }
-            s0 = __reduce_add_sync(0xffffffffu, s0);
-            s1 = __reduce_add_sync(0xffffffffu, s1);
-            if (lane == 0) {
-                const int in0 = (int)(min(c0 + r, (b0 + 1) << 8) - c0), in1 = r - in0;
-                int *bk = ws.blk + 3 * b0;
-                if (s0) {
-                    atomicAdd(bk, s0);
-                    atomicAdd(bk + 2, s0 * (r - 1));
-                }
-                if (lf) atomicAdd(bk + 1, in0);
-                if (in1 > 0) {
-                    if (s1) {
-                        atomicAdd(bk + 3, s1);
-                        atomicAdd(bk + 5, s1 * (r - 1));
-                    }
-                    if (lf) atomicAdd(bk + 4, in1);
-                }
-            }
-        }
-        __syncwarp();
         f = fn;
         pair = pair_next;
         buf ^= 1;

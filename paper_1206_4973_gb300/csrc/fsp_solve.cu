@@ -444,10 +444,6 @@ __global__ void __launch_bounds__(SELECT_B) k_select(SolveWs ws, int n, int stri
 {
     pdl_launch_dependents();  // the bounding kernel stages its tables meanwhile
     pdl_wait();
-    {  // the elimination's per-block counts, which the family kernel adds to
-        const long long nb = (pool + n + SOLVE_B - 1) / SOLVE_B;
-        for (long long i = threadIdx.x; i < 3 * nb; i += SELECT_B) ws.blk[i] = 0;
-    }
     SolveCtl *ctl = ws.ctl;
     const long long S = ctl->stack_size;
     // nothing to do: an error (a malformed start record), an empty stack, or
@@ -587,16 +583,14 @@ __device__ __forceinline__ int solve_ub_new(const SolveCtl *ctl)
 // Elimination (Sec. II-A), step 1: survivors (not complete schedules, bound
 // below the new UB) and leaves per block of 256 children.  Both elimination
 // kernels are held to 32 registers: 8 blocks of 256 per SM, one wave for a
-// pool of 2^18 children.  counted: the family kernel has already added the
-// counts against the iteration's UB, which stand unless a leaf lowered it.
-__global__ void __launch_bounds__(SOLVE_B, 8) k_count(SolveWs ws, int n, int stride, int counted)
+// pool of 2^18 children.
+__global__ void __launch_bounds__(SOLVE_B, 8) k_count(SolveWs ws, int n, int stride)
 {
     pdl_launch_dependents();
     pdl_wait();
     const SolveCtl *ctl = ws.ctl;
     const long long nch = ctl->n_children;
     const int ubn = solve_ub_new(ctl);
-    if (counted && ubn == ctl->ub_iter) return;
     const long long c = (long long)blockIdx.x * SOLVE_B + threadIdx.x;
     bool leaf = false, surv = false;
     int dch = 0;
@@ -1270,8 +1264,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
             }
             if (prof) LTRY(cudaEventRecord(pe[2], st));
-            const int counted = P->bf != nullptr && P->bl == nullptr;  // the family kernel ran
-            LTRY(launch_pdl(k_count, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs, counted));
+            LTRY(launch_pdl(k_count, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
             LTRY(launch_pdl(k_push, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
             if (prof) LTRY(cudaEventRecord(pe[3], st));
             LTRY(cudaGetLastError());
