@@ -926,13 +926,12 @@ static double wall_seconds()
 // Options, workspace layout and kernels of one search.
 // Launch with programmatic stream serialization (the kernel may start while
 // the one ahead of it on the stream finishes; it calls pdl_wait() before it
-// reads what that one writes).  FSP_PDL=0 launches in plain stream order.
+// reads what that one writes); on = false (FSP_PDL=0, read once per call)
+// launches in plain stream order.
 template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
-                              Args... args)
+static cudaError_t launch_pdl(bool on, void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t st, Args... args)
 {
-    const char *e = getenv("FSP_PDL");
-    const bool on = !(e && e[0] == '0');
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(block);
@@ -1105,6 +1104,8 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
     const BranchBound2Fn bb2 = P->bb2;
     const int per_cta = P->per_cta;
     const bool prof = timed && o.profile;
+    const char *pdl_env = getenv("FSP_PDL");
+    const bool pdl = !(pdl_env && pdl_env[0] == '0');  // programmatic dependent launch of the step's kernels
     int rc = FSP_OK;
     cudaStream_t st = (cudaStream_t)o.stream;
     SolveWs ws;
@@ -1192,7 +1193,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             if (wide) k_solve_init_nodes_wide<<<gi, SOLVE_B, 0, st>>>(ws, I->n, I->stride, o.init_count);
             const int scanned = gi > INIT_SCAN_BLOCKS;
             if (scanned) k_init_scan<<<1, 1024, 0, st>>>(ws, gi);
-            TRY(launch_pdl(k_init_cum, gi, SOLVE_B, 0, st, ws, I->n, I->stride, (long long)o.init_count, scanned));
+            TRY(launch_pdl(pdl, k_init_cum, gi, SOLVE_B, 0, st, ws, I->n, I->stride, (long long)o.init_count, scanned));
         } else {
             k_solve_init<<<1, 128, 0, st>>>(ws, I->n, rs, ub0);
         }
@@ -1215,7 +1216,7 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
             const int grid_bb = (int)((pool + I->n + per_cta - 1) / per_cta);
             idle = false;
             if (prof) LTRY(cudaEventRecord(pe[0], st));
-            LTRY(launch_pdl(k_select, 1, SELECT_B, 0, st, ws, I->n, rs, pool, (long long)o.node_budget,
+            LTRY(launch_pdl(pdl, k_select, 1, SELECT_B, 0, st, ws, I->n, rs, pool, (long long)o.node_budget,
                             (long long)o.max_iterations, (int)(P->bf == nullptr)));
             if (prof) LTRY(cudaEventRecord(pe[1], st));
             if (P->bidir && !P->bf) {  // children, their bounds, then the exact values of the complete ones
@@ -1257,15 +1258,15 @@ static int solve_run(fsp_instance *I, int32_t ub0, int32_t *cmax, int32_t *perm,
                 const int grid_f = (int)(fam < I->sm_count ? fam : I->sm_count);
                 DevInst Df = D;
                 Df.stride = rs;  // bidirectional records are wider
-                LTRY(launch_pdl(P->bf, (unsigned)grid_f, FL.warps * 32, FL.bytes, st, Df, ws, FL));
+                LTRY(launch_pdl(pdl, P->bf, (unsigned)grid_f, FL.warps * 32, FL.bytes, st, Df, ws, FL));
             } else if (bb2) {
                 bb2<<<grid_bb, shp.B, shp.L2.bytes, st>>>(D, ws, shp.L2);
             } else {
                 bb<<<grid_bb, shp.B, shp.L.bytes, st>>>(D, ws, shp.L);
             }
             if (prof) LTRY(cudaEventRecord(pe[2], st));
-            LTRY(launch_pdl(k_count, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
-            LTRY(launch_pdl(k_push, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
+            LTRY(launch_pdl(pdl, k_count, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
+            LTRY(launch_pdl(pdl, k_push, (unsigned)grid, SOLVE_B, 0, st, ws, I->n, rs));
             if (prof) LTRY(cudaEventRecord(pe[3], st));
             LTRY(cudaGetLastError());
 #undef LTRY
