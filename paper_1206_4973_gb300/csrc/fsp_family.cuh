@@ -306,7 +306,20 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
             // 32, so the lanes' reads of different rows fall in distinct banks)
             int32_t Ck = 0;
             if (d > 0) {
-                for (int i = 0; i < d; ++i) T[32 * i + lane] = pq_s[rec_s[i] * mp + k].x;
+                // four prefix jobs per round (one word of the record), all four
+                // loads issued before the stores (the stores may alias them)
+                for (int i0 = 0; i0 < d; i0 += 4) {
+                    const uint32_t wj = *reinterpret_cast<const uint32_t *>(rec_s + i0);
+                    int32_t v[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int j = i0 + b < d ? (int)((wj >> (8 * b)) & 0xFFu) : 0;
+                        v[b] = pq_s[j * mp + k].x;
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (i0 + b < d) T[32 * (i0 + b) + lane] = v[b];
+                }
 #pragma unroll 4
                 for (int t = 0; t < d + MT - 1; ++t) {
                     int32_t up = __shfl_up_sync(0xffffffffu, Ck, 1);
@@ -324,7 +337,14 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 // from the last at step t, after lane k+1 has finished it on machine k+1
                 // (the suffix's p values staged in the lane's column like the prefix's)
                 int32_t Dk = 0;
-                for (int si = 0; si < d2; ++si) T[32 * si + lane] = pq_s[rec_s[n - 1 - si] * mp + k].x;
+                for (int s0 = 0; s0 < d2; s0 += 4) {
+                    int32_t v[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) v[b] = s0 + b < d2 ? pq_s[rec_s[n - 1 - s0 - b] * mp + k].x : 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b)
+                        if (s0 + b < d2) T[32 * (s0 + b) + lane] = v[b];
+                }
 #pragma unroll 4
                 for (int t = 0; t < d2 + MT - 1; ++t) {
                     int32_t down = __shfl_down_sync(0xffffffffu, Dk, 1);
