@@ -300,12 +300,27 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 else Q2 = min(Q2, v.y);
             }
             // release times: lane k takes prefix position t - k at step t,
-            // after lane k-1 has finished that position on machine k-1.  Its
-            // p values are staged first in its own column of the scan table
-            // (free until the pair scans; row i = prefix position i, stride
-            // 32, so the lanes' reads of different rows fall in distinct banks)
+            // after lane k-1 has finished that position on machine k-1.  With
+            // 10 machines or more its p values are staged first in its own
+            // column of the scan table (free until the pair scans; row i =
+            // prefix position i, stride 32, so the lanes' reads of different
+            // rows fall in distinct banks); with 5, where the prefix is long
+            // against the wavefront's width, each step reads its own p value,
+            // two steps ahead of its use (measured faster there)
             int32_t Ck = 0;
-            if (d > 0) {
+            if (MT < 10 && d > 0) {
+                int32_t p0 = fam_prefix_p(0, lane, d, k, mp, rec_s, pq_s);
+                int32_t p1 = fam_prefix_p(1, lane, d, k, mp, rec_s, pq_s);
+                for (int t = 0; t < d + MT - 1; ++t) {
+                    const int32_t p2 = fam_prefix_p(t + 2, lane, d, k, mp, rec_s, pq_s);
+                    int32_t up = __shfl_up_sync(0xffffffffu, Ck, 1);
+                    if (lane == 0) up = 0;
+                    const int i = t - lane;
+                    if (lane < MT && i >= 0 && i < d) Ck = max(Ck, up) + p0;
+                    p0 = p1;
+                    p1 = p2;
+                }
+            } else if (d > 0) {
                 // four prefix jobs per round (one word of the record), all four
                 // loads issued before the stores (the stores may alias them)
                 for (int i0 = 0; i0 < d; i0 += 4) {
@@ -337,20 +352,30 @@ __device__ __forceinline__ void fam_bound(const FamView &V, const uint8_t *rec_s
                 // from the last at step t, after lane k+1 has finished it on machine k+1
                 // (the suffix's p values staged in the lane's column like the prefix's)
                 int32_t Dk = 0;
-                for (int s0 = 0; s0 < d2; s0 += 4) {
-                    int32_t v[4];
+                if (MT < 10) {
+                    for (int t = 0; t < d2 + MT - 1; ++t) {
+                        int32_t down = __shfl_down_sync(0xffffffffu, Dk, 1);
+                        if (lane == MT - 1) down = 0;
+                        const int si = t - (MT - 1 - lane);
+                        if (lane < MT && si >= 0 && si < d2)
+                            Dk = max(Dk, down) + pq_s[rec_s[n - 1 - si] * mp + k].x;
+                    }
+                } else {
+                    for (int s0 = 0; s0 < d2; s0 += 4) {
+                        int32_t v[4];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) v[b] = s0 + b < d2 ? pq_s[rec_s[n - 1 - s0 - b] * mp + k].x : 0;
+                        for (int b = 0; b < 4; ++b) v[b] = s0 + b < d2 ? pq_s[rec_s[n - 1 - s0 - b] * mp + k].x : 0;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b)
-                        if (s0 + b < d2) T[32 * (s0 + b) + lane] = v[b];
-                }
+                        for (int b = 0; b < 4; ++b)
+                            if (s0 + b < d2) T[32 * (s0 + b) + lane] = v[b];
+                    }
 #pragma unroll 4
-                for (int t = 0; t < d2 + MT - 1; ++t) {
-                    int32_t down = __shfl_down_sync(0xffffffffu, Dk, 1);
-                    if (lane == MT - 1) down = 0;
-                    const int si = t - (MT - 1 - lane);
-                    if (lane < MT && si >= 0 && si < d2) Dk = max(Dk, down) + T[32 * si + lane];
+                    for (int t = 0; t < d2 + MT - 1; ++t) {
+                        int32_t down = __shfl_down_sync(0xffffffffu, Dk, 1);
+                        if (lane == MT - 1) down = 0;
+                        const int si = t - (MT - 1 - lane);
+                        if (lane < MT && si >= 0 && si < d2) Dk = max(Dk, down) + T[32 * si + lane];
+                    }
                 }
                 if (lane < MT) pd[lane] = Dk;
             }
