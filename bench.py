@@ -46,8 +46,11 @@ SMS, INT_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
 ALU_LANES_PER_SM = 64
 # DRAM bytes (read + write) of one launch of the dominant kernel (k_branch_family on the step), from
 # one ncu capture of `bench.py --profile-case` (dram__bytes_read.sum + dram__bytes_write.sum); set to
-# None when that kernel changes, until it is captured again.
-BB_TRAFFIC_BYTES = 1080320
+# None when that kernel changes, until it is captured again.  The kernel has changed since the last
+# capture (its staged p values are now loaded four at a time), so the value is None and the last
+# capture's figure is reported beside it as such.
+BB_TRAFFIC_BYTES = None
+BB_TRAFFIC_LAST_CAPTURE = 1080320
 
 
 def work_ops(depth, n=N_JOBS, m=N_MACH):
@@ -679,6 +682,9 @@ def main():
     alu_peak = SMS * ALU_LANES_PER_SM * SM_MAX_MHZ * 1e6
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                 "frac": achieved / peak_ops, "traffic": BB_TRAFFIC_BYTES,
+                "traffic_last_capture": {"bytes": BB_TRAFFIC_LAST_CAPTURE,
+                                         "of": "the previous revision of k_branch_family (the same global "
+                                               "accesses; its shared-memory staging differed)"},
                 "kernel": "k_branch_family (branching + bounding of the pool's children, one warp per parent)",
                 "ops_per_launch": ops_per_step, "children_per_launch": n_children,
                 "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int32 lanes x {SM_MAX_MHZ:.0f} MHz (issue ceiling)",
