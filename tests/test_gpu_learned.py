@@ -119,7 +119,7 @@ def test_trained_network_cuts_more_than_untrained(F):
 
 def test_trained_network_time_against_the_plain_orders(F, monkeypatch):
     """What the trained network buys in time, on a fixed node budget: the
-    oracle judges the search (the learned search equals oracle.solve on a
+    oracle checks the search (the learned search equals oracle.solve on a
     budget it finishes quickly); on a larger budget the three arms explore
     the same nodes, and the learned order (inference included) takes less
     time than the plain order bounded child by child, the paper's one bound
